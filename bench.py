@@ -1,0 +1,313 @@
+"""Benchmark of the step-1 hot path at L = 451 (the paper's Algorithm 1 on synthetic inputs).
+
+One step = the sieve bound over 10^6 sampled starts (labs_sample_threshold) + 65,536 skew-symmetric
+self-avoiding walks of 10^5 flips each behind 256 distinct 24-element prefixes (labs_skew_search):
+6.55e9 flips, each scanning 202 neighbours x 225 even lags.  Metric: flips/s (higher is better).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own 65,536 walks (walk ids offset by
+rank), no data-path collective; value = all ranks' flips / max-over-ranks time ("weak" scaling).
+The reference arm (--impl reference) is the CPU oracle timed on the host cores on a bounded sample.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import labs_inputs as inp  # noqa: E402
+
+W1 = inp.STEP1_451
+METRIC = "flips/s"
+WORKLOAD = "step1_skew_walks_L451_p24_65536walks_1e5flips"
+SM_MAX_MHZ = 2070.0
+SMS = 152
+LANES_PER_SM = 128  # 4 schedulers x 32 lanes: one lane-instruction issue slot each per cycle
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "walk_kernel_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2409_07222_gb300", "csrc", f) for f in ("walk.cu", "labs_core.cuh")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--walks", type=int, default=W1["n_walks"])
+    ap.add_argument("--flips", type=int, default=W1["flip_budget"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-walks", type=int, default=64)
+    ap.add_argument("--cpu-flips", type=int, default=3000)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def terms_per_flip(L, p):
+    k = (L - 1) // 2
+    return (k - p + 1) * ((L - 1) // 2)  # free neighbours x even lags
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(flips_per_launch):
+    """DRAM bytes of one walk-kernel launch, scaled from the committed ncu capture; None if stale."""
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_flip"] * flips_per_launch
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(walks, flips, threads=None):
+    """The oracle (plain C over +-1 arrays) on a bounded sample of the same workload."""
+    import oracle
+
+    threads = threads or os.cpu_count() or 1
+    L, p = W1["L"], W1["p"]
+    pre = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"])
+    n_thr = max(1, W1["n_thresh_samples"] * walks // W1["n_walks"])
+    rank = min(n_thr - 1, W1["thresh_rank"] * walks // W1["n_walks"])
+    t0 = time.perf_counter()
+    thr = oracle.threshold(L, True, p, pre, W1["seed"], n_thr, rank)
+    oracle.walk_search(L, True, p, pre, walks, flips, W1["T_i"], W1["seed"], R=W1["R"], bloom_log2=W1["bloom_log2"],
+                       bloom_k=W1["bloom_k"], E_thr=thr, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": walks * flips / dt, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": "%d walks x %d flips of the L=451 p=24 workload (walk ids 0..%d) + sieve bound over %d "
+                      "samples, %.1f s" % (walks, flips, walks - 1, n_thr, dt)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    # each step is a bounded sample of the workload; the whole run stays within a few minutes
+    walks, flips = args.cpu_walks, max(200, args.cpu_flips // 2)
+    for _ in range(args.warmup):
+        cpu_baseline(walks, max(50, flips // 10))
+    t, vals = 0.0, []
+    res = None
+    for _ in range(args.steps):
+        res = cpu_baseline(walks, flips)
+        vals.append(res["value"])
+    value = statistics.mean(vals)
+    res["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": walks * flips / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": W1["L"], "p": W1["p"], "walks": W1["n_walks"],
+                       "flips_per_walk": W1["flip_budget"]},
+            "cpu_baseline": res, "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    lg.load()
+
+    L, p, R = W1["L"], W1["p"], W1["R"]
+    n_walks, budget = args.walks, args.flips
+    pre_h = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"])
+    pre = torch.from_numpy(pre_h.view(np.int64)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    thr = torch.empty(1, dtype=torch.int32, device=dev)
+
+    def step():
+        thr_t = lg.labs_sample_threshold(L, True, p, pre, W1["seed"], W1["n_thresh_samples"], W1["thresh_rank"])
+        thr.copy_(thr_t)  # torch copy outside the library: stays out of the walk-kernel window below
+        cfg = lg.make_walk_cfg(L, skew=True, p=p, n_walks=n_walks, flip_budget=budget, T_i=W1["T_i"],
+                               seed=W1["seed"], R=R, bloom_log2=W1["bloom_log2"], bloom_k=W1["bloom_k"],
+                               walk_begin=rank * n_walks, E_thr_dev=thr)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out, _, st = lg.labs_skew_search(cfg, pre, with_walk_stats=False)
+        e1.record()
+        return e0, e1, out, st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    clocks = ClockSampler(local)
+    step_ms, walk_ms = [], []
+    flips_seen = 0
+    launches_per_step = 4 + 2  # sample, select, histogram, select; walk init, walk
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        e0, e1, out, st = step()
+        s1.record()
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        walk_ms.append(e0.elapsed_time(e1))
+        flips_seen += int(lg.stats_numpy(st)["flips"])
+    barrier()
+    clk = clocks.stop()
+
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        f = torch.tensor([flips_seen], dtype=torch.int64, device=dev)
+        torch.distributed.all_reduce(f)
+        flips_seen = int(f.item())
+    expected = args.steps * n_walks * budget * ws
+    if flips_seen != expected:
+        raise RuntimeError("walks made %d flips, expected %d" % (flips_seen, expected))
+    value = flips_seen / (total_ms * 1e-3)
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms = []
+        cfg = lg.make_walk_cfg(L, skew=True, p=p, n_walks=n_walks, flip_budget=budget, T_i=W1["T_i"],
+                               seed=W1["seed"], R=R, bloom_log2=W1["bloom_log2"], bloom_k=W1["bloom_k"],
+                               E_thr=lg.LABS_AUTO_THRESHOLD, n_thresh_samples=W1["n_thresh_samples"],
+                               thresh_rank=W1["thresh_rank"], walk_begin=rank * n_walks)
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out_h, st_h = lg.labs_skew_search_host(cfg, pre_h, device=local)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        tot = sum(e2e_ms)
+        if ws > 1:
+            t = torch.tensor([tot], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        e2e = {"value": args.steps * n_walks * budget * ws / (tot * 1e-3), "unit": METRIC,
+               "h2d_bytes_per_step": int(pre_h.nbytes),
+               "d2h_bytes_per_step": int(n_walks * R * 96 + 48)}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    flips_per_launch = n_walks * budget
+    terms = flips_per_launch * terms_per_flip(L, p)
+    walk_s = statistics.mean(walk_ms) * 1e-3
+    achieved = terms / walk_s / 1e9
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "p": p, "walks_per_gpu": n_walks, "flips_per_walk": budget,
+                   "T_i": W1["T_i"], "prefixes": W1["n_prefix"], "thresh_samples": W1["n_thresh_samples"],
+                   "R": R, "bloom_bits": 1 << W1["bloom_log2"], "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "walks sharded by rank" if ws > 1 else "single GPU"},
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                     "traffic": traffic_per_launch(flips_per_launch),
+                     "kernel": "walk_kernel", "walk_kernel_ms": walk_s * 1e3,
+                     "work": "%d neighbour-lag terms per flip (202 free x 225 even lags), one int32 multiply-add "
+                             "each; peak = 152 SMs x 128 lanes x 2070 MHz" % terms_per_flip(L, p)},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_walks, args.cpu_flips)
+    print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

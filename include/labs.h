@@ -1,0 +1,173 @@
+/*
+ * labs.h -- C ABI of liblabs.so, a GB300 (sm_103a) implementation of the hot path of the dual-step
+ * search for low-autocorrelation binary sequences of Psenicnik, Mlinaric, Brest and Boskovic,
+ * "Dual-Step Optimization for Binary Sequences with High Merit Factors" (arXiv 2409.07222).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Sequences S = (s_1..s_L), s_i in {+1,-1}, 2 <= L <= 576, are bit-packed into W = ceil(L/64)
+ *    uint64 words: bit (i-1) % 64 of word (i-1) / 64 holds s_i, bit value 1 meaning +1 (the paper's
+ *    hexadecimal coding, Section 4, where a binary 0 stands for -1).  Bits above L-1 must be zero.
+ *  - Unless stated otherwise, pointers are DEVICE pointers owned by the caller; the library never
+ *    frees caller memory.  Internal workspace lives in the opaque context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *    stream-ordered and asynchronous: argument errors are returned immediately, device-side errors
+ *    (capacity, timeouts) are reported through the stats/status outputs once the stream has reached
+ *    them.  A context must not be used by two host threads at once.
+ *  - Every call returns LABS_OK or one of the LABS_ERR_* codes below.
+ *  - Energies are exact integers: E < L^3/3 < 2^31 for L <= 576.
+ */
+#ifndef LABS_H_
+#define LABS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LABS_OK 0
+#define LABS_ERR_INVALID_ARG 1 /* bad size, length, mode, alignment or layout */
+#define LABS_ERR_CAPACITY 2    /* a bounded device structure (heap, hash table, buffer) overflowed */
+#define LABS_ERR_TIMEOUT 3     /* a capped device-side wait gave up */
+#define LABS_ERR_CUDA 4        /* a CUDA runtime call or launch failed */
+#define LABS_ERR_NOMEM 5       /* workspace allocation failed */
+
+#define LABS_MAX_L 576
+#define LABS_MAX_W 9
+#define LABS_AUTO_THRESHOLD ((int32_t)0x80000000) /* E_thr: sample it (Algorithm 1's E_l) */
+
+typedef struct labs_ctx labs_ctx;
+
+/* Creates a context bound to CUDA device `device`.  *out receives the handle. */
+int labs_ctx_create(labs_ctx** out, int device);
+/* Releases the context's workspace.  Synchronises the device first. */
+void labs_ctx_destroy(labs_ctx* ctx);
+/* Static string naming a status code. */
+const char* labs_status_string(int status);
+/* Version of this ABI (bumped on any incompatible change). */
+int labs_abi_version(void);
+
+/*
+ * labs_energy_batch -- Section 1 definitions: C_k(S) = sum_{i=1}^{L-k} s_i s_{i+k} and
+ * E(S) = sum_{k=1}^{L-1} C_k(S)^2, for n sequences at once (Algorithm 1's and 2's ENERGY).
+ *   seqs   [n][W] uint64, device, 8-byte aligned.
+ *   E_out  [n] int32, device.
+ *   C_out  nullable; [n][L-1] int32, device: C_out[q*(L-1) + k-1] = C_k of sequence q.
+ * Errors: LABS_ERR_INVALID_ARG if L outside [2, 576], n < 0 or a pointer is NULL/misaligned.
+ */
+int labs_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out,
+                      void* stream);
+
+/*
+ * labs_flip_deltas -- the single-flip neighbourhood scan of BEST_NEIGHBOUR (Algorithm 1, Section 3)
+ * and of Algorithm 2's loop: Delta E of every neighbour, exactly.
+ *   skew = 0: unrestricted neighbourhood (SEQUENCE_FLIP): dE[q][i-1] = E(S with s_i negated) - E(S)
+ *             for i = p+1..L.
+ *   skew = 1: skew-symmetric neighbourhood (SEQUENCE_FLIP_SKEW, Eq. 2-3; L odd, L = 2k+1, inputs
+ *             must be skew-symmetric): for every free position m in [p+1, k+1] the neighbour negates
+ *             s_m and its mirror s_{L+1-m} (the centre k+1 alone); dE[q][m-1] holds its Delta E.
+ *   Entries outside the free range are INT32_MAX.  dE is [n][L] int32, device.
+ *   C      nullable; [n][L-1] int32 correlation tables as written by labs_energy_batch.  When given,
+ *          the kernel uses them instead of rebuilding them (results are identical when they match).
+ * Errors: LABS_ERR_INVALID_ARG for L outside [2, 576], odd/even mismatch with `skew`, p out of range.
+ */
+int labs_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int L, int64_t n, int skew, int p,
+                     int32_t* dE_out, void* stream);
+
+/* One candidate record of the sieve (Algorithm 1's E < E_l test).  96 bytes. */
+typedef struct {
+  int32_t E;     /* energy of seq */
+  uint32_t walk; /* global walk id that reached it */
+  uint32_t step; /* that walk's accepted-flip count when it was reached (1-based) */
+  uint32_t pad;
+  uint64_t fp; /* 64-bit Zobrist fingerprint of seq */
+  uint64_t seq[LABS_MAX_W];
+} labs_candidate;
+
+/*
+ * Walk configuration (Algorithm 1).  Readings where the paper gives no value:
+ *  - a walk restarts (fresh free elements, same prefix, Bloom filter cleared) after T_i accepted
+ *    flips or when no unexplored neighbour is left; flip_budget counts accepted flips over all of a
+ *    walk's segments;
+ *  - BEST_NEIGHBOUR picks the smallest (Delta E, m) whose neighbour fingerprint is not in the Bloom
+ *    filter (2^bloom_log2 bits, bloom_k probes, double hashing of the fingerprint);
+ *  - the sieve keeps per walk the R smallest distinct (E, fp) states with E <= E_thr reached by a flip.
+ * Walk w uses prefix w mod n_prefix and draws its free elements from the counter-based SplitMix64
+ * stream (seed, walk=1, w, segment).
+ */
+typedef struct {
+  int32_t L;            /* 2..576 */
+  int32_t skew;         /* 1: skew-symmetric walk, L odd (Algorithm 1); 0: unrestricted walk */
+  int32_t p;            /* prefix length (restriction class, Eq. 3); <= k (skew) or < L */
+  int32_t T_i;          /* segment length; <= 0 means 8(L+1)/2 = 4(L+1) */
+  int64_t n_walks;      /* walks; walk ids are walk_begin .. walk_begin+n_walks-1 */
+  int64_t walk_begin;   /* first global walk id (lets a caller shard walks) */
+  int64_t flip_budget;  /* accepted flips per walk */
+  uint64_t seed;        /* stream seed */
+  int32_t R;            /* candidates kept per walk, 1..32 */
+  int32_t bloom_log2;   /* Bloom filter bits = 2^bloom_log2, 5..15 */
+  int32_t bloom_k;      /* Bloom probes, 1..8 */
+  int32_t E_thr;        /* sieve bound (E <= E_thr passes) or LABS_AUTO_THRESHOLD */
+  int64_t n_thresh_samples; /* auto threshold: starts sampled (stream (seed, 2, i, 0)), e.g. 10^6 */
+  int64_t thresh_rank;      /* auto threshold: 0-based rank of E_thr among the samples, e.g. 999 */
+  int32_t E_target;     /* record each walk's first flip reaching E <= E_target; INT32_MIN = off */
+  int32_t tile_m;       /* neighbours per lane tile (4, 8, 12 or 16); 0 = autotuned */
+  int32_t warps_per_cta;/* walks resident per CTA (1..8); 0 = autotuned */
+  int32_t reserved;
+  const int32_t* E_thr_dev; /* nullable device int32: when set, the sieve bound is read from it (for
+                               instance written by labs_sample_threshold on the same stream) and
+                               E_thr is ignored */
+} labs_walk_cfg;
+
+/* Aggregates over all walks of one call, written to device memory. */
+typedef struct {
+  int64_t flips;        /* accepted flips */
+  int64_t segments;     /* walk segments started */
+  int64_t bloom_skips;  /* Bloom-positive neighbours that ranked ahead of the chosen move */
+  int64_t dead_ends;    /* segments ended because every neighbour was explored */
+  int32_t E_thr;        /* sieve bound actually used */
+  int32_t best_E;       /* lowest energy reached by any flip */
+  int32_t status;       /* LABS_OK or a device-side error */
+  int32_t reserved;
+} labs_walk_stats;
+
+/*
+ * labs_skew_search -- step 1 of the paper (Algorithm 1, Fig. 2-3): n_walks independent self-avoiding
+ * walks, one per warp, each behind a fixed prefix, sieving candidates with E <= E_thr.
+ *   prefixes   [n_prefix][ceil(p/64)] uint64, device: bit j of word 0 is 1 iff s_{j+1} = +1.
+ *   out        [n_walks][R] labs_candidate, device, sorted by (E, fp) per walk; unused slots have
+ *              E = INT32_MAX, fp = ~0 and zero elsewhere.
+ *   walk_stats nullable; [n_walks][6] int64, device: flips, segments, bloom_skips, dead_ends, best_E,
+ *              first flip count with E <= E_target (-1 if never or off).
+ *   stats      labs_walk_stats, device.
+ * Errors: LABS_ERR_INVALID_ARG on a bad configuration.
+ */
+int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
+                     labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, void* stream);
+
+/*
+ * labs_sample_threshold -- the sieve bound E_l of Algorithm 1 under the nearest-rank reading: draws
+ * n_samples starts exactly like walk starts (sample i: prefix i mod n_prefix, stream (seed, 2, i, 0))
+ * and writes the 0-based `rank`-th smallest sampled energy to *E_thr_out (device int32).
+ *   E_samples nullable; [n_samples] int32, device: the sampled energies in sample order.
+ */
+int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
+                          uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out, int32_t* E_samples,
+                          void* stream);
+
+/*
+ * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
+ * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
+ * s_{p+1+j} = -1.
+ *   out_min_E [1] int32, out_count [1] uint64 (assignments reaching the minimum),
+ *   out_argmin_free [1] uint64 (smallest such assignment), out_argmin_seq [W] uint64; all device.
+ */
+int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
+                         uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABS_H_ */

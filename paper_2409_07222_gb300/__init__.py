@@ -1,0 +1,178 @@
+"""GB300-native hot path of the dual-step LABS search (arXiv 2409.07222).
+
+Thin binding over liblabs.so (include/labs.h): every function here only marshals arguments (torch
+tensors for device memory, the current CUDA stream) and calls the C ABI of the same name; all
+arithmetic runs in the library's sm_103a kernels.  Packed sequences are int64 (or uint64) tensors of
+shape [n, W], W = ceil(L/64): bit (i-1) % 64 of word (i-1) // 64 is 1 iff s_i = +1.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (INT32_MAX, INT32_MIN, LABS_AUTO_THRESHOLD, LABS_MAX_L, LABS_MAX_W, LabsError, WalkCfg,
+                   load, status_string)
+
+CANDIDATE_DTYPE = np.dtype(
+    [("E", "<i4"), ("walk", "<u4"), ("step", "<u4"), ("pad", "<u4"), ("fp", "<u8"), ("seq", "<u8", (LABS_MAX_W,))]
+)
+WALK_STATS_DTYPE = np.dtype(
+    [("flips", "<i8"), ("segments", "<i8"), ("bloom_skips", "<i8"), ("dead_ends", "<i8"), ("E_thr", "<i4"),
+     ("best_E", "<i4"), ("status", "<i4"), ("reserved", "<i4")]
+)
+assert CANDIDATE_DTYPE.itemsize == _lib.CANDIDATE_BYTES and WALK_STATS_DTYPE.itemsize == _lib.WALK_STATS_BYTES
+
+_ctxs = {}
+
+
+def words_per_seq(L):
+    return (L + 63) // 64
+
+
+def context(device=None):
+    """The library context of a CUDA device (created on first use)."""
+    dev = _device(device)
+    idx = dev.index
+    if idx not in _ctxs:
+        h = ctypes.c_void_p()
+        _lib.check(load().labs_ctx_create(ctypes.byref(h), idx), "labs_ctx_create")
+        _ctxs[idx] = h
+    return _ctxs[idx]
+
+
+def _device(device):
+    if isinstance(device, torch.device):
+        return device if device.index is not None else torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cuda", torch.cuda.current_device() if device is None else device)
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dev_words(seqs, L):
+    if not seqs.is_cuda:
+        raise ValueError("sequences must be a CUDA tensor")
+    if seqs.dtype not in (torch.int64, torch.uint64):
+        raise ValueError("sequences must be int64/uint64 words")
+    s = seqs.reshape(-1, words_per_seq(L))
+    if not s.is_contiguous():
+        s = s.contiguous()
+    return s
+
+
+def labs_energy_batch(seqs, L, with_C=False):
+    """E [n] int32 (and C [n, L-1] int32 when with_C) of the packed sequences."""
+    s = _dev_words(seqs, L)
+    n = s.shape[0]
+    E = torch.empty(n, dtype=torch.int32, device=s.device)
+    C = torch.empty((n, L - 1), dtype=torch.int32, device=s.device) if with_C else None
+    _lib.check(load().labs_energy_batch(context(s.device.index), _ptr(s), L, n, _ptr(E), _ptr(C), _stream(s.device)),
+               "labs_energy_batch")
+    return (E, C) if with_C else E
+
+
+def labs_flip_deltas(seqs, L, skew=False, p=0, C=None):
+    """dE [n, L] int32: Delta E of every neighbour (position m-1), INT32_MAX outside the free range."""
+    s = _dev_words(seqs, L)
+    n = s.shape[0]
+    dE = torch.empty((n, L), dtype=torch.int32, device=s.device)
+    if C is not None:
+        C = C.reshape(n, L - 1).to(torch.int32).contiguous()
+    _lib.check(load().labs_flip_deltas(context(s.device.index), _ptr(s), _ptr(C), L, n, int(bool(skew)), p, _ptr(dE),
+                                       _stream(s.device)), "labs_flip_deltas")
+    return dE
+
+
+def _prefix_tensor(prefixes, p, device):
+    pw = max(1, (p + 63) // 64)
+    if isinstance(prefixes, torch.Tensor):
+        t = prefixes.to(device=device)
+        if t.dtype == torch.uint64:
+            t = t.view(torch.int64)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(np.asarray(prefixes, dtype=np.uint64)).view(np.int64)).to(device)
+    return t.reshape(-1, pw).contiguous()
+
+
+def labs_sample_threshold(L, skew, p, prefixes, seed, n_samples, rank, return_samples=False, device=None):
+    """Sieve bound: 0-based `rank`-th smallest energy of n_samples walk-like starts (device int32 [1])."""
+    dev = _device(device)
+    pre = _prefix_tensor(prefixes, p, dev)
+    thr = torch.empty(1, dtype=torch.int32, device=dev)
+    samples = torch.empty(n_samples, dtype=torch.int32, device=dev) if return_samples else None
+    _lib.check(load().labs_sample_threshold(context(dev.index), L, int(bool(skew)), p, _ptr(pre), pre.shape[0], seed,
+                                            n_samples, rank, _ptr(thr), _ptr(samples), _stream(dev)),
+               "labs_sample_threshold")
+    return (thr, samples) if return_samples else thr
+
+
+def make_walk_cfg(L, skew=True, p=0, n_walks=1, flip_budget=1000, T_i=0, seed=0, R=16, bloom_log2=15, bloom_k=4,
+                  E_thr=INT32_MAX, n_thresh_samples=0, thresh_rank=0, E_target=INT32_MIN, walk_begin=0, tile_m=0,
+                  warps_per_cta=0, E_thr_dev=None):
+    """labs_walk_cfg; E_thr_dev (a device int32 tensor) makes the walk read its sieve bound from it."""
+    cfg = WalkCfg()
+    cfg.L, cfg.skew, cfg.p, cfg.T_i = L, int(bool(skew)), p, T_i
+    cfg.n_walks, cfg.walk_begin, cfg.flip_budget, cfg.seed = n_walks, walk_begin, flip_budget, seed
+    cfg.R, cfg.bloom_log2, cfg.bloom_k, cfg.E_thr = R, bloom_log2, bloom_k, E_thr
+    cfg.n_thresh_samples, cfg.thresh_rank = n_thresh_samples, thresh_rank
+    cfg.E_target, cfg.tile_m, cfg.warps_per_cta = E_target, tile_m, warps_per_cta
+    cfg.E_thr_dev = E_thr_dev.data_ptr() if E_thr_dev is not None else None
+    return cfg
+
+
+def labs_skew_search(cfg, prefixes, device=None, with_walk_stats=True):
+    """Algorithm 1 walks on the device.
+
+    Returns (candidates uint8 [n_walks * R * 96] device tensor, walk_stats int64 [n_walks, 6] or None,
+    stats uint8 [48] device tensor).  ``candidates_numpy`` / ``stats_numpy`` decode them.
+    """
+    dev = _device(device)
+    pre = _prefix_tensor(prefixes, cfg.p, dev)
+    out = torch.empty(max(1, cfg.n_walks * cfg.R * _lib.CANDIDATE_BYTES), dtype=torch.uint8, device=dev)
+    ws = torch.empty((max(1, cfg.n_walks), 6), dtype=torch.int64, device=dev) if with_walk_stats else None
+    st = torch.empty(_lib.WALK_STATS_BYTES, dtype=torch.uint8, device=dev)
+    _lib.check(load().labs_skew_search(context(dev.index), ctypes.byref(cfg), _ptr(pre), pre.shape[0], _ptr(out),
+                                       _ptr(ws), _ptr(st), _stream(dev)), "labs_skew_search")
+    return out, ws, st
+
+
+def labs_skew_search_host(cfg, prefixes_host, device=None):
+    """End-to-end form: host prefixes in, host candidates/stats out (copies included)."""
+    dev = _device(device)
+    pre_h = torch.from_numpy(np.ascontiguousarray(np.asarray(prefixes_host, dtype=np.uint64)).view(np.int64))
+    pre_h = pre_h.pin_memory()
+    pre = pre_h.to(dev, non_blocking=True)
+    out, ws, st = labs_skew_search(cfg, pre, device=dev, with_walk_stats=False)
+    out_h = torch.empty(out.shape, dtype=torch.uint8, pin_memory=True)
+    st_h = torch.empty(st.shape, dtype=torch.uint8, pin_memory=True)
+    out_h.copy_(out, non_blocking=True)
+    st_h.copy_(st, non_blocking=True)
+    torch.cuda.current_stream(dev).synchronize()
+    return out_h, st_h
+
+
+def candidates_numpy(out, n_walks, R):
+    a = out.cpu().numpy()[: n_walks * R * _lib.CANDIDATE_BYTES]
+    return a.view(CANDIDATE_DTYPE).reshape(n_walks, R)
+
+
+def stats_numpy(st):
+    return st.cpu().numpy().view(WALK_STATS_DTYPE)[0]
+
+
+def labs_skew_exhaustive(L, p=0, prefix=0, device=None):
+    """(min E, count, argmin free-bit integer, argmin packed words) over all skew sequences."""
+    dev = _device(device)
+    minE = torch.empty(1, dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    arg = torch.empty(1, dtype=torch.int64, device=dev)
+    seq = torch.zeros(words_per_seq(L), dtype=torch.int64, device=dev)
+    _lib.check(load().labs_skew_exhaustive(context(dev.index), L, p, prefix, _ptr(minE), _ptr(cnt), _ptr(arg),
+                                           _ptr(seq), _stream(dev)), "labs_skew_exhaustive")
+    return minE, cnt, arg, seq

@@ -1,0 +1,168 @@
+// api.cu -- the C ABI of liblabs.so: context, argument validation, dispatch to the kernels.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "labs_core.cuh"
+#include "labs_internal.h"
+
+namespace labsg {
+
+void* ws_get(labs_ctx* ctx, int slot, size_t bytes) {
+  if (slot < 0 || slot >= 8) return nullptr;
+  if (ctx->ws_bytes[slot] >= bytes && ctx->ws[slot]) return ctx->ws[slot];
+  if (ctx->ws[slot]) {
+    cudaDeviceSynchronize();
+    cudaFree(ctx->ws[slot]);
+    ctx->ws[slot] = nullptr;
+    ctx->ws_bytes[slot] = 0;
+  }
+  size_t want = bytes < 256 ? 256 : bytes;
+  void* p = nullptr;
+  if (cudaMalloc(&p, want) != cudaSuccess) return nullptr;
+  ctx->ws[slot] = p;
+  ctx->ws_bytes[slot] = want;
+  return p;
+}
+
+}  // namespace labsg
+
+namespace {
+
+bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+int set_device(labs_ctx* ctx) { return cudaSetDevice(ctx->device) == cudaSuccess ? LABS_OK : LABS_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int labs_abi_version(void) { return 1; }
+
+const char* labs_status_string(int status) {
+  switch (status) {
+    case LABS_OK: return "ok";
+    case LABS_ERR_INVALID_ARG: return "invalid argument";
+    case LABS_ERR_CAPACITY: return "capacity exceeded";
+    case LABS_ERR_TIMEOUT: return "device wait timed out";
+    case LABS_ERR_CUDA: return "CUDA error";
+    case LABS_ERR_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+int labs_ctx_create(labs_ctx** out, int device) {
+  if (!out) return LABS_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return LABS_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return LABS_ERR_CUDA;
+  labs_ctx* c = new (std::nothrow) labs_ctx();
+  if (!c) return LABS_ERR_NOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->device = device;
+  int sms = 0, optin = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->num_sms = sms > 0 ? sms : 1;
+  c->smem_optin = (size_t)optin;
+  *out = c;
+  return LABS_OK;
+}
+
+void labs_ctx_destroy(labs_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (int i = 0; i < 8; i++)
+    if (ctx->ws[i]) cudaFree(ctx->ws[i]);
+  delete ctx;
+}
+
+int labs_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out,
+                      void* stream) {
+  if (!ctx || L < 2 || L > LABS_MAX_L || n < 0) return LABS_ERR_INVALID_ARG;
+  if (n > 0 && (!seqs || !E_out || !aligned8(seqs) || !aligned4(E_out) || (C_out && !aligned4(C_out))))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_energy_batch(ctx, seqs, L, n, E_out, C_out, (cudaStream_t)stream);
+}
+
+int labs_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int L, int64_t n, int skew, int p,
+                     int32_t* dE_out, void* stream) {
+  if (!ctx || L < 2 || L > LABS_MAX_L || n < 0 || (skew != 0 && skew != 1) || p < 0) return LABS_ERR_INVALID_ARG;
+  if (skew && (L % 2 == 0 || L < 3 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
+  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
+  if (n > 0 && (!seqs || !dE_out || !aligned8(seqs) || !aligned4(dE_out) || (C && !aligned4(C))))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_flip_deltas(ctx, seqs, C, L, n, skew, p, dE_out, (cudaStream_t)stream);
+}
+
+static int check_walk_shape(int L, int skew, int p, int n_prefix, const uint64_t* prefixes) {
+  if (L < 3 || L > LABS_MAX_L || (skew != 0 && skew != 1) || p < 0 || n_prefix < 1) return LABS_ERR_INVALID_ARG;
+  if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
+  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
+  if (p > 64 * LABS_MAX_W) return LABS_ERR_INVALID_ARG;
+  if (!prefixes || !aligned8(prefixes)) return LABS_ERR_INVALID_ARG;
+  return LABS_OK;
+}
+
+int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
+                          uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out, int32_t* E_samples,
+                          void* stream) {
+  if (!ctx) return LABS_ERR_INVALID_ARG;
+  int s = check_walk_shape(L, skew, p, n_prefix, prefixes);
+  if (s != LABS_OK) return s;
+  if (n_samples < 1 || rank < 0 || rank >= n_samples || !E_thr_out || !aligned4(E_thr_out) ||
+      (E_samples && !aligned4(E_samples)))
+    return LABS_ERR_INVALID_ARG;
+  s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  int pw = p > 0 ? (p + 63) / 64 : 1;
+  return labsg::launch_sample_threshold(ctx, L, skew, p, prefixes, n_prefix, pw, seed, n_samples, rank, E_thr_out,
+                                       E_samples, (cudaStream_t)stream);
+}
+
+int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
+                     labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, void* stream) {
+  if (!ctx || !cfg) return LABS_ERR_INVALID_ARG;
+  int s = check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
+  if (s != LABS_OK) return s;
+  if (cfg->n_walks < 0 || cfg->walk_begin < 0 || cfg->flip_budget < 0 || cfg->R < 1 || cfg->R > labsg::kMaxR ||
+      cfg->bloom_log2 < 5 || cfg->bloom_log2 > 15 || cfg->bloom_k < 1 || cfg->bloom_k > 8)
+    return LABS_ERR_INVALID_ARG;
+  if (cfg->walk_begin + cfg->n_walks > 0xffffffffLL) return LABS_ERR_INVALID_ARG;  // walk ids are stored as u32
+  if (cfg->flip_budget > 0xffffffffLL) return LABS_ERR_INVALID_ARG;               // steps are stored as u32
+  if (cfg->tile_m != 0 && cfg->tile_m != 4 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16)
+    return LABS_ERR_INVALID_ARG;
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
+  if (cfg->E_thr_dev && !aligned4(cfg->E_thr_dev)) return LABS_ERR_INVALID_ARG;
+  if (!cfg->E_thr_dev && cfg->E_thr == LABS_AUTO_THRESHOLD &&
+      (cfg->n_thresh_samples < 1 || cfg->thresh_rank < 0 || cfg->thresh_rank >= cfg->n_thresh_samples))
+    return LABS_ERR_INVALID_ARG;
+  if (!stats || !aligned8(stats) || (cfg->n_walks > 0 && (!out || !aligned8(out))) ||
+      (walk_stats && !aligned8(walk_stats)))
+    return LABS_ERR_INVALID_ARG;
+  s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_skew_search(ctx, cfg, prefixes, n_prefix, out, walk_stats, stats, (cudaStream_t)stream);
+}
+
+int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
+                         uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
+  if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;
+  if ((L - 1) / 2 - p + 1 > 40 || p > 64) return LABS_ERR_INVALID_ARG;
+  if (!out_min_E || !out_count || !out_argmin_free || !out_argmin_seq || !aligned4(out_min_E) ||
+      !aligned8(out_count) || !aligned8(out_argmin_free) || !aligned8(out_argmin_seq))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_skew_exhaustive(ctx, L, p, prefix, out_min_E, out_count, out_argmin_free, out_argmin_seq,
+                                      (cudaStream_t)stream);
+}
+
+}  // extern "C"

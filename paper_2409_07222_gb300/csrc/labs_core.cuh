@@ -1,0 +1,478 @@
+// labs_core.cuh -- device building blocks shared by the LABS kernels (sm_103a).
+//
+// One walk (or one sequence) is owned by one warp.  Its state lives in the warp's shared-memory slab:
+//   * the sequence, bit-packed (32-bit words, 1 = +1);
+//   * the correlation table C_{lambda g}, g = 1..G, as int16 (master) and int8 (fast-path copy);
+//   * "byte windows": for every neighbour m the kernel needs s_{m + lambda g} and s_{m - lambda g}
+//     for g = 1..G.  They are stored as one byte per position, enc(s) = s + 1 in {0, 2} and 1 for a
+//     position outside 1..L, in a forward array and a reversed array per position class, so that both
+//     windows of every neighbour are contiguous and increasing in g.
+//
+// lambda is the lag stride: 2 for skew-symmetric walks (odd lags have C = 0 by Eq. 2 and stay 0 under
+// skew-preserving flips, so only even lags are tracked and positions split by parity into two
+// classes), 1 for unrestricted walks.
+//
+// Single-flip Delta E (Section 3, linear-time neighbour evaluation).  Flipping F in {{m}, {m, m'}}
+// changes C_kappa by delta_kappa = -alpha s_m y_kappa with
+//   y_kappa = s_{m+kappa}[valid] + s_{m-kappa}[valid]      (the pair (m, m') itself excluded),
+//   alpha   = 2 (single flip, or the skew centre), 4 (skew pair m, m' = L+1-m: the mirror products
+//             equal the direct ones for even kappa),
+// so Delta E = sum_kappa delta(2C + delta) = -2 alpha s_m T_m + alpha^2 Q_m, where
+//   T_m = sum_kappa C_kappa y_kappa                    -- O(#lags) per neighbour: the hot loop
+//   Q_m = sum_kappa y_kappa^2 = n_f + n_b + 2 P_m      -- P_m = sum s_{m-kappa} s_{m+kappa}, kept
+//                                                        incrementally (O(1) per neighbour per flip).
+// The hot loop computes T_m four lags at a time: y' = fwd4 + bwd4 (bytes 0..4, no carries) and
+// dp4a(y', C4) accumulates sum C (y + 2); 2 sum C is subtracted once.  With |C| <= 127 the table fits
+// int8 (dp4a); otherwise the exact int16 path (dp2a) runs.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "labs.h"
+
+namespace labsg {
+
+constexpr int kMaxL = LABS_MAX_L;
+constexpr int kQOff = 3;             // class index of the first position of a class
+constexpr int kDirBytes = 1216;      // byte-window array per direction (two 608-byte classes when skew)
+constexpr int kClassBytes = 608;
+constexpr int kCLen = 592;           // correlation table slots (>= 4 * NG + 4 for every L <= 576)
+constexpr int kBitWords = 20;        // 18 words for 576 bits + 2 zero words for funnel shifts
+constexpr int kMaxR = 32;
+
+// ------------------------------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), counter form: output i of the generator whose state
+// starts at `key`.  Streams are keyed by chaining at(at(at(seed, purpose), a), b).
+// ------------------------------------------------------------------------------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+enum : uint64_t { kPurposeWalk = 1, kPurposeThresh = 2, kPurposeZobrist = 0x5A0B };
+
+__host__ __device__ __forceinline__ uint64_t sm64_at(uint64_t key, uint64_t i) {
+  uint64_t z = key + (i + 1) * kGamma;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t stream_key(uint64_t seed, uint64_t purpose, uint64_t a, uint64_t b) {
+  return sm64_at(sm64_at(sm64_at(seed, purpose), a), b);
+}
+
+// Zobrist key of position i (1-based) for length L, given zkey = stream_key(0, Zobrist, L, 0).
+__device__ __forceinline__ uint64_t zobrist(uint64_t zkey, int i) { return sm64_at(zkey, (uint64_t)(i - 1)); }
+
+// ------------------------------------------------------------------------------------------------
+// Warp helpers
+// ------------------------------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ int warp_sum_i32(int v) { return __reduce_add_sync(kFull, v); }
+__device__ __forceinline__ int warp_min_i32(int v) { return __reduce_min_sync(kFull, v); }
+__device__ __forceinline__ int warp_max_i32(int v) { return __reduce_max_sync(kFull, v); }
+__device__ __forceinline__ unsigned warp_min_u32(unsigned v) { return __reduce_min_sync(kFull, v); }
+
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint64_t warp_xor_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v ^= __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Layout of one walk for (L, skew, p, M).  Identical on every lane (pure function of its inputs).
+// ------------------------------------------------------------------------------------------------
+struct Layout {
+  int L, skew, p, lam, G, NG, c, mlast;
+  int ncls;
+  int tile_first[2], ntiles[2];
+  int n_tiles;
+  int Qr;
+  int M;
+};
+
+// word offset of class `cls` inside the fwd/bwd arrays (class 1 exists only for skew walks)
+__host__ __device__ __forceinline__ int cls_words(int cls) { return cls * (kClassBytes / 4); }
+
+// class and class index of position i (1-based)
+__host__ __device__ __forceinline__ int pos_cls(const Layout& ly, int i) { return ly.skew ? (i & 1) : 0; }
+__host__ __device__ __forceinline__ int pos_q(const Layout& ly, int i) {
+  return ly.skew ? ((i - ((i & 1) ? 1 : 2)) >> 1) + kQOff : i - 1 + kQOff;
+}
+__host__ __device__ __forceinline__ int q_pos(const Layout& ly, int cls, int q) {
+  return ly.skew ? 2 * (q - kQOff) + (cls ? 1 : 2) : q - kQOff + 1;
+}
+
+__host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, int M) {
+  ly.L = L;
+  ly.skew = skew;
+  ly.p = p;
+  ly.M = M;
+  ly.lam = skew ? 2 : 1;
+  ly.G = (L - 1) / ly.lam;
+  ly.NG = (ly.G + 3) / 4;
+  ly.c = (L + 1) / 2;
+  ly.mlast = skew ? ly.c : L;
+  ly.ncls = skew ? 2 : 1;
+  ly.n_tiles = 0;
+  int qmax_end = 0;
+  for (int cls = 0; cls < 2; cls++) {
+    ly.tile_first[cls] = 0;
+    ly.ntiles[cls] = 0;
+    if (cls >= ly.ncls) continue;
+    int i_lo = p + 1, i_hi = ly.mlast;
+    if (skew) {
+      if ((i_lo & 1) != cls) i_lo++;
+      if ((i_hi & 1) != cls) i_hi--;
+    }
+    if (i_lo > i_hi) continue;
+    int q_lo = pos_q(ly, i_lo), q_hi = pos_q(ly, i_hi);
+    int first = ((q_lo - 3) / 4) * 4 + 3;
+    int nt = (q_hi - first + 1 + M - 1) / M;
+    ly.tile_first[cls] = first;
+    ly.ntiles[cls] = nt;
+    ly.n_tiles += nt;
+    int end = first + nt * M - 1;
+    if (end > qmax_end) qmax_end = end;
+  }
+  ly.Qr = qmax_end + ((2 - (qmax_end & 3)) & 3);
+  // byte windows must stay inside a class array (see the bound derivation in the design notes)
+  int cap = skew ? kClassBytes : kDirBytes;
+  int need_f = qmax_end + 4 * ly.NG + 8;
+  int need_b = ly.Qr + 4 * ly.NG + 8;
+  return need_f < cap && need_b < cap && 4 * ly.NG + 4 <= kCLen && L >= 2 && L <= kMaxL;
+}
+
+// Tile tau -> (class, first class index).
+__device__ __forceinline__ void tile_of(const Layout& ly, int tau, int& cls, int& q0) {
+  if (tau < ly.ntiles[0]) {
+    cls = 0;
+    q0 = ly.tile_first[0] + tau * ly.M;
+  } else {
+    cls = 1;
+    q0 = ly.tile_first[1] + (tau - ly.ntiles[0]) * ly.M;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Shared-memory slab of one warp
+// ------------------------------------------------------------------------------------------------
+struct __align__(16) ScanSmem {
+  uint32_t fwd[kDirBytes / 4];
+  uint32_t bwd[kDirBytes / 4];
+  int16_t C16[kCLen];  // C_{lambda (h+1)} at h, zero beyond G
+  int8_t C8[kCLen];    // int8 copy, valid when every |C| <= 127
+  uint32_t bits[kBitWords];
+};
+
+__device__ __forceinline__ int seq_bit(const ScanSmem& sm, int i) { return (sm.bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1; }
+
+__device__ __forceinline__ int fwd_byte(const ScanSmem& sm, const Layout& ly, int cls, int q) {
+  return reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(cls))[q];
+}
+__device__ __forceinline__ int bwd_byte(const ScanSmem& sm, const Layout& ly, int cls, int t) {
+  return reinterpret_cast<const uint8_t*>(sm.bwd + cls_words(cls))[t];
+}
+// s_i in {-1, +1} read from the forward byte array
+__device__ __forceinline__ int s_at(const ScanSmem& sm, const Layout& ly, int i) {
+  return fwd_byte(sm, ly, pos_cls(ly, i), pos_q(ly, i)) - 1;
+}
+
+// Byte windows from the packed bits (whole arrays, pads included).
+__device__ inline void build_bytes(ScanSmem& sm, const Layout& ly) {
+  const int lane = lane_id();
+  const int words_per_cls = (ly.skew ? kClassBytes : kDirBytes) / 4;
+  for (int cls = 0; cls < ly.ncls; cls++) {
+    uint32_t* F = sm.fwd + cls_words(cls);
+    uint32_t* B = sm.bwd + cls_words(cls);
+    for (int w = lane; w < words_per_cls; w += 32) {
+      uint32_t fw = 0, bw = 0;
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        int t = 4 * w + e;
+        int i = q_pos(ly, cls, t);
+        uint32_t fb = (i >= 1 && i <= ly.L) ? (seq_bit(sm, i) ? 2u : 0u) : 1u;
+        int ib = q_pos(ly, cls, ly.Qr - t);
+        uint32_t bb = (ib >= 1 && ib <= ly.L) ? (seq_bit(sm, ib) ? 2u : 0u) : 1u;
+        fw |= fb << (8 * e);
+        bw |= bb << (8 * e);
+      }
+      F[w] = fw;
+      B[w] = bw;
+    }
+  }
+  __syncwarp();
+}
+
+// C_k = (L-k) - 2 popc((x XOR (x >> k)) restricted to the low L-k bits) from the packed bits.
+__device__ __forceinline__ int corr_lag(const uint32_t* bits, int L, int k) {
+  const int n = L - k;  // number of products s_i s_{i+k}
+  const int ws = k >> 5, sh = k & 31;
+  const int nw = (n + 31) >> 5;
+  int dis = 0;
+  for (int w = 0; w < nw; w++) {
+    uint32_t x = bits[w] ^ __funnelshift_r(bits[w + ws], bits[w + ws + 1], sh);
+    int rem = n - 32 * w;
+    if (rem < 32) x &= (1u << rem) - 1u;
+    dis += __popc(x);
+  }
+  return n - 2 * dis;
+}
+
+// C_{lambda g} for g = 1..G; lanes split the lags.  Writes C16 (zero-padded to kCLen) and returns E on
+// every lane (sum over the tracked lags; for skew inputs the untracked odd lags are zero).
+__device__ inline int build_table(ScanSmem& sm, const Layout& ly) {
+  const int lane = lane_id();
+  int e_part = 0;
+  for (int h = lane; h < kCLen; h += 32) {
+    int g = h + 1;
+    int cval = (g <= ly.G) ? corr_lag(sm.bits, ly.L, ly.lam * g) : 0;
+    sm.C16[h] = (int16_t)cval;
+    e_part += cval * cval;
+  }
+  __syncwarp();
+  return warp_sum_i32(e_part);
+}
+
+// int8 copy of the table; returns true on every lane if all |C| <= 127 (fast path allowed).
+__device__ inline bool pack_c8(ScanSmem& sm) {
+  const int lane = lane_id();
+  bool ok = true;
+  for (int h = lane; h < kCLen; h += 32) {
+    int v = sm.C16[h];
+    ok &= (v >= -127 && v <= 127);
+    sm.C8[h] = (int8_t)max(-127, min(127, v));
+  }
+  __syncwarp();
+  return __all_sync(kFull, ok);
+}
+
+__device__ inline int table_sum(const ScanSmem& sm) {
+  int s = 0;
+  for (int h = lane_id(); h < kCLen; h += 32) s += sm.C16[h];
+  return warp_sum_i32(s);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Hot loop: acc[j] = sum_{h < 4 NG} C8[h] * y'_{h+1}(m_j) for the M neighbours of one tile
+// (class `cls`, class indices q0 .. q0+M-1; q0 = 3 mod 4 so every window has a static alignment).
+// ------------------------------------------------------------------------------------------------
+template <int M, bool WIDE>
+__device__ __forceinline__ void scan_tile(const ScanSmem& sm, const Layout& ly, int cls, int q0, int (&acc)[M]) {
+  constexpr int K = M / 4 + 1;
+  const uint32_t* Fw = sm.fwd + cls_words(cls);
+  const uint32_t* Bw = sm.bwd + cls_words(cls);
+  const int tf0 = (q0 + 1) >> 2;
+  const int tb0 = ((ly.Qr - q0 + 1) >> 2) - M / 4;
+  uint32_t wf[K], wb[K];
+#pragma unroll
+  for (int a = 0; a < K; a++) {
+    wf[a] = Fw[tf0 + a];
+    wb[a] = Bw[tb0 + a];
+  }
+#pragma unroll
+  for (int j = 0; j < M; j++) acc[j] = 0;
+  const uint32_t* C8w = reinterpret_cast<const uint32_t*>(sm.C8);
+  const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16);
+  const int NG = ly.NG;
+  for (int u0 = 0; u0 < NG; u0 += K) {
+#pragma unroll
+    for (int du = 0; du < K; du++) {
+      const int u = u0 + du;
+      if (u < NG) {
+        uint32_t c4 = 0, clo = 0, chi = 0;
+        if (WIDE) {
+          clo = C16w[2 * u];
+          chi = C16w[2 * u + 1];
+        } else {
+          c4 = C8w[u];
+        }
+#pragma unroll
+        for (int j = 0; j < M; j++) {
+          const int af = (du + (j >> 2)) % K;
+          const int rf = j & 3;
+          const uint32_t f = rf ? __funnelshift_r(wf[af], wf[(af + 1) % K], 8 * rf) : wf[af];
+          const int ab = (du + M / 4 - ((j + 3) >> 2)) % K;
+          const int rb = (4 - (j & 3)) & 3;
+          const uint32_t b = rb ? __funnelshift_r(wb[ab], wb[(ab + 1) % K], 8 * rb) : wb[ab];
+          const int y4 = (int)(f + b);
+          if (WIDE) {
+            acc[j] = __dp2a_lo((int)clo, y4, acc[j]);
+            acc[j] = __dp2a_hi((int)chi, y4, acc[j]);
+          } else {
+            acc[j] = __dp4a(y4, (int)c4, acc[j]);
+          }
+        }
+        wf[du % K] = Fw[tf0 + u + K];
+        wb[du % K] = Bw[tb0 + u + K];
+      }
+    }
+  }
+}
+
+// Per-neighbour constants of slot (cls, q): position, whether it is a neighbour, pair flag, counts.
+struct SlotInfo {
+  int m;       // position (1-based)
+  int active;  // inside the free range
+  int pair;    // skew pair flip (m != centre)
+  int nf, nb;  // valid forward / backward lags
+  int gd;      // lag index of the excluded pair (m, m') when pair, else 0
+};
+
+__device__ __forceinline__ SlotInfo slot_info(const Layout& ly, int cls, int q) {
+  SlotInfo si;
+  si.m = q_pos(ly, cls, q);
+  si.active = (si.m >= ly.p + 1 && si.m <= ly.mlast) ? 1 : 0;
+  si.pair = (ly.skew && si.m != ly.c) ? 1 : 0;
+  si.nf = (ly.L - si.m) / ly.lam;
+  si.nb = (si.m - 1) / ly.lam;
+  si.gd = si.pair ? (ly.L + 1 - 2 * si.m) / 2 : 0;
+  return si;
+}
+
+// P_m from scratch: sum over g <= min(nf, nb), g != gd, of s_{m - lambda g} s_{m + lambda g}.
+__device__ __forceinline__ int p_from_scratch(const ScanSmem& sm, const Layout& ly, int cls, int q, const SlotInfo& si) {
+  if (!si.active) return 0;
+  int gmax = min(si.nf, si.nb);
+  int P = 0;
+  for (int g = 1; g <= gmax; g++) {
+    if (g == si.gd) continue;
+    P += (fwd_byte(sm, ly, cls, q + g) - 1) * (bwd_byte(sm, ly, cls, ly.Qr - q + g) - 1);
+  }
+  return P;
+}
+
+// Delta E of slot (cls, q) from its accumulator, the table sum SC and P.
+__device__ __forceinline__ int finish_delta(const ScanSmem& sm, const Layout& ly, int cls, int q, const SlotInfo& si,
+                                            int acc, int SC, int P) {
+  int s_m = fwd_byte(sm, ly, cls, q) - 1;
+  int T = acc - 2 * SC;
+  int alpha = si.pair ? 4 : 2;
+  if (si.pair) {
+    // s_{m'} = (-1)^{c-m} s_m by Eq. (2); remove the product with the mirror from the g = gd term
+    int s_mp = ((ly.c - si.m) & 1) ? -s_m : s_m;
+    T -= (int)sm.C16[si.gd - 1] * s_mp;
+  }
+  int Q = si.nf + si.nb - si.pair + 2 * P;
+  return -2 * alpha * s_m * T + alpha * alpha * Q;
+}
+
+// P maintenance for one slot when the set F = {f0, f1} (f1 = 0 when single) flips; reads pre-flip s.
+__device__ __forceinline__ int p_update(const ScanSmem& sm, const Layout& ly, const SlotInfo& si, int P, int f0,
+                                        int f1) {
+  if (!si.active) return P;
+  int gmax = min(si.nf, si.nb);
+  int fs[2] = {f0, f1};
+#pragma unroll
+  for (int a = 0; a < 2; a++) {
+    int f = fs[a];
+    if (f == 0) continue;
+    int kap = si.m > f ? si.m - f : f - si.m;
+    if (kap == 0 || (kap % ly.lam) != 0) continue;
+    int g = kap / ly.lam;
+    if (g > gmax || g == si.gd) continue;
+    int other = 2 * si.m - f;
+    if (other == f0 || other == f1) continue;
+    P -= 2 * s_at(sm, ly, f) * s_at(sm, ly, other);
+  }
+  return P;
+}
+
+// Table update for flipping neighbour m* (pre-flip s): C_{lambda g} += -alpha s_m* y_g(m*), and the int8
+// copy alongside.  Returns the change of the table sum; *fast receives whether every |C| <= 127.
+__device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bool* fast) {
+  const int cls = pos_cls(ly, mstar), q = pos_q(ly, mstar);
+  const int pair = (ly.skew && mstar != ly.c) ? 1 : 0;
+  const int alpha = pair ? 4 : 2;
+  const int s_m = fwd_byte(sm, ly, cls, q) - 1;
+  const int gd = pair ? (ly.L + 1 - 2 * mstar) / 2 : 0;
+  const int s_mp = pair ? (((ly.c - mstar) & 1) ? -s_m : s_m) : 0;
+  int dsum = 0;
+  bool ok = true;
+  for (int h = lane_id(); h < ly.G; h += 32) {
+    int g = h + 1;
+    int y = (fwd_byte(sm, ly, cls, q + g) - 1) + (bwd_byte(sm, ly, cls, ly.Qr - q + g) - 1);
+    if (g == gd) y -= s_mp;
+    int d = -alpha * s_m * y;
+    int v = sm.C16[h] + d;
+    sm.C16[h] = (int16_t)v;
+    sm.C8[h] = (int8_t)max(-127, min(127, v));
+    ok &= (v >= -127 && v <= 127);
+    dsum += d;
+  }
+  __syncwarp();
+  *fast = __all_sync(kFull, ok);
+  return warp_sum_i32(dsum);
+}
+
+// Negates s_i in the bits and both byte arrays (call from one lane per position, then __syncwarp).
+__device__ __forceinline__ void flip_position(ScanSmem& sm, const Layout& ly, int i) {
+  const int cls = pos_cls(ly, i), q = pos_q(ly, i);
+  uint8_t* F = reinterpret_cast<uint8_t*>(sm.fwd + cls_words(cls));
+  uint8_t* B = reinterpret_cast<uint8_t*>(sm.bwd + cls_words(cls));
+  F[q] = (uint8_t)(2 - F[q]);
+  B[ly.Qr - q] = (uint8_t)(2 - B[ly.Qr - q]);
+  sm.bits[(i - 1) >> 5] ^= 1u << ((i - 1) & 31);
+}
+
+// Copies packed 64-bit words from global memory into the slab bits (zero-padded).
+__device__ inline void load_bits(ScanSmem& sm, const uint64_t* src, int L) {
+  const int W32 = (L + 31) >> 5;
+  for (int w = lane_id(); w < kBitWords; w += 32) {
+    uint32_t v = 0;
+    if (w < W32) {
+      uint64_t x = src[w >> 1];
+      v = (w & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+      int rem = L - 32 * w;
+      if (rem < 32) v &= (1u << rem) - 1u;
+    }
+    sm.bits[w] = v;
+  }
+  __syncwarp();
+}
+
+// Builds a walk start into the bits: s_1..s_p from the prefix, free element j (position p+1+j) is +1
+// iff bit j%64 of output j/64 of stream `key`; skew walks fill the last k by Eq. (2).
+__device__ inline void build_start(ScanSmem& sm, const Layout& ly, const uint64_t* prefix, uint64_t key) {
+  const int lane = lane_id();
+  const int W32 = (ly.L + 31) >> 5;
+  for (int w = 0; w < kBitWords; w++) {
+    int i = 32 * w + lane + 1;
+    int bit = 0;
+    if (i <= ly.L) {
+      int src = i;
+      int neg = 0;
+      if (ly.skew && i > ly.c) {
+        src = 2 * ly.c - i;
+        neg = (i - ly.c) & 1;
+      }
+      int b;
+      if (src <= ly.p) {
+        b = (int)((prefix[(src - 1) >> 6] >> ((src - 1) & 63)) & 1u);
+      } else {
+        int j = src - ly.p - 1;
+        b = (int)((sm64_at(key, (uint64_t)(j >> 6)) >> (j & 63)) & 1u);
+      }
+      bit = b ^ neg;
+    }
+    unsigned word = __ballot_sync(kFull, bit);
+    if (lane == 0) sm.bits[w] = (w < W32) ? word : 0u;
+  }
+  __syncwarp();
+}
+
+// Zobrist fingerprint of the sequence in the bits.
+__device__ inline uint64_t fingerprint(const ScanSmem& sm, int L, uint64_t zkey) {
+  uint64_t h = 0;
+  for (int i = lane_id() + 1; i <= L; i += 32)
+    if (!seq_bit(sm, i)) h ^= zobrist(zkey, i);
+  return warp_xor_u64(h);
+}
+
+}  // namespace labsg

@@ -1,0 +1,40 @@
+// labs_internal.h -- host-side declarations shared by the translation units of liblabs.so.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "labs.h"
+
+struct labs_ctx {
+  int device;
+  int num_sms;
+  size_t smem_optin;
+  // growable device workspace, one region per purpose
+  void* ws[8];
+  size_t ws_bytes[8];
+};
+
+namespace labsg {
+
+enum WsSlot { kWsThreshSamples = 0, kWsThreshHist = 1, kWsWalkCounters = 2, kWsThreshValue = 3, kWsPq0 = 4 };
+
+// Returns a device region of at least `bytes` for `slot`, growing it if needed (not capturable).
+void* ws_get(labs_ctx* ctx, int slot, size_t bytes);
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LABS_OK : LABS_ERR_CUDA; }
+
+// Host launchers (argument validation happens in the C-ABI layer).
+int launch_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out,
+                        cudaStream_t st);
+int launch_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int L, int64_t n, int skew, int p,
+                       int32_t* dE_out, cudaStream_t st);
+int launch_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
+                            int prefix_words, uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out,
+                            int32_t* E_samples, cudaStream_t st);
+int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
+                       labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, cudaStream_t st);
+int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
+                           uint64_t* out_argmin_free, uint64_t* out_argmin_seq, cudaStream_t st);
+
+}  // namespace labsg
