@@ -112,7 +112,7 @@ typedef struct {
   int64_t n_thresh_samples; /* auto threshold: starts sampled (stream (seed, 2, i, 0)), e.g. 10^6 */
   int64_t thresh_rank;      /* auto threshold: 0-based rank of E_thr among the samples, e.g. 999 */
   int32_t E_target;     /* record each walk's first flip reaching E <= E_target; INT32_MIN = off */
-  int32_t tile_m;       /* neighbours per lane tile (4, 8, 12 or 16); 0 = autotuned */
+  int32_t tile_m;       /* neighbours per tile (8, 12 or 16); 0 = autotuned */
   int32_t warps_per_cta;/* walks resident per CTA (1..8); 0 = autotuned */
   int32_t reserved;
   const int32_t* E_thr_dev; /* nullable device int32: when set, the sieve bound is read from it (for

@@ -137,7 +137,7 @@ int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* pr
     return LABS_ERR_INVALID_ARG;
   if (cfg->walk_begin + cfg->n_walks > 0xffffffffLL) return LABS_ERR_INVALID_ARG;  // walk ids are stored as u32
   if (cfg->flip_budget > 0xffffffffLL) return LABS_ERR_INVALID_ARG;               // steps are stored as u32
-  if (cfg->tile_m != 0 && cfg->tile_m != 4 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16)
+  if (cfg->tile_m != 0 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16)
     return LABS_ERR_INVALID_ARG;
   if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
   if (cfg->E_thr_dev && !aligned4(cfg->E_thr_dev)) return LABS_ERR_INVALID_ARG;

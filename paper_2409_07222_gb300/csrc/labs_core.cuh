@@ -36,7 +36,7 @@ constexpr int kMaxL = LABS_MAX_L;
 constexpr int kQOff = 3;             // class index of the first position of a class
 constexpr int kDirBytes = 1216;      // byte-window array per direction (two 608-byte classes when skew)
 constexpr int kClassBytes = 608;
-constexpr int kCLen = 592;           // correlation table slots (>= 4 * NG + 4 for every L <= 576)
+constexpr int kCLen = 608;           // correlation table slots (>= 4 * padded group count, L <= 576)
 constexpr int kBitWords = 20;        // 18 words for 576 bits + 2 zero words for funnel shifts
 constexpr int kMaxR = 32;
 
@@ -89,12 +89,16 @@ __device__ __forceinline__ uint64_t warp_xor_u64(uint64_t v) {
 // Layout of one walk for (L, skew, p, M).  Identical on every lane (pure function of its inputs).
 // ------------------------------------------------------------------------------------------------
 struct Layout {
-  int L, skew, p, lam, G, NG, c, mlast;
+  int L, skew, p, lam, lsh, G, NG, c, mlast;  // lam = 1 << lsh
   int ncls;
   int tile_first[2], ntiles[2];
   int n_tiles;
   int Qr;
-  int M;
+  int M, H;   // neighbours per tile, lag ranges per tile (lanes sharing a tile)
+  int R;      // ring length M/4 + 1; group ranges are multiples of R
+  int NGh;    // groups of lag range 0 (range 1, when H = 2, is [NGh, NGend))
+  int NGend;  // padded end of the groups (C = 0 beyond NG)
+  int n_tasks;
 };
 
 // word offset of class `cls` inside the fwd/bwd arrays (class 1 exists only for skew walks)
@@ -109,13 +113,16 @@ __host__ __device__ __forceinline__ int q_pos(const Layout& ly, int cls, int q) 
   return ly.skew ? 2 * (q - kQOff) + (cls ? 1 : 2) : q - kQOff + 1;
 }
 
-__host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, int M) {
+__host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, int M, int H = 1) {
   ly.L = L;
   ly.skew = skew;
   ly.p = p;
   ly.M = M;
+  ly.H = H;
+  ly.R = M / 4 + 1;
   ly.lam = skew ? 2 : 1;
-  ly.G = (L - 1) / ly.lam;
+  ly.lsh = skew ? 1 : 0;
+  ly.G = (L - 1) >> ly.lsh;
   ly.NG = (ly.G + 3) / 4;
   ly.c = (L + 1) / 2;
   ly.mlast = skew ? ly.c : L;
@@ -142,11 +149,22 @@ __host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, 
     if (end > qmax_end) qmax_end = end;
   }
   ly.Qr = qmax_end + ((2 - (qmax_end & 3)) & 3);
+  ly.n_tasks = ly.n_tiles * H;
+  if (H == 1) {
+    ly.NGh = ((ly.NG + ly.R - 1) / ly.R) * ly.R;
+    ly.NGend = ly.NGh;
+  } else {
+    int half = (ly.NG + 1) / 2;
+    ly.NGh = ((half + ly.R - 1) / ly.R) * ly.R;
+    int rest = ly.NG - ly.NGh;
+    ly.NGend = ly.NGh + (rest > 0 ? ((rest + ly.R - 1) / ly.R) * ly.R : 0);
+  }
   // byte windows must stay inside a class array (see the bound derivation in the design notes)
   int cap = skew ? kClassBytes : kDirBytes;
-  int need_f = qmax_end + 4 * ly.NG + 8;
-  int need_b = ly.Qr + 4 * ly.NG + 8;
-  return need_f < cap && need_b < cap && 4 * ly.NG + 4 <= kCLen && L >= 2 && L <= kMaxL;
+  int need_f = qmax_end + 4 * ly.NGend + 8;
+  int need_b = ly.Qr + 4 * ly.NGend + 8;
+  return (H == 1 || H == 2) && M % 4 == 0 && need_f < cap && need_b < cap && 4 * ly.NGend <= kCLen && L >= 2 &&
+         L <= kMaxL;
 }
 
 // Tile tau -> (class, first class index).
@@ -260,60 +278,84 @@ __device__ inline int table_sum(const ScanSmem& sm) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Hot loop: acc[j] = sum_{h < 4 NG} C8[h] * y'_{h+1}(m_j) for the M neighbours of one tile
-// (class `cls`, class indices q0 .. q0+M-1; q0 = 3 mod 4 so every window has a static alignment).
+// Hot loop: acc[j] += sum_{u in [u_begin, u_end)} sum_{e<4} C8[4u+e] * y'_{4u+e+1}(m_j) for the M
+// neighbours of one tile (class `cls`, class indices q0 .. q0+M-1; q0 = 3 mod 4 so every window has a
+// static alignment).  u_end - u_begin must be a multiple of R = M/4 + 1.
 // ------------------------------------------------------------------------------------------------
 template <int M, bool WIDE>
-__device__ __forceinline__ void scan_tile(const ScanSmem& sm, const Layout& ly, int cls, int q0, int (&acc)[M]) {
-  constexpr int K = M / 4 + 1;
+__device__ __forceinline__ void scan_range(const ScanSmem& sm, const Layout& ly, int cls, int q0, int u_begin,
+                                           int u_end, int (&acc)[M]) {
+  // Word streams: plain words P[t] (ring of R) and, for byte offsets r = 1..3, the realigned words
+  // S_r[t] = bytes 4t+r .. 4t+r+3 (rings of R).  Each new word costs one load and three funnel
+  // shifts per direction, shared by every neighbour of the tile.
+  constexpr int K4 = M / 4;
+  constexpr int R = K4 + 1;
   const uint32_t* Fw = sm.fwd + cls_words(cls);
   const uint32_t* Bw = sm.bwd + cls_words(cls);
-  const int tf0 = (q0 + 1) >> 2;
-  const int tb0 = ((ly.Qr - q0 + 1) >> 2) - M / 4;
-  uint32_t wf[K], wb[K];
+  const int tf0 = ((q0 + 1) >> 2) + u_begin;
+  const int tb0 = ((ly.Qr - q0 + 1) >> 2) - K4 + u_begin;
+  uint32_t pf[R], pb[R], sf[3][R], sb[3][R];
 #pragma unroll
-  for (int a = 0; a < K; a++) {
-    wf[a] = Fw[tf0 + a];
-    wb[a] = Bw[tb0 + a];
+  for (int a = 0; a < R; a++) {
+    pf[a] = Fw[tf0 + a];
+    pb[a] = Bw[tb0 + a];
   }
 #pragma unroll
-  for (int j = 0; j < M; j++) acc[j] = 0;
-  const uint32_t* C8w = reinterpret_cast<const uint32_t*>(sm.C8);
-  const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16);
-  const int NG = ly.NG;
-  for (int u0 = 0; u0 < NG; u0 += K) {
+  for (int a = 0; a < K4; a++)
 #pragma unroll
-    for (int du = 0; du < K; du++) {
+    for (int r = 1; r < 4; r++) {
+      sf[r - 1][a] = __funnelshift_r(pf[a], pf[a + 1], 8 * r);
+      sb[r - 1][a] = __funnelshift_r(pb[a], pb[a + 1], 8 * r);
+    }
+  const uint32_t* C8w = reinterpret_cast<const uint32_t*>(sm.C8) + u_begin;
+  const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16) + 2 * u_begin;
+  const int n = u_end - u_begin;
+  for (int u0 = 0; u0 < n; u0 += R) {
+#pragma unroll
+    for (int du = 0; du < R; du++) {
       const int u = u0 + du;
-      if (u < NG) {
-        uint32_t c4 = 0, clo = 0, chi = 0;
-        if (WIDE) {
-          clo = C16w[2 * u];
-          chi = C16w[2 * u + 1];
-        } else {
-          c4 = C8w[u];
-        }
+      uint32_t c4 = 0, clo = 0, chi = 0;
+      if (WIDE) {
+        clo = C16w[2 * u];
+        chi = C16w[2 * u + 1];
+      } else {
+        c4 = C8w[u];
+      }
 #pragma unroll
-        for (int j = 0; j < M; j++) {
-          const int af = (du + (j >> 2)) % K;
-          const int rf = j & 3;
-          const uint32_t f = rf ? __funnelshift_r(wf[af], wf[(af + 1) % K], 8 * rf) : wf[af];
-          const int ab = (du + M / 4 - ((j + 3) >> 2)) % K;
-          const int rb = (4 - (j & 3)) & 3;
-          const uint32_t b = rb ? __funnelshift_r(wb[ab], wb[(ab + 1) % K], 8 * rb) : wb[ab];
-          const int y4 = (int)(f + b);
-          if (WIDE) {
-            acc[j] = __dp2a_lo((int)clo, y4, acc[j]);
-            acc[j] = __dp2a_hi((int)chi, y4, acc[j]);
-          } else {
-            acc[j] = __dp4a(y4, (int)c4, acc[j]);
-          }
+      for (int j = 0; j < M; j++) {
+        const int af = (du + (j >> 2)) % R;
+        const int rf = j & 3;
+        const uint32_t f = rf ? sf[rf - 1][af] : pf[af];
+        const int ab = (du + K4 - ((j + 3) >> 2)) % R;
+        const int rb = (4 - (j & 3)) & 3;
+        const uint32_t b = rb ? sb[rb - 1][ab] : pb[ab];
+        const int y4 = (int)(f + b);
+        if (WIDE) {
+          acc[j] = __dp2a_lo((int)clo, y4, acc[j]);
+          acc[j] = __dp2a_hi((int)chi, y4, acc[j]);
+        } else {
+          acc[j] = __dp4a(y4, (int)c4, acc[j]);
         }
-        wf[du % K] = Fw[tf0 + u + K];
-        wb[du % K] = Bw[tb0 + u + K];
+      }
+      // advance: word u + R enters slot du; S_r[u + K4] goes to slot (du + K4) % R
+      pf[du] = Fw[tf0 + u + R];
+      pb[du] = Bw[tb0 + u + R];
+      const int sl = (du + K4) % R;
+#pragma unroll
+      for (int r = 1; r < 4; r++) {
+        sf[r - 1][sl] = __funnelshift_r(pf[sl], pf[du], 8 * r);
+        sb[r - 1][sl] = __funnelshift_r(pb[sl], pb[du], 8 * r);
       }
     }
   }
+}
+
+// The whole lag range of one tile (single lane per tile).
+template <int M, bool WIDE>
+__device__ __forceinline__ void scan_tile(const ScanSmem& sm, const Layout& ly, int cls, int q0, int (&acc)[M]) {
+#pragma unroll
+  for (int j = 0; j < M; j++) acc[j] = 0;
+  scan_range<M, WIDE>(sm, ly, cls, q0, 0, ly.NGh, acc);
 }
 
 // Per-neighbour constants of slot (cls, q): position, whether it is a neighbour, pair flag, counts.
@@ -330,9 +372,9 @@ __device__ __forceinline__ SlotInfo slot_info(const Layout& ly, int cls, int q) 
   si.m = q_pos(ly, cls, q);
   si.active = (si.m >= ly.p + 1 && si.m <= ly.mlast) ? 1 : 0;
   si.pair = (ly.skew && si.m != ly.c) ? 1 : 0;
-  si.nf = (ly.L - si.m) / ly.lam;
-  si.nb = (si.m - 1) / ly.lam;
-  si.gd = si.pair ? (ly.L + 1 - 2 * si.m) / 2 : 0;
+  si.nf = (ly.L - si.m) >> ly.lsh;
+  si.nb = (si.m - 1) >> ly.lsh;
+  si.gd = si.pair ? (ly.L + 1 - 2 * si.m) >> 1 : 0;
   return si;
 }
 
@@ -364,22 +406,26 @@ __device__ __forceinline__ int finish_delta(const ScanSmem& sm, const Layout& ly
 }
 
 // P maintenance for one slot when the set F = {f0, f1} (f1 = 0 when single) flips; reads pre-flip s.
+// s0, s1 are the pre-flip values at f0, f1.  The pair (m - kappa, m + kappa) touches F only when
+// kappa = |m - f| is a multiple of lambda, and changes sign unless both ends are in F.
 __device__ __forceinline__ int p_update(const ScanSmem& sm, const Layout& ly, const SlotInfo& si, int P, int f0,
-                                        int f1) {
+                                        int s0, int f1, int s1) {
   if (!si.active) return P;
-  int gmax = min(si.nf, si.nb);
-  int fs[2] = {f0, f1};
+  const int gmax = min(si.nf, si.nb);
+  const int lmask = ly.lam - 1;
 #pragma unroll
   for (int a = 0; a < 2; a++) {
-    int f = fs[a];
+    const int f = a ? f1 : f0;
+    const int sf = a ? s1 : s0;
     if (f == 0) continue;
-    int kap = si.m > f ? si.m - f : f - si.m;
-    if (kap == 0 || (kap % ly.lam) != 0) continue;
-    int g = kap / ly.lam;
+    const int d = si.m - f;
+    const int kap = d < 0 ? -d : d;
+    if (kap == 0 || (kap & lmask)) continue;
+    const int g = kap >> ly.lsh;
     if (g > gmax || g == si.gd) continue;
-    int other = 2 * si.m - f;
+    const int other = si.m + d;
     if (other == f0 || other == f1) continue;
-    P -= 2 * s_at(sm, ly, f) * s_at(sm, ly, other);
+    P -= 2 * sf * s_at(sm, ly, other);
   }
   return P;
 }
@@ -391,7 +437,7 @@ __device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bo
   const int pair = (ly.skew && mstar != ly.c) ? 1 : 0;
   const int alpha = pair ? 4 : 2;
   const int s_m = fwd_byte(sm, ly, cls, q) - 1;
-  const int gd = pair ? (ly.L + 1 - 2 * mstar) / 2 : 0;
+  const int gd = pair ? (ly.L + 1 - 2 * mstar) >> 1 : 0;
   const int s_mp = pair ? (((ly.c - mstar) & 1) ? -s_m : s_m) : 0;
   int dsum = 0;
   bool ok = true;
@@ -411,14 +457,15 @@ __device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bo
   return warp_sum_i32(dsum);
 }
 
-// Negates s_i in the bits and both byte arrays (call from one lane per position, then __syncwarp).
+// Negates s_i in the bits and both byte arrays (one lane per position, distinct positions may run
+// on different lanes at once; then __syncwarp).
 __device__ __forceinline__ void flip_position(ScanSmem& sm, const Layout& ly, int i) {
   const int cls = pos_cls(ly, i), q = pos_q(ly, i);
   uint8_t* F = reinterpret_cast<uint8_t*>(sm.fwd + cls_words(cls));
   uint8_t* B = reinterpret_cast<uint8_t*>(sm.bwd + cls_words(cls));
   F[q] = (uint8_t)(2 - F[q]);
   B[ly.Qr - q] = (uint8_t)(2 - B[ly.Qr - q]);
-  sm.bits[(i - 1) >> 5] ^= 1u << ((i - 1) & 31);
+  atomicXor(&sm.bits[(i - 1) >> 5], 1u << ((i - 1) & 31));
 }
 
 // Copies packed 64-bit words from global memory into the slab bits (zero-padded).

@@ -25,6 +25,7 @@ struct WalkSmem {
 };
 
 struct WalkParams {
+  Layout ly;  // computed on the host; read from the kernel's parameter space
   int L, skew, p, T_i, R, bloom_log2, bloom_k, prefix_words, n_prefix, M;
   int64_t n_walks, walk_begin, flip_budget;
   uint64_t seed;
@@ -67,67 +68,91 @@ __device__ __forceinline__ bool key_less(int Ea, uint64_t fa, int Eb, uint64_t f
   return Ea < Eb || (Ea == Eb && fa < fb);
 }
 
-// Per-slot state lives in shared memory, lane-major ([slot][lane], conflict-free): packed slot info,
-// P_m and the latest Delta E.  Keeping it out of registers leaves the scan its registers.
-template <int S>
-struct SlotSmem {
-  uint32_t info[S][32];  // m | nf << 10 | nb << 20 | active << 30 | pair << 31
-  int pm[S][32];
-  int de[S][32];
+// Per-slot constants derived from the position m: alpha, the excluded lag gd, the sign relation
+// s_{m'} = sigma s_m (Eq. 2) and K0 = alpha^2 (n_f + n_b - pair).
+struct SlotConst {
+  int alpha, gd, sigma, K0, gmax;
 };
 
-__device__ __forceinline__ uint32_t pack_info(const SlotInfo& si) {
-  return (uint32_t)si.m | ((uint32_t)si.nf << 10) | ((uint32_t)si.nb << 20) | ((uint32_t)si.active << 30) |
-         ((uint32_t)si.pair << 31);
+// Closed forms: skew walks (L = 2c - 1, m <= c): n_f + n_b = G - 1 + (m & 1), n_b <= n_f, the excluded
+// lag of the pair (m, m') is g = c - m and s_{m'} = (-1)^{c-m} s_m (Eq. 2).  Unrestricted walks:
+// n_f + n_b = L - 1.
+__device__ __forceinline__ SlotConst slot_const(const Layout& ly, int m) {
+  SlotConst k;
+  if (ly.skew) {
+    const int pair = m != ly.c;
+    k.alpha = pair ? 4 : 2;
+    k.gd = ly.c - m;
+    k.sigma = (k.gd & 1) ? -1 : 1;
+    k.K0 = k.alpha * k.alpha * (ly.G - 1 + (m & 1) - pair);
+    k.gmax = (m - 1) >> 1;
+  } else {
+    k.alpha = 2;
+    k.gd = 0;
+    k.sigma = 1;
+    k.K0 = 4 * (ly.L - 1);
+    k.gmax = min(ly.L - m, m - 1);
+  }
+  return k;
 }
 
-__device__ __forceinline__ SlotInfo unpack_info(const Layout& ly, uint32_t v) {
-  SlotInfo si;
-  si.m = (int)(v & 1023u);
-  si.nf = (int)((v >> 10) & 1023u);
-  si.nb = (int)((v >> 20) & 1023u);
-  si.active = (int)((v >> 30) & 1u);
-  si.pair = (int)(v >> 31);
-  si.gd = si.pair ? (ly.L + 1 - 2 * si.m) / 2 : 0;
-  return si;
+// P bookkeeping of one slot (class index q) when position f (class cf, class index qf, pre-flip value
+// sf) flips: the product s_{m - lambda g} s_{m + lambda g} with g = |q - qf| loses its sign unless g is
+// outside 1..gmax, is the excluded pair lag, or the product's other end flips too (the skew centre
+// when a pair flips).  The other end has class index 2q - qf.
+__device__ __forceinline__ int p_step(const ScanSmem& sm, int cls, int q, const SlotConst& k, int P, int cf, int qf,
+                                      int sf) {
+  const int d = q - qf;
+  const int g = d < 0 ? -d : d;
+  if (cls == cf && (unsigned)(g - 1) < (unsigned)k.gmax && g != k.gd) {
+    const uint8_t* F = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(cls));
+    P -= 2 * sf * ((int)F[q + d] - 1);
+  }
+  return P;
 }
 
-template <int M, int NP>
+template <int M, int H, int NP>
 __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
-  constexpr int S = M * NP;
+  constexpr int MH = M / H;   // slots owned by a lane per pass
+  constexpr int S = NP * MH;  // slots owned by a lane
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   WalkSmem& ws = reinterpret_cast<WalkSmem*>(smem_raw)[wid];
-  SlotSmem<S>& ss = reinterpret_cast<SlotSmem<S>*>(smem_raw + sizeof(WalkSmem) * (blockDim.x >> 5))[wid];
+  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + sizeof(WalkSmem) * nwarps);
   ScanSmem& sm = ws.s;
   const int lane = lane_id();
-  Layout ly;
-  make_layout(ly, P.L, P.skew, P.p, M);
+  const Layout& ly = P.ly;
   const uint64_t zkey = stream_key(0, kPurposeZobrist, (uint64_t)P.L, 0);
   const int32_t E_thr = P.E_thr_ptr ? *P.E_thr_ptr : P.E_thr_value;
   const uint32_t bmask = (1u << P.bloom_log2) - 1u;
   const int bwords = 1 << (P.bloom_log2 - 5);
   const int W = (P.L + 63) >> 6;
   const int R = P.R;
+  // Zobrist keys of this length, shared by the block (index i-1 for position i)
+  for (int i = threadIdx.x; i < P.L; i += blockDim.x) ztab[i] = zobrist(zkey, i + 1);
+  __syncthreads();
 
-  // this lane's tiles (one per pass) and slot info
-  int tcls[NP], tq0[NP];
+  // this lane's task per pass: tile (class, q0) and lag range h; its slots are tile positions
+  // h*MH .. h*MH+MH-1 (after the partial sums of the H lanes of a tile are combined)
+  int tcls[NP], tq0[NP], th[NP];
   bool thas[NP];
+  int slot_m[S];  // position of each owned slot, 0 if none
 #pragma unroll
   for (int ps = 0; ps < NP; ps++) {
-    int tau = ps * 32 + lane;
-    thas[ps] = tau < ly.n_tiles;
+    const int task = ps * 32 + lane;
+    thas[ps] = task < ly.n_tasks;
+    th[ps] = H == 2 ? (task & 1) : 0;
     tcls[ps] = 0;
     tq0[ps] = 0;
-    if (thas[ps]) tile_of(ly, tau, tcls[ps], tq0[ps]);
+    const int tile = H == 2 ? (task >> 1) : task;
+    if (tile < ly.n_tiles) tile_of(ly, tile, tcls[ps], tq0[ps]);
 #pragma unroll
-    for (int j = 0; j < M; j++) {
-      SlotInfo si = slot_info(ly, tcls[ps], tq0[ps] + j);
-      if (!thas[ps]) si.active = 0;
-      ss.info[ps * M + j][lane] = pack_info(si);
+    for (int k = 0; k < MH; k++) {
+      const int m = q_pos(ly, tcls[ps], tq0[ps] + th[ps] * MH + k);
+      slot_m[ps * MH + k] = (thas[ps] && m >= ly.p + 1 && m <= ly.mlast) ? m : 0;
     }
   }
-  __syncwarp();
 
   long long agg_flips = 0, agg_segs = 0, agg_skips = 0, agg_dead = 0;
   int agg_best = INT32_MAX;
@@ -157,10 +182,15 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
     uint64_t wfp = ~0ull;
     int wlane = 0;
 
-    long long flips = 0, segs = 0, skips = 0, dead = 0, first_hit = -1;
+    // flip_budget < 2^32 is checked by the host, so the per-walk counters fit 32 bits (skips: 64)
+    unsigned flips = 0, segs = 0, dead = 0;
+    long long skips = 0;
+    int first_hit = -1;
     int bestE = INT32_MAX;
+    int slot_P[S], slot_ms[S];  // P_m and s_m * m
 
-    while (flips < P.flip_budget) {
+    const unsigned budget = (unsigned)P.flip_budget;
+    while (flips < budget) {
       for (int t = lane; t < bwords; t += 32) ws.bloom[t] = 0u;
       build_start(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
       segs++;
@@ -171,42 +201,63 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
       bool fast = pack_c8(sm);
       build_bytes(sm, ly);
 #pragma unroll
-      for (int ps = 0; ps < NP; ps++)
-#pragma unroll
-        for (int j = 0; j < M; j++) {
-          SlotInfo si = unpack_info(ly, ss.info[ps * M + j][lane]);
-          ss.pm[ps * M + j][lane] = p_from_scratch(sm, ly, tcls[ps], tq0[ps] + j, si);
+      for (int t = 0; t < S; t++) {
+        slot_P[t] = 0;
+        const int m = slot_m[t];
+        slot_ms[t] = m;
+        if (m) {
+          SlotInfo si = slot_info(ly, pos_cls(ly, m), pos_q(ly, m));
+          slot_P[t] = p_from_scratch(sm, ly, pos_cls(ly, m), pos_q(ly, m), si);
+          slot_ms[t] = s_at(sm, ly, m) * m;
         }
+      }
 
       int it = 0;
-      while (it < P.T_i && flips < P.flip_budget) {
+      int mprev = 0;  // free position flipped by the previous move of this segment
+      while (it < P.T_i && flips < budget) {
         it++;
         // ---- scan; each lane keeps its best (Delta E, m)
         int bd = INT32_MAX, bm = INT32_MAX;
+        int dprev = INT32_MAX;  // this lane's Delta E of the move back (only its owner sets it)
+        int slot_d[S];
 #pragma unroll
         for (int ps = 0; ps < NP; ps++) {
+          int acc[M];
+#pragma unroll
+          for (int j = 0; j < M; j++) acc[j] = 0;
           if (thas[ps]) {
-            int acc[M];
+            const int u_begin = th[ps] ? ly.NGh : 0;
+            const int u_end = th[ps] ? ly.NGend : ly.NGh;
             if (fast)
-              scan_tile<M, false>(sm, ly, tcls[ps], tq0[ps], acc);
+              scan_range<M, false>(sm, ly, tcls[ps], tq0[ps], u_begin, u_end, acc);
             else
-              scan_tile<M, true>(sm, ly, tcls[ps], tq0[ps], acc);
+              scan_range<M, true>(sm, ly, tcls[ps], tq0[ps], u_begin, u_end, acc);
+          }
+          if (H == 2) {
 #pragma unroll
-            for (int j = 0; j < M; j++) {
-              SlotInfo si = unpack_info(ly, ss.info[ps * M + j][lane]);
-              int d = INT32_MAX;
-              if (si.active) {
-                d = finish_delta(sm, ly, tcls[ps], tq0[ps] + j, si, acc[j], SC, ss.pm[ps * M + j][lane]);
-                if (d < bd || (d == bd && si.m < bm)) {
-                  bd = d;
-                  bm = si.m;
-                }
+            for (int j = 0; j < M; j++) acc[j] += __shfl_xor_sync(kFull, acc[j], 1);
+          }
+#pragma unroll
+          for (int k = 0; k < MH; k++) {
+            const int t = ps * MH + k;
+            const int ms = slot_ms[t];
+            const int m = ms < 0 ? -ms : ms;
+            const int a = (H == 2 && th[ps]) ? acc[MH + k] : acc[k];
+            int d = INT32_MAX;
+            if (m) {
+              const SlotConst kc = slot_const(ly, m);
+              const int s_m = ms < 0 ? -1 : 1;
+              d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * slot_P[t];
+              if (kc.alpha == 4) d += 8 * kc.sigma * (int)sm.C16[kc.gd - 1];
+              if (m == mprev) {
+                dprev = d;  // the state just left: certainly in the Bloom filter
+                d = INT32_MAX;
+              } else if (d < bd || (d == bd && m < bm)) {
+                bd = d;
+                bm = m;
               }
-              ss.de[ps * M + j][lane] = d;
             }
-          } else {
-#pragma unroll
-            for (int j = 0; j < M; j++) ss.de[ps * M + j][lane] = INT32_MAX;  // read by the exclusion rescan
+            slot_d[t] = d;
           }
         }
         // ---- select: smallest (Delta E, m) whose neighbour is not in the Bloom filter
@@ -216,8 +267,8 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
           int dmin = warp_min_i32(bd);
           if (dmin == INT32_MAX) break;
           int mm = (int)warp_min_u32(bd == dmin ? (unsigned)bm : 0xffffffffu);
-          uint64_t cand = fp ^ zobrist(zkey, mm);
-          if (ly.skew && mm != ly.c) cand ^= zobrist(zkey, ly.L + 1 - mm);
+          uint64_t cand = fp ^ ztab[mm - 1];
+          if (ly.skew && mm != ly.c) cand ^= ztab[ly.L - mm];
           if (!bloom_test(ws.bloom, cand, P.bloom_k, bmask)) {
             mstar = mm;
             dstar = dmin;
@@ -226,19 +277,15 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
           }
           skips++;
           if (bd == dmin && bm == mm) {
-            // the owner lane drops that neighbour and recomputes its best from the stored deltas
+            // the owner lane's next best: smallest key ranked after (dmin, mm); keys ranked ahead were
+            // excluded earlier in this step
             bd = INT32_MAX;
             int nbm = INT32_MAX;
 #pragma unroll
-            for (int s = 0; s < S; s++) {
-              int d = ss.de[s][lane];
-              int m = (int)(ss.info[s][lane] & 1023u);
+            for (int t = 0; t < S; t++) {
+              const int d = slot_d[t], m = slot_ms[t] < 0 ? -slot_ms[t] : slot_ms[t];
               if (d == INT32_MAX) continue;
-              if (m == mm) {
-                ss.de[s][lane] = INT32_MAX;
-                continue;
-              }
-              if (d < dmin || (d == dmin && m <= mm)) continue;  // already ranked ahead, hence excluded
+              if (d < dmin || (d == dmin && m <= mm)) continue;
               if (d < bd || (d == bd && m < nbm)) {
                 bd = d;
                 nbm = m;
@@ -247,29 +294,43 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
             bm = nbm;
           }
         }
+        // the move back ranked ahead of the chosen move: count it as a Bloom skip
+        if (__any_sync(kFull, dprev != INT32_MAX && (mstar < 0 || dprev < dstar || (dprev == dstar && mprev < mstar))))
+          skips++;
         if (mstar < 0) {
           dead++;
           break;
         }
         // ---- apply
         const int f1 = (ly.skew && mstar != ly.c) ? ly.L + 1 - mstar : 0;
+        const int c0 = pos_cls(ly, mstar), q0f = pos_q(ly, mstar);
+        const int s0 = s_at(sm, ly, mstar);
+        const int q1f = f1 ? pos_q(ly, f1) : 0;  // the mirror has the class of m*
+        const int s1 = f1 ? s_at(sm, ly, f1) : 0;
 #pragma unroll
-        for (int s = 0; s < S; s++) {
-          SlotInfo si = unpack_info(ly, ss.info[s][lane]);
-          ss.pm[s][lane] = p_update(sm, ly, si, ss.pm[s][lane], mstar, f1);
+        for (int t = 0; t < S; t++) {
+          const int m = slot_ms[t] < 0 ? -slot_ms[t] : slot_ms[t];
+          if (m) {
+            const SlotConst kc = slot_const(ly, m);
+            const int cls = pos_cls(ly, m), q = pos_q(ly, m);
+            if (!(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
+              slot_P[t] = p_step(sm, cls, q, kc, slot_P[t], c0, q0f, s0);
+              if (f1) slot_P[t] = p_step(sm, cls, q, kc, slot_P[t], c0, q1f, s1);
+            }
+            if (m == mstar) slot_ms[t] = -slot_ms[t];
+          }
         }
+        mprev = mstar;
         SC += table_update(sm, ly, mstar, &fast);
-        if (lane == 0) {
-          flip_position(sm, ly, mstar);
-          if (f1) flip_position(sm, ly, f1);
-        }
+        if (lane == 0) flip_position(sm, ly, mstar);
+        if (lane == 1 && f1) flip_position(sm, ly, f1);
         __syncwarp();
         E += dstar;
         fp = nfp;
         bloom_add(ws.bloom, fp, P.bloom_k, bmask);
         flips++;
         if (E < bestE) bestE = E;
-        if (first_hit < 0 && E <= P.E_target) first_hit = flips;
+        if (first_hit < 0 && E <= P.E_target) first_hit = (int)flips;
         // ---- sieve
         if (E <= E_thr && key_less(E, fp, wE, wfp)) {
           bool dup = __any_sync(kFull, lane < R && cE != INT32_MAX && cfp == fp);
@@ -318,10 +379,10 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
     __syncwarp();
     if (P.walk_stats && lane == 0) {
       int64_t* st = P.walk_stats + (int64_t)wrel * 6;
-      st[0] = flips;
-      st[1] = segs;
+      st[0] = (int64_t)flips;
+      st[1] = (int64_t)segs;
       st[2] = skips;
-      st[3] = dead;
+      st[3] = (int64_t)dead;
       st[4] = bestE;
       st[5] = first_hit;
     }
@@ -435,10 +496,10 @@ __global__ void finish_select_kernel(const unsigned* __restrict__ hist2, long lo
   }
 }
 
-template <int M, int NP>
+template <int M, int H, int NP>
 int launch_walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st) {
-  size_t smem = (sizeof(WalkSmem) + sizeof(SlotSmem<M * NP>)) * (size_t)warps;
-  auto kern = walk_kernel<M, NP>;
+  size_t smem = sizeof(WalkSmem) * (size_t)warps + sizeof(uint64_t) * LABS_MAX_L;
+  auto kern = walk_kernel<M, H, NP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return LABS_ERR_CUDA;
   int per_sm = 0;
@@ -476,26 +537,32 @@ int launch_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_
   return cuda_status(cudaGetLastError());
 }
 
-// Picks the tile size M and pass count NP: least per-lane scan work NP * M, ties to the larger tile
-// (fewer window loads per multiply-add).  NP <= 3 (<= 2 for M = 16).
-static void choose_tiles(int L, int skew, int p, int req_m, int* M, int* NP) {
-  const int cand[4] = {4, 8, 12, 16};
-  int bestM = 0, bestNP = 0;
-  for (int a = 0; a < 4; a++) {
-    int m = cand[a];
-    if (req_m && m != req_m) continue;
+// Walk-kernel variants: (tile M, lag ranges H, passes NP).  The chooser takes the variant with the
+// least per-lane scan work NP * M / H (ties: more lanes per tile, then the larger tile).
+struct Variant {
+  int M, H, NP;
+};
+static const Variant kVariants[] = {{8, 1, 1},  {8, 1, 2},  {8, 1, 3},  {12, 1, 1}, {12, 1, 2}, {12, 2, 1},
+                                    {12, 2, 2}, {16, 1, 1}, {16, 1, 2}, {16, 2, 1}, {16, 2, 2}, {16, 2, 3}};
+
+static bool choose_variant(int L, int skew, int p, int req_m, Variant* out) {
+  bool found = false;
+  Variant best{0, 0, 0};
+  for (const Variant& v : kVariants) {
+    if (req_m && v.M != req_m) continue;
     Layout ly;
-    if (!make_layout(ly, L, skew, p, m)) continue;
-    int np = (ly.n_tiles + 31) / 32;
+    if (!make_layout(ly, L, skew, p, v.M, v.H)) continue;
+    int np = (ly.n_tasks + 31) / 32;
     if (np < 1) np = 1;
-    if (np > (m == 16 ? 2 : 3)) continue;
-    if (bestM == 0 || np * m < bestNP * bestM || (np * m == bestNP * bestM && m > bestM)) {
-      bestM = m;
-      bestNP = np;
+    if (np != v.NP) continue;
+    int cost = v.NP * v.M / v.H, bcost = found ? best.NP * best.M / best.H : 0;
+    if (!found || cost < bcost || (cost == bcost && (v.H > best.H || (v.H == best.H && v.M > best.M)))) {
+      best = v;
+      found = true;
     }
   }
-  *M = bestM;
-  *NP = bestNP;
+  *out = best;
+  return found;
 }
 
 int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
@@ -519,10 +586,10 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
   P.out = out;
   P.walk_stats = walk_stats;
   P.stats = stats;
-  int M = 0, NP = 0;
-  choose_tiles(P.L, P.skew, P.p, cfg->tile_m, &M, &NP);
-  if (M == 0) return LABS_ERR_INVALID_ARG;
-  P.M = M;
+  Variant v;
+  if (!choose_variant(P.L, P.skew, P.p, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
+  P.M = v.M;
+  make_layout(P.ly, P.L, P.skew, P.p, v.M, v.H);
 
   char* w = static_cast<char*>(ws_get(ctx, kWsWalkCounters, 256));
   if (!w) return LABS_ERR_NOMEM;
@@ -542,18 +609,19 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
   walk_init_kernel<<<1, 1, 0, st>>>(stats, P.E_thr_ptr, P.E_thr_value, P.counter);
   if (P.n_walks == 0) return cuda_status(cudaGetLastError());
   int warps = cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8;
-  switch (M * 10 + NP) {
-    case 41: return launch_walk_t<4, 1>(ctx, P, warps, st);
-    case 42: return launch_walk_t<4, 2>(ctx, P, warps, st);
-    case 43: return launch_walk_t<4, 3>(ctx, P, warps, st);
-    case 81: return launch_walk_t<8, 1>(ctx, P, warps, st);
-    case 82: return launch_walk_t<8, 2>(ctx, P, warps, st);
-    case 83: return launch_walk_t<8, 3>(ctx, P, warps, st);
-    case 121: return launch_walk_t<12, 1>(ctx, P, warps, st);
-    case 122: return launch_walk_t<12, 2>(ctx, P, warps, st);
-    case 123: return launch_walk_t<12, 3>(ctx, P, warps, st);
-    case 161: return launch_walk_t<16, 1>(ctx, P, warps, st);
-    case 162: return launch_walk_t<16, 2>(ctx, P, warps, st);
+  switch (v.M * 100 + v.H * 10 + v.NP) {
+    case 811: return launch_walk_t<8, 1, 1>(ctx, P, warps, st);
+    case 812: return launch_walk_t<8, 1, 2>(ctx, P, warps, st);
+    case 813: return launch_walk_t<8, 1, 3>(ctx, P, warps, st);
+    case 1621: return launch_walk_t<16, 2, 1>(ctx, P, warps, st);
+    case 1622: return launch_walk_t<16, 2, 2>(ctx, P, warps, st);
+    case 1623: return launch_walk_t<16, 2, 3>(ctx, P, warps, st);
+    case 1211: return launch_walk_t<12, 1, 1>(ctx, P, warps, st);
+    case 1212: return launch_walk_t<12, 1, 2>(ctx, P, warps, st);
+    case 1221: return launch_walk_t<12, 2, 1>(ctx, P, warps, st);
+    case 1222: return launch_walk_t<12, 2, 2>(ctx, P, warps, st);
+    case 1611: return launch_walk_t<16, 1, 1>(ctx, P, warps, st);
+    case 1612: return launch_walk_t<16, 1, 2>(ctx, P, warps, st);
     default: return LABS_ERR_INVALID_ARG;
   }
 }
