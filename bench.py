@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
-    ap.add_argument("--cpu-flips", type=int, default=3000)
+    ap.add_argument("--cpu-flips", type=int, default=6000)
     return ap.parse_args()
 
 
@@ -71,8 +71,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(flips_per_launch):
-    """DRAM bytes of one walk-kernel launch, scaled from the committed ncu capture; None if stale."""
+def traffic_per_launch(n_walks):
+    """DRAM bytes of one walk-kernel launch, scaled by walks from the committed ncu capture of a smaller
+    launch (its traffic is the per-walk candidate records and statistics); None if the kernel changed."""
     try:
         with open(PROFILE_TRAFFIC) as f:
             d = json.load(f)
@@ -80,7 +81,7 @@ def traffic_per_launch(flips_per_launch):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d["dram_bytes_per_flip"] * flips_per_launch
+    return d["dram_bytes_per_walk"] * n_walks
 
 
 class ClockSampler:
@@ -296,7 +297,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-                     "traffic": traffic_per_launch(flips_per_launch),
+                     "traffic": traffic_per_launch(n_walks),
                      "kernel": "walk_kernel", "walk_kernel_ms": walk_s * 1e3,
                      "work": "%d neighbour-lag terms per flip (202 free x 225 even lags), one int32 multiply-add "
                              "each; peak = 152 SMs x 128 lanes x 2070 MHz" % terms_per_flip(L, p)},
