@@ -157,6 +157,26 @@ int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t*
                           void* stream);
 
 /*
+ * labs_sample_threshold_noalloc -- the same sieve bound as labs_sample_threshold for callers that may
+ * not allocate device memory: an application whose allocator owns every device byte (a framework memory
+ * pool, a fixed arena sized at start-up) forbids direct cudaMalloc, and a latency-sensitive caller avoids
+ * it because it can synchronise the device.  The paper has no counterpart; this is a property of the
+ * library, not of the method.
+ *   No context is needed and nothing is allocated: no cudaMalloc, cudaFree or allocating library routine
+ *   is called.  The scratch (sampled energies and histograms) is one fixed device array of 4.26 MB that
+ *   every GPU loading the library holds until the process exits.
+ *   Runs on the current device and `stream`; arguments as in labs_sample_threshold (prefixes device,
+ *   E_thr_out device int32); the sampled energies are not returned.
+ *   n_samples may be at most 1,048,576 (2^20); larger values return LABS_ERR_CAPACITY.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ *   first call before any stream capture.
+ *   Every call shares the one array and clears the parts that must start at zero; calls that overlap on
+ *   the GPU (other streams, other host threads) race on it and must be serialised by the caller.
+ */
+int labs_sample_threshold_noalloc(int L, int skew, int p, const uint64_t* prefixes, int n_prefix, uint64_t seed,
+                                  int64_t n_samples, int64_t rank, int32_t* E_thr_out, void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

@@ -112,6 +112,22 @@ def labs_sample_threshold(L, skew, p, prefixes, seed, n_samples, rank, return_sa
     return (thr, samples) if return_samples else thr
 
 
+def labs_sample_threshold_noalloc(L, skew, p, prefixes, seed, n_samples, rank, device=None):
+    """The sieve bound through the allocation-free entry point (fixed scratch, at most 2^20 samples).
+
+    For callers that may not allocate device memory; ``prefixes`` and the returned int32 [1] tensor
+    are the caller's.
+    """
+    dev = _device(device)
+    pre = _prefix_tensor(prefixes, p, dev)
+    thr = torch.empty(1, dtype=torch.int32, device=dev)
+    with torch.cuda.device(dev):
+        _lib.check(load().labs_sample_threshold_noalloc(L, int(bool(skew)), p, _ptr(pre), pre.shape[0], seed,
+                                                        n_samples, rank, _ptr(thr), _stream(dev)),
+                   "labs_sample_threshold_noalloc")
+    return thr
+
+
 def make_walk_cfg(L, skew=True, p=0, n_walks=1, flip_budget=1000, T_i=0, seed=0, R=16, bloom_log2=15, bloom_k=4,
                   E_thr=INT32_MAX, n_thresh_samples=0, thresh_rank=0, E_target=INT32_MIN, walk_begin=0, tile_m=0,
                   warps_per_cta=0, E_thr_dev=None):

@@ -33,6 +33,7 @@ SIGNATURES = {
     "labs_skew_search": (_ci, [_P, _P, _P, _ci, _P, _P, _P, _P]),
     "labs_sample_threshold": (_ci, [_P, _ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P, _P]),
     "labs_skew_exhaustive": (_ci, [_P, _ci, _ci, _u64, _P, _P, _P, _P, _P]),
+    "labs_sample_threshold_noalloc": (_ci, [_ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P]),
 }
 
 

@@ -12,6 +12,7 @@
 //   apply  -- O(L) table update, byte/bit flips, fingerprint, Bloom insert,
 //   sieve  -- the walk's R best distinct (E, fp) states with E <= E_thr, one per lane.
 #include <algorithm>
+#include <mutex>
 
 #include "labs_core.cuh"
 #include "labs_internal.h"
@@ -627,3 +628,80 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
 }
 
 }  // namespace labsg
+
+// ---------------------------------------------------------------------------------------------
+// Sieve bound without any allocation (labs_sample_threshold_noalloc).
+//
+// Some callers cannot allocate device memory while they run this library.  An application whose
+// allocator owns every device byte (a framework memory pool, a fixed arena sized at start-up) forbids
+// direct cudaMalloc; latency-sensitive callers avoid it because it can synchronise the device; and no
+// library context (which grows workspace on demand) may exist at all.  For them this entry point runs the
+// same kernels as labs_sample_threshold with its scratch -- the sampled energies, both histograms and the
+// selected bin -- in one file-scope device array of fixed size, loaded with the library.
+// ---------------------------------------------------------------------------------------------
+namespace labsg {
+namespace {
+
+constexpr int64_t kNoAllocMaxSamples = int64_t(1) << 20;  // 1,048,576 samples (>= the 10^6 sieve sample)
+constexpr size_t kNoAllocSamplesBytes = sizeof(int32_t) * (size_t)kNoAllocMaxSamples;
+constexpr size_t kNoAllocHistBytes = sizeof(unsigned) * 2 * kHistBins;
+constexpr size_t kNoAllocBytes = kNoAllocSamplesBytes + kNoAllocHistBytes + 256;  // + the selected bin
+
+// Every GPU that loads the library holds these 4.26 MB until the process exits.  All calls share it.
+static __device__ __align__(256) unsigned char g_threshold_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kNoAllocMaxDevices];  // device address of g_threshold_scratch per device
+
+// Set-up, once per device, with that device current: the host-side name of the array is not a device
+// address, so ask the runtime for it.
+int threshold_scratch(int device, unsigned char** out) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_threshold_scratch) != cudaSuccess || !p) return LABS_ERR_CUDA;
+    g_scratch_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+  return LABS_OK;
+}
+
+}  // namespace
+}  // namespace labsg
+
+extern "C" int labs_sample_threshold_noalloc(int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
+                                             uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out,
+                                             void* stream) {
+  using namespace labsg;
+  if (L < 3 || L > LABS_MAX_L || (skew != 0 && skew != 1) || p < 0 || n_prefix < 1) return LABS_ERR_INVALID_ARG;
+  if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
+  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
+  if (!prefixes || (reinterpret_cast<uintptr_t>(prefixes) & 7u) || !E_thr_out ||
+      (reinterpret_cast<uintptr_t>(E_thr_out) & 3u))
+    return LABS_ERR_INVALID_ARG;
+  if (n_samples < 1 || rank < 0 || rank >= n_samples) return LABS_ERR_INVALID_ARG;
+  if (n_samples > kNoAllocMaxSamples) return LABS_ERR_CAPACITY;  // beyond the fixed scratch
+  int device = 0, sms = 0;
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kNoAllocMaxDevices) return LABS_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    return LABS_ERR_CUDA;
+  unsigned char* base = nullptr;
+  int s = threshold_scratch(device, &base);
+  if (s != LABS_OK) return s;
+  int32_t* Es = reinterpret_cast<int32_t*>(base);
+  unsigned* hist = reinterpret_cast<unsigned*>(base + kNoAllocSamplesBytes);
+  long long* sel = reinterpret_cast<long long*>(base + kNoAllocSamplesBytes + kNoAllocHistBytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int prefix_words = p > 0 ? (p + 63) / 64 : 1;
+  // the histograms keep the previous call's counts: clear them first
+  if (cudaMemsetAsync(hist, 0, kNoAllocHistBytes, st) != cudaSuccess) return LABS_ERR_CUDA;
+  int64_t blocks = std::min<int64_t>((n_samples + kSampleWarps - 1) / kSampleWarps, (int64_t)sms * 8);
+  sample_kernel<<<(unsigned)blocks, 32 * kSampleWarps, 0, st>>>(L, skew, p, prefixes, n_prefix, prefix_words, seed,
+                                                                 n_samples, Es, hist);
+  select_bin_kernel<<<1, 1024, 0, st>>>(hist, rank, sel);
+  int64_t hb = std::min<int64_t>((n_samples + 255) / 256, (int64_t)sms * 8);
+  hist_low_kernel<<<(unsigned)hb, 256, 0, st>>>(Es, n_samples, sel, hist + kHistBins);
+  finish_select_kernel<<<1, 1024, 0, st>>>(hist + kHistBins, sel, E_thr_out);
+  return cudaGetLastError() == cudaSuccess ? LABS_OK : LABS_ERR_CUDA;
+}
