@@ -147,6 +147,44 @@ int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* pr
                      labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, void* stream);
 
 /*
+ * Mixed-length batch (step 1 over many lengths at once; the paper runs lengths as separate jobs, so this
+ * batching is the library's).  Odd lengths walk skew-symmetrically behind the prefix (Algorithm 1),
+ * even lengths walk the unrestricted neighbourhood with no prefix.
+ */
+typedef struct {
+  int32_t n_len;            /* lengths in the batch, 1..96 */
+  int32_t p;                /* prefix length for odd lengths (<= k of the shortest odd length) */
+  int64_t flip_budget;      /* accepted flips per walk, < 2^32 */
+  uint64_t seed;            /* stream seed (walks: (seed, 1, walk, segment); samples: (seed, 2, i, 0)) */
+  int32_t R;                /* candidates kept per walk, 1..32 */
+  int32_t bloom_log2;       /* 5..15 */
+  int32_t bloom_k;          /* 1..8 */
+  int32_t T_i;              /* segment length; <= 0 means 4(L+1) for each length */
+  int64_t n_thresh_samples; /* per-length sieve bound: samples (<= 2^31) */
+  int64_t thresh_rank;      /* per-length sieve bound: 0-based rank */
+  int32_t E_target;         /* per-walk first flip reaching E <= E_target (walk_stats[5]); INT32_MIN = off */
+  int32_t tile_m;           /* 0: autotuned (timed trial, cached per length set and SM count); 8, 12, 16 */
+  int32_t warps_per_cta;    /* 0: autotuned; 1..8 */
+  int32_t use_graph;        /* 1: capture the step into a CUDA graph on first use and replay it */
+} labs_batch_cfg;
+
+/*
+ * labs_batched_search -- every length's sieve bound (as labs_sample_threshold), then ONE persistent
+ * launch over all (length, walk) work items, pulled from a device counter.
+ *   lengths [n_len] int32 HOST, 3..576; walks [n_len] int64 HOST, walks per length (walk ids 0..walks-1
+ *   within each length).
+ *   prefixes as in labs_skew_search.  out [sum walks][R] candidates, DEVICE, grouped by length in the
+ *   given order; walk_stats nullable [sum walks][6] int64 DEVICE; E_thr_out nullable [n_len] int32 DEVICE
+ *   (the sieve bounds used); stats DEVICE (E_thr reports the first length's bound).
+ *   With use_graph the first call with a given configuration and buffers captures the step into a CUDA
+ *   graph (on a private stream) and later calls replay it on `stream`.
+ * Errors: LABS_ERR_INVALID_ARG on a bad configuration or a length that fits no tile variant.
+ */
+int labs_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
+                        const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                        int32_t* E_thr_out, labs_walk_stats* stats, void* stream);
+
+/*
  * labs_sample_threshold -- the sieve bound E_l of Algorithm 1 under the nearest-rank reading: draws
  * n_samples starts exactly like walk starts (sample i: prefix i mod n_prefix, stream (seed, 2, i, 0))
  * and writes the 0-based `rank`-th smallest sampled energy to *E_thr_out (device int32).

@@ -11,8 +11,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (INT32_MAX, INT32_MIN, LABS_AUTO_THRESHOLD, LABS_MAX_L, LABS_MAX_W, LabsError, WalkCfg,
-                   load, status_string)
+from ._lib import (INT32_MAX, INT32_MIN, LABS_AUTO_THRESHOLD, LABS_MAX_L, LABS_MAX_W, BatchCfg, LabsError,
+                   WalkCfg, load, status_string)
 
 CANDIDATE_DTYPE = np.dtype(
     [("E", "<i4"), ("walk", "<u4"), ("step", "<u4"), ("pad", "<u4"), ("fp", "<u8"), ("seq", "<u8", (LABS_MAX_W,))]
@@ -156,6 +156,41 @@ def labs_skew_search(cfg, prefixes, device=None, with_walk_stats=True):
     _lib.check(load().labs_skew_search(context(dev.index), ctypes.byref(cfg), _ptr(pre), pre.shape[0], _ptr(out),
                                        _ptr(ws), _ptr(st), _stream(dev)), "labs_skew_search")
     return out, ws, st
+
+
+def make_batch_cfg(n_len, p=24, flip_budget=10000, seed=2410, R=16, bloom_log2=15, bloom_k=4, T_i=0,
+                   n_thresh_samples=1000000, thresh_rank=999, E_target=INT32_MIN, tile_m=0, warps_per_cta=0,
+                   use_graph=True):
+    cfg = BatchCfg()
+    cfg.n_len, cfg.p, cfg.flip_budget, cfg.seed = n_len, p, flip_budget, seed
+    cfg.R, cfg.bloom_log2, cfg.bloom_k, cfg.T_i = R, bloom_log2, bloom_k, T_i
+    cfg.n_thresh_samples, cfg.thresh_rank, cfg.E_target = n_thresh_samples, thresh_rank, E_target
+    cfg.tile_m, cfg.warps_per_cta, cfg.use_graph = tile_m, warps_per_cta, int(bool(use_graph))
+    return cfg
+
+
+def labs_batched_search(cfg, lengths, walks, prefixes, device=None, out=None, walk_stats=True):
+    """Mixed-length step 1 in one persistent launch (odd lengths skew, even unrestricted).
+
+    Returns (candidates uint8 device tensor [sum(walks) * R * 96], walk_stats int64 [sum(walks), 6] or
+    None, per-length sieve bounds int32 [n_len], stats uint8 [48]).  Pass `out` (and reuse the returned
+    tensors) to replay the captured graph with the same buffers.
+    """
+    dev = _device(device)
+    Ls = np.ascontiguousarray(np.asarray(lengths, dtype=np.int32))
+    Ws = np.ascontiguousarray(np.asarray(walks, dtype=np.int64))
+    total = int(Ws.sum())
+    pre = _prefix_tensor(prefixes, cfg.p, dev)
+    if out is None:
+        out = (torch.empty(max(1, total * cfg.R * _lib.CANDIDATE_BYTES), dtype=torch.uint8, device=dev),
+               torch.empty((max(1, total), 6), dtype=torch.int64, device=dev) if walk_stats else None,
+               torch.empty(len(Ls), dtype=torch.int32, device=dev),
+               torch.empty(_lib.WALK_STATS_BYTES, dtype=torch.uint8, device=dev))
+    cand, ws, thr, st = out
+    _lib.check(load().labs_batched_search(context(dev.index), ctypes.byref(cfg), ctypes.c_void_p(Ls.ctypes.data),
+                                          ctypes.c_void_p(Ws.ctypes.data), _ptr(pre), pre.shape[0], _ptr(cand),
+                                          _ptr(ws), _ptr(thr), _ptr(st), _stream(dev)), "labs_batched_search")
+    return out
 
 
 def labs_skew_search_host(cfg, prefixes_host, device=None):

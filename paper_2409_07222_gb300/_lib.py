@@ -34,6 +34,7 @@ SIGNATURES = {
     "labs_sample_threshold": (_ci, [_P, _ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P, _P]),
     "labs_skew_exhaustive": (_ci, [_P, _ci, _ci, _u64, _P, _P, _P, _P, _P]),
     "labs_sample_threshold_noalloc": (_ci, [_ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P]),
+    "labs_batched_search": (_ci, [_P, _P, _P, _P, _P, _ci, _P, _P, _P, _P, _P]),
 }
 
 
@@ -48,6 +49,17 @@ class WalkCfg(ctypes.Structure):
         ("n_thresh_samples", _i64), ("thresh_rank", _i64),
         ("E_target", _i32), ("tile_m", _i32), ("warps_per_cta", _i32), ("reserved", _i32),
         ("E_thr_dev", _P),
+    ]
+
+
+class BatchCfg(ctypes.Structure):
+    """labs_batch_cfg (include/labs.h)."""
+
+    _fields_ = [
+        ("n_len", _i32), ("p", _i32), ("flip_budget", _i64), ("seed", _u64),
+        ("R", _i32), ("bloom_log2", _i32), ("bloom_k", _i32), ("T_i", _i32),
+        ("n_thresh_samples", _i64), ("thresh_rank", _i64),
+        ("E_target", _i32), ("tile_m", _i32), ("warps_per_cta", _i32), ("use_graph", _i32),
     ]
 
 

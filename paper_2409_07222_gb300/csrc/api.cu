@@ -75,6 +75,8 @@ void labs_ctx_destroy(labs_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (int i = 0; i < 8; i++)
     if (ctx->ws[i]) cudaFree(ctx->ws[i]);
   delete ctx;
@@ -150,6 +152,37 @@ int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* pr
   s = set_device(ctx);
   if (s != LABS_OK) return s;
   return labsg::launch_skew_search(ctx, cfg, prefixes, n_prefix, out, walk_stats, stats, (cudaStream_t)stream);
+}
+
+int labs_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
+                        const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                        int32_t* E_thr_out, labs_walk_stats* stats, void* stream) {
+  if (!ctx || !cfg || !lengths || !walks || cfg->n_len < 1 || cfg->n_len > 96) return LABS_ERR_INVALID_ARG;
+  int64_t total = 0;
+  int min_odd = LABS_MAX_L + 1;
+  for (int i = 0; i < cfg->n_len; i++) {
+    if (lengths[i] < 3 || lengths[i] > LABS_MAX_L || walks[i] < 0) return LABS_ERR_INVALID_ARG;
+    if (lengths[i] & 1) min_odd = lengths[i] < min_odd ? lengths[i] : min_odd;
+    total += walks[i];
+  }
+  if (cfg->p < 0 || (min_odd <= LABS_MAX_L && cfg->p > (min_odd - 1) / 2)) return LABS_ERR_INVALID_ARG;
+  if (n_prefix < 1 || !prefixes || !aligned8(prefixes)) return LABS_ERR_INVALID_ARG;
+  if (total > 0xffffffffLL || cfg->flip_budget < 0 || cfg->flip_budget > 0xffffffffLL) return LABS_ERR_INVALID_ARG;
+  if (cfg->R < 1 || cfg->R > labsg::kMaxR || cfg->bloom_log2 < 5 || cfg->bloom_log2 > 15 || cfg->bloom_k < 1 ||
+      cfg->bloom_k > 8)
+    return LABS_ERR_INVALID_ARG;
+  if (cfg->n_thresh_samples < 1 || cfg->n_thresh_samples > 0x7fffffffLL || cfg->thresh_rank < 0 ||
+      cfg->thresh_rank >= cfg->n_thresh_samples)
+    return LABS_ERR_INVALID_ARG;
+  if (cfg->tile_m != 0 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16) return LABS_ERR_INVALID_ARG;
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
+  if (!stats || !aligned8(stats) || (total > 0 && (!out || !aligned8(out))) || (walk_stats && !aligned8(walk_stats)) ||
+      (E_thr_out && !aligned4(E_thr_out)))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_batched_search(ctx, cfg, lengths, walks, prefixes, n_prefix, out, walk_stats, E_thr_out, stats,
+                                      (cudaStream_t)stream);
 }
 
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,

@@ -6,6 +6,8 @@
 
 #include "labs.h"
 
+constexpr int kMaxTuned = 16;
+
 struct labs_ctx {
   int device;
   int num_sms;
@@ -13,11 +15,19 @@ struct labs_ctx {
   // growable device workspace, one region per purpose
   void* ws[8];
   size_t ws_bytes[8];
+  // autotuner cache: (length-set key) -> tile M, lag ranges H, walks per CTA
+  int n_tuned;
+  uint64_t tuned_key[kMaxTuned];
+  int tuned[kMaxTuned][3];
+  // captured batched step (one at a time) and the stream it was captured on
+  cudaGraphExec_t graph_exec;
+  uint64_t graph_key;
+  cudaStream_t capture_stream;
 };
 
 namespace labsg {
 
-enum WsSlot { kWsThreshSamples = 0, kWsThreshHist = 1, kWsWalkCounters = 2, kWsThreshValue = 3, kWsPq0 = 4 };
+enum WsSlot { kWsThreshSamples = 0, kWsThreshHist = 1, kWsWalkCounters = 2, kWsBatchThresholds = 3, kWsPq0 = 4 };
 
 // Returns a device region of at least `bytes` for `slot`, growing it if needed (not capturable).
 void* ws_get(labs_ctx* ctx, int slot, size_t bytes);
@@ -34,6 +44,9 @@ int launch_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_
                             int32_t* E_samples, cudaStream_t st);
 int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
                        labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, cudaStream_t st);
+int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
+                          const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                          int32_t* E_thr_out, labs_walk_stats* stats, cudaStream_t st);
 int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                            uint64_t* out_argmin_free, uint64_t* out_argmin_seq, cudaStream_t st);
 

@@ -1,18 +1,21 @@
-// walk.cu -- step 1 of the dual-step search: Algorithm 1's self-avoiding walks (labs_skew_search)
-// and the sieve bound E_l (labs_sample_threshold).
+// walk.cu -- step 1 of the dual-step search: Algorithm 1's self-avoiding walks (labs_skew_search,
+// labs_batched_search) and the sieve bound E_l (labs_sample_threshold).
 //
 // GB300 mapping.  The paper runs one walk per thread block with a shared-memory reduction (Fig. 3);
 // here one walk is one warp (shuffle/redux reductions, no block barriers) and a persistent grid pulls
-// walk ids from a device counter, so long and short walks balance across the 152 SMs.  Each warp's
-// state (sequence bits, byte windows, correlation table, Bloom filter of 2^bloom_log2 bits) lives in
-// its shared-memory slab; a step is
+// work items (length, walk) from a device counter, so walks of different lengths and lengths of
+// different cost balance across the 152 SMs in one launch.  Each warp's state (sequence bits, byte
+// windows, correlation table, Bloom filter of 2^bloom_log2 bits, per-neighbour slots) lives in its
+// shared-memory slab; a step is
 //   scan   -- Delta E of every free neighbour (tiled dp4a loop, labs_core.cuh),
 //   select -- warp argmin of (Delta E, m); Bloom test of the winner's fingerprint; on a hit the owner
-//             lane excludes that neighbour and the argmin repeats (same result as testing them all),
-//   apply  -- O(L) table update, byte/bit flips, fingerprint, Bloom insert,
+//             lane drops that neighbour and the argmin repeats (same result as testing them all),
+//   apply  -- O(L) table update, O(1)-per-neighbour P update, byte/bit flips, fingerprint, Bloom insert,
 //   sieve  -- the walk's R best distinct (E, fp) states with E <= E_thr, one per lane.
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "labs_core.cuh"
 #include "labs_internal.h"
@@ -20,24 +23,35 @@
 namespace labsg {
 namespace {
 
+constexpr int kMaxLens = 96;    // lengths in one launch (kernel parameter table)
+constexpr int kMaxPasses = 3;   // lane passes over the tasks of one walk
+
 struct WalkSmem {
   ScanSmem s;
   uint32_t bloom[1024];  // up to 2^15 bits
 };
 
+// Per-length entry of a launch: the layout (tiles, windows) and where its walks sit among the items.
+struct LenEntry {
+  Layout ly;
+  int T_i;
+  int32_t E_thr_value;  // used when WalkParams::E_thr_dev is null
+  int64_t item_begin;   // first work item of this length
+  int64_t walk_begin;   // global walk id of its first walk
+};
+
 struct WalkParams {
-  Layout ly;  // computed on the host; read from the kernel's parameter space
-  int L, skew, p, T_i, R, bloom_log2, bloom_k, prefix_words, n_prefix, M;
-  int64_t n_walks, walk_begin, flip_budget;
+  int n_len, R, bloom_log2, bloom_k, prefix_words, n_prefix, slot_stride;
+  int32_t E_target;
+  int64_t n_items, flip_budget;
   uint64_t seed;
   const uint64_t* prefixes;
-  const int32_t* E_thr_ptr;  // nullable: use E_thr_value
-  int32_t E_thr_value;
-  int32_t E_target;
-  labs_candidate* out;
-  int64_t* walk_stats;
+  const int32_t* E_thr_dev;  // nullable: per-length sieve bounds in device memory
+  labs_candidate* out;       // [n_items][R]
+  int64_t* walk_stats;       // nullable: [n_items][6]
   labs_walk_stats* stats;
   unsigned long long* counter;
+  LenEntry len[kMaxLens];
 };
 
 __device__ __forceinline__ uint32_t bloom_idx(uint64_t fp, int j, uint32_t mask) {
@@ -69,8 +83,6 @@ __device__ __forceinline__ bool key_less(int Ea, uint64_t fa, int Eb, uint64_t f
   return Ea < Eb || (Ea == Eb && fa < fb);
 }
 
-// Per-slot constants derived from the position m: alpha, the excluded lag gd, the sign relation
-// s_{m'} = sigma s_m (Eq. 2) and K0 = alpha^2 (n_f + n_b - pair).
 struct SlotConst {
   int alpha, gd, sigma, K0, gmax;
 };
@@ -112,61 +124,79 @@ __device__ __forceinline__ int p_step(const ScanSmem& sm, int cls, int q, const 
   return P;
 }
 
-template <int M, int H, int NP>
-__global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
-  constexpr int MH = M / H;   // slots owned by a lane per pass
-  constexpr int S = NP * MH;  // slots owned by a lane
+// Task of `lane` in pass `ps`: tile (class, q0), lag range h, whether it exists.
+__device__ __forceinline__ bool lane_task(const Layout& ly, int H, int ps, int lane, int& cls, int& q0, int& h) {
+  const int task = ps * 32 + lane;
+  h = H == 2 ? (task & 1) : 0;
+  cls = 0;
+  q0 = 0;
+  if (task >= ly.n_tasks) return false;
+  tile_of(ly, H == 2 ? (task >> 1) : task, cls, q0);
+  return true;
+}
+
+// One walk-step kernel for every length of the launch.  Template: tile size M and lag ranges per tile H
+// (the autotuned "words per thread"); the number of lane passes is per length (<= kMaxPasses).
+// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): Delta E (int32),
+// P_m (int16, |P| <= L/2) and s_m * m (int16).
+// ONE: a single-length launch -- the length's entry is read at a fixed parameter offset and its
+// Zobrist keys are tabulated once per block in shared memory.
+template <int M, int H, bool ONE>
+__global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ WalkParams P) {
+  constexpr int MH = M / H;  // slots owned by a lane per pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   WalkSmem& ws = reinterpret_cast<WalkSmem*>(smem_raw)[wid];
-  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + sizeof(WalkSmem) * nwarps);
   ScanSmem& sm = ws.s;
+  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * 8) * nwarps);
+  if (ONE) {
+    const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)P.len[0].ly.L, 0);
+    for (int i = threadIdx.x; i < P.len[0].ly.L; i += blockDim.x) ztab[i] = zobrist(zk, i + 1);
+    __syncthreads();
+  }
+  unsigned char* slot_base = smem_raw + sizeof(WalkSmem) * nwarps + (size_t)wid * P.slot_stride * 32 * 8;
+  int* sl_d = reinterpret_cast<int*>(slot_base);
+  int16_t* sl_P = reinterpret_cast<int16_t*>(slot_base + (size_t)P.slot_stride * 32 * 4);
+  int16_t* sl_ms = sl_P + P.slot_stride * 32;
   const int lane = lane_id();
-  const Layout& ly = P.ly;
-  const uint64_t zkey = stream_key(0, kPurposeZobrist, (uint64_t)P.L, 0);
-  const int32_t E_thr = P.E_thr_ptr ? *P.E_thr_ptr : P.E_thr_value;
   const uint32_t bmask = (1u << P.bloom_log2) - 1u;
   const int bwords = 1 << (P.bloom_log2 - 5);
-  const int W = (P.L + 63) >> 6;
   const int R = P.R;
-  // Zobrist keys of this length, shared by the block (index i-1 for position i)
-  for (int i = threadIdx.x; i < P.L; i += blockDim.x) ztab[i] = zobrist(zkey, i + 1);
-  __syncthreads();
-
-  // this lane's task per pass: tile (class, q0) and lag range h; its slots are tile positions
-  // h*MH .. h*MH+MH-1 (after the partial sums of the H lanes of a tile are combined)
-  int tcls[NP], tq0[NP], th[NP];
-  bool thas[NP];
-  int slot_m[S];  // position of each owned slot, 0 if none
-#pragma unroll
-  for (int ps = 0; ps < NP; ps++) {
-    const int task = ps * 32 + lane;
-    thas[ps] = task < ly.n_tasks;
-    th[ps] = H == 2 ? (task & 1) : 0;
-    tcls[ps] = 0;
-    tq0[ps] = 0;
-    const int tile = H == 2 ? (task >> 1) : task;
-    if (tile < ly.n_tiles) tile_of(ly, tile, tcls[ps], tq0[ps]);
-#pragma unroll
-    for (int k = 0; k < MH; k++) {
-      const int m = q_pos(ly, tcls[ps], tq0[ps] + th[ps] * MH + k);
-      slot_m[ps * MH + k] = (thas[ps] && m >= ly.p + 1 && m <= ly.mlast) ? m : 0;
-    }
-  }
+  const unsigned budget = (unsigned)P.flip_budget;  // < 2^32, checked by the host
 
   long long agg_flips = 0, agg_segs = 0, agg_skips = 0, agg_dead = 0;
   int agg_best = INT32_MAX;
 
   while (true) {
-    unsigned long long wrel = 0;
-    if (lane == 0) wrel = atomicAdd(P.counter, 1ull);
-    wrel = __shfl_sync(kFull, wrel, 0);
-    if ((long long)wrel >= P.n_walks) break;
-    const int64_t w = P.walk_begin + (int64_t)wrel;
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(P.counter, 1ull);
+    item = __shfl_sync(kFull, item, 0);
+    if ((long long)item >= P.n_items) break;
+    int li = 0;
+    if (!ONE)
+      while (li + 1 < P.n_len && P.len[li + 1].item_begin <= (long long)item) li++;
+    const LenEntry& le = ONE ? P.len[0] : P.len[li];
+    const Layout& ly = le.ly;
+    const int64_t w = le.walk_begin + ((long long)item - le.item_begin);
     const uint64_t* prefix = P.prefixes + (w % P.n_prefix) * P.prefix_words;
-    labs_candidate* rec = P.out + (int64_t)wrel * R;
+    const uint64_t zkey = stream_key(0, kPurposeZobrist, (uint64_t)ly.L, 0);
+    const int32_t E_thr = P.E_thr_dev ? P.E_thr_dev[li] : le.E_thr_value;
+    const int W = (ly.L + 63) >> 6;
+    const int NP = (ly.n_tasks + 31) >> 5;
+    const int S = NP * MH;
+    labs_candidate* rec = P.out + (int64_t)item * R;
 
+    // slot positions of this length
+    for (int ps = 0; ps < NP; ps++) {
+      int cls, q0, h;
+      const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+#pragma unroll
+      for (int k = 0; k < MH; k++) {
+        const int m = q_pos(ly, cls, q0 + h * MH + k);
+        sl_ms[(ps * MH + k) * 32 + lane] = (int16_t)((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0);
+      }
+    }
     // empty sieve slots
     for (int r = lane; r < R; r += 32) {
       rec[r].E = INT32_MAX;
@@ -183,56 +213,53 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
     uint64_t wfp = ~0ull;
     int wlane = 0;
 
-    // flip_budget < 2^32 is checked by the host, so the per-walk counters fit 32 bits (skips: 64)
     unsigned flips = 0, segs = 0, dead = 0;
     long long skips = 0;
     int first_hit = -1;
     int bestE = INT32_MAX;
-    int slot_P[S], slot_ms[S];  // P_m and s_m * m
 
-    const unsigned budget = (unsigned)P.flip_budget;
     while (flips < budget) {
       for (int t = lane; t < bwords; t += 32) ws.bloom[t] = 0u;
       build_start(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
       segs++;
-      uint64_t fp = fingerprint(sm, P.L, zkey);
+      uint64_t fp = fingerprint(sm, ly.L, zkey);
       bloom_add(ws.bloom, fp, P.bloom_k, bmask);
       int E = build_table(sm, ly);
       int SC = table_sum(sm);
       bool fast = pack_c8(sm);
       build_bytes(sm, ly);
-#pragma unroll
       for (int t = 0; t < S; t++) {
-        slot_P[t] = 0;
-        const int m = slot_m[t];
-        slot_ms[t] = m;
+        int m = sl_ms[t * 32 + lane];
+        m = m < 0 ? -m : m;
+        int Pm = 0;
         if (m) {
           SlotInfo si = slot_info(ly, pos_cls(ly, m), pos_q(ly, m));
-          slot_P[t] = p_from_scratch(sm, ly, pos_cls(ly, m), pos_q(ly, m), si);
-          slot_ms[t] = s_at(sm, ly, m) * m;
+          Pm = p_from_scratch(sm, ly, pos_cls(ly, m), pos_q(ly, m), si);
+          sl_ms[t * 32 + lane] = (int16_t)(s_at(sm, ly, m) * m);
         }
+        sl_P[t * 32 + lane] = (int16_t)Pm;
       }
 
       int it = 0;
       int mprev = 0;  // free position flipped by the previous move of this segment
-      while (it < P.T_i && flips < budget) {
+      while (it < le.T_i && flips < budget) {
         it++;
         // ---- scan; each lane keeps its best (Delta E, m)
         int bd = INT32_MAX, bm = INT32_MAX;
         int dprev = INT32_MAX;  // this lane's Delta E of the move back (only its owner sets it)
-        int slot_d[S];
-#pragma unroll
         for (int ps = 0; ps < NP; ps++) {
+          int cls, q0, h;
+          const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
           int acc[M];
 #pragma unroll
           for (int j = 0; j < M; j++) acc[j] = 0;
-          if (thas[ps]) {
-            const int u_begin = th[ps] ? ly.NGh : 0;
-            const int u_end = th[ps] ? ly.NGend : ly.NGh;
+          if (has) {
+            const int u_begin = h ? ly.NGh : 0;
+            const int u_end = h ? ly.NGend : ly.NGh;
             if (fast)
-              scan_range<M, false>(sm, ly, tcls[ps], tq0[ps], u_begin, u_end, acc);
+              scan_range<M, false>(sm, ly, cls, q0, u_begin, u_end, acc);
             else
-              scan_range<M, true>(sm, ly, tcls[ps], tq0[ps], u_begin, u_end, acc);
+              scan_range<M, true>(sm, ly, cls, q0, u_begin, u_end, acc);
           }
           if (H == 2) {
 #pragma unroll
@@ -241,14 +268,14 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
 #pragma unroll
           for (int k = 0; k < MH; k++) {
             const int t = ps * MH + k;
-            const int ms = slot_ms[t];
+            const int ms = sl_ms[t * 32 + lane];
             const int m = ms < 0 ? -ms : ms;
-            const int a = (H == 2 && th[ps]) ? acc[MH + k] : acc[k];
+            const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
             int d = INT32_MAX;
             if (m) {
               const SlotConst kc = slot_const(ly, m);
               const int s_m = ms < 0 ? -1 : 1;
-              d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * slot_P[t];
+              d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * (int)sl_P[t * 32 + lane];
               if (kc.alpha == 4) d += 8 * kc.sigma * (int)sm.C16[kc.gd - 1];
               if (m == mprev) {
                 dprev = d;  // the state just left: certainly in the Bloom filter
@@ -258,18 +285,18 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
                 bm = m;
               }
             }
-            slot_d[t] = d;
+            sl_d[t * 32 + lane] = d;
           }
         }
         // ---- select: smallest (Delta E, m) whose neighbour is not in the Bloom filter
         int mstar = -1, dstar = 0;
         uint64_t nfp = 0;
         for (int guard = 0; guard <= S * 32; guard++) {
-          int dmin = warp_min_i32(bd);
+          const int dmin = warp_min_i32(bd);
           if (dmin == INT32_MAX) break;
-          int mm = (int)warp_min_u32(bd == dmin ? (unsigned)bm : 0xffffffffu);
-          uint64_t cand = fp ^ ztab[mm - 1];
-          if (ly.skew && mm != ly.c) cand ^= ztab[ly.L - mm];
+          const int mm = (int)warp_min_u32(bd == dmin ? (unsigned)bm : 0xffffffffu);
+          uint64_t cand = fp ^ (ONE ? ztab[mm - 1] : zobrist(zkey, mm));
+          if (ly.skew && mm != ly.c) cand ^= ONE ? ztab[ly.L - mm] : zobrist(zkey, ly.L + 1 - mm);
           if (!bloom_test(ws.bloom, cand, P.bloom_k, bmask)) {
             mstar = mm;
             dstar = dmin;
@@ -279,12 +306,13 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
           skips++;
           if (bd == dmin && bm == mm) {
             // the owner lane's next best: smallest key ranked after (dmin, mm); keys ranked ahead were
-            // excluded earlier in this step
+            // dropped earlier in this step
             bd = INT32_MAX;
             int nbm = INT32_MAX;
-#pragma unroll
             for (int t = 0; t < S; t++) {
-              const int d = slot_d[t], m = slot_ms[t] < 0 ? -slot_ms[t] : slot_ms[t];
+              const int d = sl_d[t * 32 + lane];
+              const int ms = sl_ms[t * 32 + lane];
+              const int m = ms < 0 ? -ms : ms;
               if (d == INT32_MAX) continue;
               if (d < dmin || (d == dmin && m <= mm)) continue;
               if (d < bd || (d == bd && m < nbm)) {
@@ -308,18 +336,18 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
         const int s0 = s_at(sm, ly, mstar);
         const int q1f = f1 ? pos_q(ly, f1) : 0;  // the mirror has the class of m*
         const int s1 = f1 ? s_at(sm, ly, f1) : 0;
-#pragma unroll
         for (int t = 0; t < S; t++) {
-          const int m = slot_ms[t] < 0 ? -slot_ms[t] : slot_ms[t];
-          if (m) {
+          const int ms = sl_ms[t * 32 + lane];
+          const int m = ms < 0 ? -ms : ms;
+          if (m && !(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
             const SlotConst kc = slot_const(ly, m);
             const int cls = pos_cls(ly, m), q = pos_q(ly, m);
-            if (!(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
-              slot_P[t] = p_step(sm, cls, q, kc, slot_P[t], c0, q0f, s0);
-              if (f1) slot_P[t] = p_step(sm, cls, q, kc, slot_P[t], c0, q1f, s1);
-            }
-            if (m == mstar) slot_ms[t] = -slot_ms[t];
+            int Pm = sl_P[t * 32 + lane];
+            Pm = p_step(sm, cls, q, kc, Pm, c0, q0f, s0);
+            if (f1) Pm = p_step(sm, cls, q, kc, Pm, c0, q1f, s1);
+            sl_P[t * 32 + lane] = (int16_t)Pm;
           }
+          if (m && m == mstar) sl_ms[t * 32 + lane] = (int16_t)(-ms);
         }
         mprev = mstar;
         SC += table_update(sm, ly, mstar, &fast);
@@ -379,7 +407,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
     if (lane < R) rec[rank] = mine;
     __syncwarp();
     if (P.walk_stats && lane == 0) {
-      int64_t* st = P.walk_stats + (int64_t)wrel * 6;
+      int64_t* st = P.walk_stats + (int64_t)item * 6;
       st[0] = (int64_t)flips;
       st[1] = (int64_t)segs;
       st[2] = skips;
@@ -402,13 +430,14 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(WalkParams P) {
   }
 }
 
-__global__ void walk_init_kernel(labs_walk_stats* stats, const int32_t* E_thr_ptr, int32_t E_thr_value,
+// Zeroes the aggregates and the work counter; E_thr reports the first length's sieve bound.
+__global__ void walk_init_kernel(labs_walk_stats* stats, const int32_t* E_thr_dev, int32_t E_thr_value,
                                  unsigned long long* counter) {
   stats->flips = 0;
   stats->segments = 0;
   stats->bloom_skips = 0;
   stats->dead_ends = 0;
-  stats->E_thr = E_thr_ptr ? *E_thr_ptr : E_thr_value;
+  stats->E_thr = E_thr_dev ? E_thr_dev[0] : E_thr_value;
   stats->best_E = INT32_MAX;
   stats->status = LABS_OK;
   stats->reserved = 0;
@@ -497,21 +526,134 @@ __global__ void finish_select_kernel(const unsigned* __restrict__ hist2, long lo
   }
 }
 
-template <int M, int H, int NP>
-int launch_walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st) {
-  size_t smem = sizeof(WalkSmem) * (size_t)warps + sizeof(uint64_t) * LABS_MAX_L;
-  auto kern = walk_kernel<M, H, NP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return LABS_ERR_CUDA;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem);
-  if (e != cudaSuccess || per_sm < 1) return LABS_ERR_CUDA;
-  long long blocks = (long long)per_sm * ctx->num_sms;
-  long long need = (P.n_walks + warps - 1) / warps;
-  if (blocks > need) blocks = need;
-  if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, 32 * warps, smem, st>>>(P);
+struct Variant {
+  int M, H;
+};
+static const Variant kVariants[] = {{8, 1}, {12, 1}, {16, 1}, {16, 2}};
+
+// Passes a length needs with variant v (0 if the layout does not fit).
+static int passes_for(int L, int skew, int p, const Variant& v) {
+  Layout ly;
+  if (!make_layout(ly, L, skew, p, v.M, v.H)) return 0;
+  int np = (ly.n_tasks + 31) / 32;
+  return np < 1 ? 1 : np;
+}
+
+template <int M, int H>
+int walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st, bool configure, long long* blocks) {
+  const bool one = P.n_len == 1;
+  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * 8) * (size_t)warps +
+                      (one ? sizeof(uint64_t) * LABS_MAX_L : 0);
+  auto kern = one ? walk_kernel<M, H, true> : walk_kernel<M, H, false>;
+  if (configure) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return LABS_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem) != cudaSuccess || per_sm < 1)
+      return LABS_ERR_CUDA;
+    long long b = (long long)per_sm * ctx->num_sms;
+    const long long need = (P.n_items + warps - 1) / warps;
+    if (b > need) b = need;
+    *blocks = b < 1 ? 1 : b;
+    return LABS_OK;
+  }
+  kern<<<(unsigned)*blocks, 32 * warps, smem, st>>>(P);
   return cuda_status(cudaGetLastError());
+}
+
+// configure = true: sets the kernel's shared-memory limit and sizes the persistent grid (*blocks);
+// configure = false: launches with that grid (no runtime call besides the launch itself).
+static int walk_variant(labs_ctx* ctx, const WalkParams& P, const Variant& v, int warps, cudaStream_t st,
+                        bool configure, long long* blocks) {
+  switch (v.M * 10 + v.H) {
+    case 81: return walk_t<8, 1>(ctx, P, warps, st, configure, blocks);
+    case 121: return walk_t<12, 1>(ctx, P, warps, st, configure, blocks);
+    case 161: return walk_t<16, 1>(ctx, P, warps, st, configure, blocks);
+    case 162: return walk_t<16, 2>(ctx, P, warps, st, configure, blocks);
+    default: return LABS_ERR_INVALID_ARG;
+  }
+}
+
+static int launch_walk(labs_ctx* ctx, const WalkParams& P, const Variant& v, int warps, cudaStream_t st) {
+  long long blocks = 0;
+  int s = walk_variant(ctx, P, v, warps, st, true, &blocks);
+  return s == LABS_OK ? walk_variant(ctx, P, v, warps, st, false, &blocks) : s;
+}
+
+// One launch's lengths.
+struct LenSpec {
+  int L, skew, p, T_i;
+  int64_t walks, walk_begin;
+};
+
+// Fills the per-length table and slot stride for variant v; false if some length does not fit.
+static bool fill_params(WalkParams& P, const std::vector<LenSpec>& lens, const Variant& v) {
+  P.n_len = (int)lens.size();
+  int64_t item = 0;
+  int maxnp = 1;
+  for (size_t i = 0; i < lens.size(); i++) {
+    LenEntry& e = P.len[i];
+    if (!make_layout(e.ly, lens[i].L, lens[i].skew, lens[i].p, v.M, v.H)) return false;
+    int np = (e.ly.n_tasks + 31) / 32;
+    if (np > kMaxPasses) return false;
+    maxnp = std::max(maxnp, np);
+    e.T_i = lens[i].T_i > 0 ? lens[i].T_i : 4 * (lens[i].L + 1);
+    e.E_thr_value = INT32_MAX;
+    e.item_begin = item;
+    e.walk_begin = lens[i].walk_begin;
+    item += lens[i].walks;
+  }
+  P.n_items = item;
+  P.slot_stride = maxnp * (v.M / v.H);
+  return true;
+}
+
+// Heuristic choice: least total per-lane scan work sum(walks * NP * M / H); ties to more lanes per tile,
+// then the larger tile.
+static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, Variant* out) {
+  bool found = false;
+  long double best_cost = 0;
+  Variant best{0, 0};
+  for (const Variant& v : kVariants) {
+    if (req_m && v.M != req_m) continue;
+    long double cost = 0;
+    bool ok = true;
+    for (const LenSpec& s : lens) {
+      int np = passes_for(s.L, s.skew, s.p, v);
+      if (np == 0 || np > kMaxPasses) {
+        ok = false;
+        break;
+      }
+      cost += (long double)std::max<int64_t>(s.walks, 1) * np * v.M / v.H;
+    }
+    if (!ok) continue;
+    if (!found || cost < best_cost || (cost == best_cost && (v.H > best.H || (v.H == best.H && v.M > best.M)))) {
+      best = v;
+      best_cost = cost;
+      found = true;
+    }
+  }
+  *out = best;
+  return found;
+}
+
+static void base_params(WalkParams& P, int R, int bloom_log2, int bloom_k, int p, int n_prefix, int64_t flip_budget,
+                        uint64_t seed, int32_t E_target, const uint64_t* prefixes, labs_candidate* out,
+                        int64_t* walk_stats, labs_walk_stats* stats, unsigned long long* counter) {
+  P.R = R;
+  P.bloom_log2 = bloom_log2;
+  P.bloom_k = bloom_k;
+  P.prefix_words = p > 0 ? (p + 63) / 64 : 1;
+  P.n_prefix = n_prefix;
+  P.flip_budget = flip_budget;
+  P.seed = seed;
+  P.E_target = E_target;
+  P.prefixes = prefixes;
+  P.out = out;
+  P.walk_stats = walk_stats;
+  P.stats = stats;
+  P.counter = counter;
+  P.E_thr_dev = nullptr;
 }
 
 }  // namespace
@@ -538,93 +680,219 @@ int launch_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_
   return cuda_status(cudaGetLastError());
 }
 
-// Walk-kernel variants: (tile M, lag ranges H, passes NP).  The chooser takes the variant with the
-// least per-lane scan work NP * M / H (ties: more lanes per tile, then the larger tile).
-struct Variant {
-  int M, H, NP;
-};
-static const Variant kVariants[] = {{8, 1, 1},  {8, 1, 2},  {8, 1, 3},  {12, 1, 1}, {12, 1, 2}, {12, 2, 1},
-                                    {12, 2, 2}, {16, 1, 1}, {16, 1, 2}, {16, 2, 1}, {16, 2, 2}, {16, 2, 3}};
-
-static bool choose_variant(int L, int skew, int p, int req_m, Variant* out) {
-  bool found = false;
-  Variant best{0, 0, 0};
-  for (const Variant& v : kVariants) {
-    if (req_m && v.M != req_m) continue;
-    Layout ly;
-    if (!make_layout(ly, L, skew, p, v.M, v.H)) continue;
-    int np = (ly.n_tasks + 31) / 32;
-    if (np < 1) np = 1;
-    if (np != v.NP) continue;
-    int cost = v.NP * v.M / v.H, bcost = found ? best.NP * best.M / best.H : 0;
-    if (!found || cost < bcost || (cost == bcost && (v.H > best.H || (v.H == best.H && v.M > best.M)))) {
-      best = v;
-      found = true;
-    }
-  }
-  *out = best;
-  return found;
-}
-
 int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
                        labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, cudaStream_t st) {
-  WalkParams P{};
-  P.L = cfg->L;
-  P.skew = cfg->skew;
-  P.p = cfg->p;
-  P.T_i = cfg->T_i > 0 ? cfg->T_i : 4 * (cfg->L + 1);
-  P.R = cfg->R;
-  P.bloom_log2 = cfg->bloom_log2;
-  P.bloom_k = cfg->bloom_k;
-  P.prefix_words = cfg->p > 0 ? (cfg->p + 63) / 64 : 1;
-  P.n_prefix = n_prefix;
-  P.n_walks = cfg->n_walks;
-  P.walk_begin = cfg->walk_begin;
-  P.flip_budget = cfg->flip_budget;
-  P.seed = cfg->seed;
-  P.prefixes = prefixes;
-  P.E_target = cfg->E_target;
-  P.out = out;
-  P.walk_stats = walk_stats;
-  P.stats = stats;
+  std::vector<LenSpec> lens{{cfg->L, cfg->skew, cfg->p, cfg->T_i, cfg->n_walks, cfg->walk_begin}};
   Variant v;
-  if (!choose_variant(P.L, P.skew, P.p, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
-  P.M = v.M;
-  make_layout(P.ly, P.L, P.skew, P.p, v.M, v.H);
-
+  if (!choose_variant(lens, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
+  WalkParams* P = new (std::nothrow) WalkParams();
+  if (!P) return LABS_ERR_NOMEM;
   char* w = static_cast<char*>(ws_get(ctx, kWsWalkCounters, 256));
-  if (!w) return LABS_ERR_NOMEM;
-  P.counter = reinterpret_cast<unsigned long long*>(w);
+  if (!w) {
+    delete P;
+    return LABS_ERR_NOMEM;
+  }
+  base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, cfg->flip_budget, cfg->seed,
+              cfg->E_target, prefixes, out, walk_stats, stats, reinterpret_cast<unsigned long long*>(w));
+  fill_params(*P, lens, v);
   int32_t* thr = reinterpret_cast<int32_t*>(w + 64);
+  int s = LABS_OK;
   if (cfg->E_thr_dev) {
-    P.E_thr_ptr = cfg->E_thr_dev;
+    P->E_thr_dev = cfg->E_thr_dev;
   } else if (cfg->E_thr == LABS_AUTO_THRESHOLD) {
-    int s = launch_sample_threshold(ctx, P.L, P.skew, P.p, prefixes, n_prefix, P.prefix_words, P.seed,
-                                    cfg->n_thresh_samples, cfg->thresh_rank, thr, nullptr, st);
-    if (s != LABS_OK) return s;
-    P.E_thr_ptr = thr;
+    s = launch_sample_threshold(ctx, cfg->L, cfg->skew, cfg->p, prefixes, n_prefix, P->prefix_words, cfg->seed,
+                                cfg->n_thresh_samples, cfg->thresh_rank, thr, nullptr, st);
+    P->E_thr_dev = thr;
   } else {
-    P.E_thr_ptr = nullptr;
-    P.E_thr_value = cfg->E_thr;
+    P->len[0].E_thr_value = cfg->E_thr;
   }
-  walk_init_kernel<<<1, 1, 0, st>>>(stats, P.E_thr_ptr, P.E_thr_value, P.counter);
-  if (P.n_walks == 0) return cuda_status(cudaGetLastError());
-  int warps = cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8;
-  switch (v.M * 100 + v.H * 10 + v.NP) {
-    case 811: return launch_walk_t<8, 1, 1>(ctx, P, warps, st);
-    case 812: return launch_walk_t<8, 1, 2>(ctx, P, warps, st);
-    case 813: return launch_walk_t<8, 1, 3>(ctx, P, warps, st);
-    case 1621: return launch_walk_t<16, 2, 1>(ctx, P, warps, st);
-    case 1622: return launch_walk_t<16, 2, 2>(ctx, P, warps, st);
-    case 1623: return launch_walk_t<16, 2, 3>(ctx, P, warps, st);
-    case 1211: return launch_walk_t<12, 1, 1>(ctx, P, warps, st);
-    case 1212: return launch_walk_t<12, 1, 2>(ctx, P, warps, st);
-    case 1221: return launch_walk_t<12, 2, 1>(ctx, P, warps, st);
-    case 1222: return launch_walk_t<12, 2, 2>(ctx, P, warps, st);
-    case 1611: return launch_walk_t<16, 1, 1>(ctx, P, warps, st);
-    case 1612: return launch_walk_t<16, 1, 2>(ctx, P, warps, st);
-    default: return LABS_ERR_INVALID_ARG;
+  if (s == LABS_OK) {
+    walk_init_kernel<<<1, 1, 0, st>>>(stats, P->E_thr_dev, P->len[0].E_thr_value, P->counter);
+    s = cuda_status(cudaGetLastError());
   }
+  if (s == LABS_OK && P->n_items > 0) s = launch_walk(ctx, *P, v, cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8, st);
+  delete P;
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched mixed-length search: every length's sieve bound, then one persistent walk launch over all
+// (length, walk) items; the sequence is captured once into a CUDA graph and replayed.  The tile variant
+// (words per thread) and the walks per CTA come from a timing autotuner cached per (length set, SMs).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+uint64_t mix_key(uint64_t h, uint64_t v) { return sm64_at(h ^ v, 0x5EED); }
+
+// Issues the whole batched step on `st`.  blocks > 0: the walk grid was sized beforehand, so nothing
+// but stream work is issued (capturable); blocks == 0: the walk kernel is configured here.
+int issue_batch(labs_ctx* ctx, const labs_batch_cfg* cfg, const std::vector<LenSpec>& lens, const Variant& v,
+                int warps, const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                int32_t* thr, labs_walk_stats* stats, unsigned long long* counter, int64_t flip_budget,
+                bool thresholds, long long blocks, cudaStream_t st) {
+  WalkParams* P = new (std::nothrow) WalkParams();
+  if (!P) return LABS_ERR_NOMEM;
+  base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, flip_budget, cfg->seed, cfg->E_target,
+              prefixes, out, walk_stats, stats, counter);
+  if (!fill_params(*P, lens, v)) {
+    delete P;
+    return LABS_ERR_INVALID_ARG;
+  }
+  P->E_thr_dev = thr;
+  int s = LABS_OK;
+  if (thresholds) {
+    for (size_t i = 0; i < lens.size() && s == LABS_OK; i++)
+      s = launch_sample_threshold(ctx, lens[i].L, lens[i].skew, lens[i].p, prefixes, n_prefix, P->prefix_words,
+                                  cfg->seed, cfg->n_thresh_samples, cfg->thresh_rank, thr + i, nullptr, st);
+  }
+  if (s == LABS_OK) {
+    walk_init_kernel<<<1, 1, 0, st>>>(stats, thr, 0, counter);
+    s = cuda_status(cudaGetLastError());
+  }
+  if (s == LABS_OK && P->n_items > 0) {
+    if (blocks > 0)
+      s = walk_variant(ctx, *P, v, warps, st, false, &blocks);
+    else
+      s = launch_walk(ctx, *P, v, warps, st);
+  }
+  delete P;
+  return s;
+}
+
+}  // namespace
+
+int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
+                          const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                          int32_t* E_thr_out, labs_walk_stats* stats, cudaStream_t st) {
+  std::vector<LenSpec> lens;
+  int64_t begin = 0;
+  for (int i = 0; i < cfg->n_len; i++) {
+    const int L = lengths[i];
+    const int skew = L & 1;
+    lens.push_back({L, skew, skew ? cfg->p : 0, cfg->T_i, walks[i], 0});
+    begin += walks[i];
+  }
+  // workspace first (nothing below may allocate once a capture has begun)
+  char* w = static_cast<char*>(ws_get(ctx, kWsWalkCounters, 256));
+  int32_t* thr = E_thr_out ? E_thr_out : static_cast<int32_t*>(ws_get(ctx, kWsBatchThresholds, sizeof(int32_t) * kMaxLens));
+  if (!w || !thr) return LABS_ERR_NOMEM;
+  if (!ws_get(ctx, kWsThreshSamples, sizeof(int32_t) * (size_t)cfg->n_thresh_samples) ||
+      !ws_get(ctx, kWsThreshHist, sizeof(unsigned) * 2 * kHistBins + 64))
+    return LABS_ERR_NOMEM;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(w);
+
+  // ---- variant and walks per CTA: given, or timed
+  Variant v{0, 0};
+  int warps = cfg->warps_per_cta;
+  uint64_t tkey = (uint64_t)ctx->num_sms;
+  for (const LenSpec& s : lens) tkey = mix_key(tkey, ((uint64_t)s.L << 40) ^ (uint64_t)s.walks);
+  tkey = mix_key(tkey, ((uint64_t)cfg->tile_m << 8) ^ (uint64_t)warps);
+  bool cached = false;
+  for (int i = 0; i < ctx->n_tuned; i++)
+    if (ctx->tuned_key[i] == tkey) {
+      v = {ctx->tuned[i][0], ctx->tuned[i][1]};
+      warps = ctx->tuned[i][2];
+      cached = true;
+    }
+  if (!cached) {
+    std::vector<Variant> vs;
+    for (const Variant& c : kVariants) {
+      if (cfg->tile_m && c.M != cfg->tile_m) continue;
+      bool ok = true;
+      for (const LenSpec& s : lens) {
+        int np = passes_for(s.L, s.skew, s.p, c);
+        ok &= np >= 1 && np <= kMaxPasses;
+      }
+      if (ok) vs.push_back(c);
+    }
+    if (vs.empty()) return LABS_ERR_INVALID_ARG;
+    std::vector<int> wps = warps > 0 ? std::vector<int>{warps} : std::vector<int>{4, 8};
+    if (vs.size() * wps.size() == 1) {
+      v = vs[0];
+      warps = wps[0];
+    } else {
+      // trial: every length with 1/16 of its walks (at least one), 512 flips each, thresholds off
+      std::vector<LenSpec> trial = lens;
+      for (LenSpec& s : trial) s.walks = std::max<int64_t>(1, s.walks / 16);
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      float best_ms = 0;
+      for (const Variant& c : vs)
+        for (int wp : wps) {
+          cudaEventRecord(e0, st);
+          int s = issue_batch(ctx, cfg, trial, c, wp, prefixes, n_prefix, out, nullptr, thr, stats, counter,
+                              std::min<int64_t>(cfg->flip_budget, 512), false, 0, st);
+          cudaEventRecord(e1, st);
+          if (s != LABS_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (v.M == 0 || ms < best_ms) {
+            best_ms = ms;
+            v = c;
+            warps = wp;
+          }
+        }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (v.M == 0) return LABS_ERR_CUDA;
+    }
+    if (ctx->n_tuned < kMaxTuned) {
+      ctx->tuned_key[ctx->n_tuned] = tkey;
+      ctx->tuned[ctx->n_tuned][0] = v.M;
+      ctx->tuned[ctx->n_tuned][1] = v.H;
+      ctx->tuned[ctx->n_tuned][2] = warps;
+      ctx->n_tuned++;
+    }
+  }
+  // kernel attributes and grid size before any capture
+  long long blocks = 0;
+  {
+    WalkParams* P = new (std::nothrow) WalkParams();
+    if (!P) return LABS_ERR_NOMEM;
+    fill_params(*P, lens, v);
+    int s = walk_variant(ctx, *P, v, warps, st, true, &blocks);
+    delete P;
+    if (s != LABS_OK) return s;
+  }
+  if (!cfg->use_graph)
+    return issue_batch(ctx, cfg, lens, v, warps, prefixes, n_prefix, out, walk_stats, thr, stats, counter,
+                       cfg->flip_budget, true, blocks, st);
+
+  // ---- CUDA graph: capture once per (configuration, buffers), replay afterwards
+  uint64_t gkey = tkey;
+  gkey = mix_key(gkey, ((uint64_t)v.M << 32) ^ ((uint64_t)v.H << 16) ^ (uint64_t)warps);
+  gkey = mix_key(gkey, (uint64_t)cfg->flip_budget ^ ((uint64_t)cfg->R << 48));
+  gkey = mix_key(gkey, cfg->seed);
+  gkey = mix_key(gkey, ((uint64_t)cfg->p << 32) ^ ((uint64_t)cfg->bloom_log2 << 16) ^ (uint64_t)cfg->bloom_k);
+  gkey = mix_key(gkey, ((uint64_t)cfg->T_i << 32) ^ (uint32_t)cfg->E_target);
+  gkey = mix_key(gkey, (uint64_t)cfg->n_thresh_samples ^ ((uint64_t)cfg->thresh_rank << 40));
+  const void* bufs[] = {prefixes, out, walk_stats, thr, stats, w, ctx->ws[kWsThreshSamples], ctx->ws[kWsThreshHist]};
+  for (const void* ptr : bufs) gkey = mix_key(gkey, (uint64_t)(uintptr_t)ptr);
+  gkey = mix_key(gkey, (uint64_t)n_prefix ^ ((uint64_t)blocks << 32));
+  if (!ctx->graph_exec || ctx->graph_key != gkey) {
+    if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return LABS_ERR_CUDA;
+    if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return LABS_ERR_CUDA;
+    int s = issue_batch(ctx, cfg, lens, v, warps, prefixes, n_prefix, out, walk_stats, thr, stats, counter,
+                        cfg->flip_budget, true, blocks, ctx->capture_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (s != LABS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return LABS_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return LABS_ERR_CUDA;
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = ex;
+    ctx->graph_key = gkey;
+  }
+  return cuda_status(cudaGraphLaunch(ctx->graph_exec, st));
 }
 
 }  // namespace labsg

@@ -53,6 +53,7 @@ def test_struct_layouts_match_header():
     from paper_2409_07222_gb300 import _lib, CANDIDATE_DTYPE, WALK_STATS_DTYPE
 
     assert ctypes.sizeof(_lib.WalkCfg) == 104
+    assert ctypes.sizeof(_lib.BatchCfg) == 72
     assert CANDIDATE_DTYPE.itemsize == 96 and WALK_STATS_DTYPE.itemsize == 48
 
 

@@ -198,3 +198,67 @@ def test_walks_shard_offset_and_ragged_counts(lg):
     pre = inp.distinct_prefixes(256, p, seed=2409)
     cand, ws, _ = run_walks(lg, L, True, p, pre, 37, 150, 64, seed=3, R=16, walk_begin=1000, warps=3)
     compare_walks(cand, ws, L, True, p, pre, 37, 150, 64, 3, 16, walk_begin=1000)
+
+
+# ------------------------------------------------------------------------------------------------
+# labs_batched_search (mixed lengths, one persistent launch, CUDA graph, autotuner)
+# ------------------------------------------------------------------------------------------------
+def _batch_vs_oracle(lg, lengths, walks, p, budget, T_i, seed, R, E_target=-(2**31), **kw):
+    pre = inp.distinct_prefixes(32, p, seed=7) if p else np.zeros(1, dtype=np.uint64)
+    cfg = lg.make_batch_cfg(len(lengths), p=p, flip_budget=budget, seed=seed, R=R, T_i=T_i, n_thresh_samples=2000,
+                            thresh_rank=20, E_target=E_target, **kw)
+    res = lg.labs_batched_search(cfg, lengths, walks, pre)
+    torch.cuda.synchronize()
+    cand, ws, thr, st = res
+    total = int(np.sum(walks))
+    cand = lg.candidates_numpy(cand, total, R)
+    ws = ws.cpu().numpy()
+    thr = thr.cpu().numpy()
+    off = 0
+    for L, n, t in zip(lengths, walks, thr):
+        skew = L % 2 == 1
+        pl = p if skew else 0
+        pre_l = pre if skew else np.zeros(1, dtype=np.uint64)
+        thr_o = oracle.threshold(L, skew, pl, pre_l, seed, 2000, 20)
+        assert int(t) == thr_o, L
+        oc, ost = oracle.walk_search(L, skew, pl, pre_l, n, budget, T_i if T_i > 0 else 4 * (L + 1), seed, R=R,
+                                     E_thr=thr_o, n_threads=8)
+        for f in ("E", "walk", "step", "fp", "seq"):
+            assert np.array_equal(cand[off:off + n][f], oc[f]), (L, f)
+        assert np.array_equal(ws[off:off + n, :5], ost), L
+        off += n
+    assert lg.stats_numpy(st)["flips"] == total * budget
+    return res, cfg, pre
+
+
+def test_batched_mixed_lengths_graph_replay(lg):
+    lengths = [451, 452, 13, 14, 101, 527, 526]
+    walks = [6, 4, 9, 5, 7, 3, 2]
+    res, cfg, pre = _batch_vs_oracle(lg, lengths, walks, p=5, budget=250, T_i=90, seed=2410, R=8)
+    before = [x.clone() if x is not None else None for x in res]
+    lg.labs_batched_search(cfg, lengths, walks, pre, out=res)  # replay of the captured graph
+    torch.cuda.synchronize()
+    for a, b in zip(before, res):
+        if a is not None:
+            assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("tile_m,warps", [(8, 4), (16, 8), (12, 2)])
+def test_batched_fixed_variants_no_graph(lg, tile_m, warps):
+    _batch_vs_oracle(lg, [450, 451, 21], [5, 6, 11], p=8, budget=180, T_i=0, seed=3, R=4,
+                     tile_m=tile_m, warps_per_cta=warps, use_graph=False)
+
+
+def test_batched_target_hits(lg):
+    # the first flip count reaching E <= E_target is reported per walk
+    lengths, walks = [101], [16]
+    pre = inp.distinct_prefixes(32, 8, seed=7)
+    cfg = lg.make_batch_cfg(1, p=8, flip_budget=400, seed=5, R=4, T_i=0, n_thresh_samples=500, thresh_rank=5,
+                            E_target=700)
+    cand, ws, thr, st = lg.labs_batched_search(cfg, lengths, walks, pre)
+    ws = ws.cpu().numpy()
+    oc, ost = oracle.walk_search(101, True, 8, pre, 16, 400, 408, 5, R=4, E_thr=int(thr.cpu()[0]), n_threads=8)
+    assert np.array_equal(ws[:, :5], ost)
+    hit = ws[:, 5]
+    assert np.all((hit == -1) | ((hit >= 1) & (hit <= 400)))
+    assert np.all((hit >= 0) == (ost[:, 4] <= 700))
