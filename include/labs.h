@@ -215,6 +215,55 @@ int labs_sample_threshold_noalloc(int L, int skew, int p, const uint64_t* prefix
                                   int64_t n_samples, int64_t rank, int32_t* E_thr_out, void* stream);
 
 /*
+ * Step 2: Algorithm 2 (priority-queue refinement over the unrestricted space) in batch-synchronous form.
+ * Readings where the paper gives no value or is ambiguous:
+ *  - keys are (E, fp) compared lexicographically; the open set holds at most `cap` entries;
+ *  - a round pops the b = min(B, open, budget left) smallest keys and scans every single-flip neighbour of
+ *    each (all L positions), skipping neighbours whose fingerprint is in the visited set H;
+ *  - the round's survivors are ordered by (E', fp', pop order, position), equal (E', fp') kept once;
+ *  - the open set becomes the cap smallest keys of (rest of open set) u survivors; H receives exactly the
+ *    admitted survivors;
+ *  - the best improves on a strict E' < E_best (to the smallest survivor key); u counts pops since the
+ *    last improvement; rotations (MAKE_ROTATIONS, T_r) are not applied.
+ * With B = 1 and a cap never reached this is Algorithm 2 step by step.
+ */
+typedef struct {
+  int32_t L;              /* 2..576 */
+  int32_t B;              /* pops per round, 1..8192 */
+  int64_t cap;            /* open-set capacity, 1..2^24 */
+  int32_t H_log2;         /* visited set: 2^H_log2 slots of 8 bytes, 10..31; it must stay <= 3/4 full */
+  int32_t T_r;            /* rotations: must be 0 */
+  int64_t max_expansions; /* pops in total */
+  int64_t T_u;            /* stop after T_u pops without improvement; <= 0: no limit */
+} labs_pq_cfg;
+
+typedef struct {
+  int64_t expansions;   /* nodes popped and scanned */
+  int64_t rounds;
+  int64_t survivors;    /* distinct neighbours not in H, summed over rounds */
+  int64_t admitted;     /* survivors that entered the open set (and H) */
+  int64_t evicted;      /* open-set entries pushed out by the capacity */
+  int64_t h_size;       /* fingerprints in H at the end */
+  int64_t improvements; /* rounds that improved the best */
+  uint64_t best_fp;
+  int32_t stop_reason;  /* 1 expansion budget, 2 open set empty, 3 T_u */
+  int32_t status;       /* LABS_OK, or LABS_ERR_CAPACITY if H filled past 3/4 (the search stops there) */
+} labs_pq_stats;
+
+/*
+ * labs_pq_refine -- runs Algorithm 2 from n_seeds candidates (for instance the step-1 sieve output) on
+ * the device until a stop condition holds.  The host drives the rounds and polls a device flag, so the
+ * call returns after `stream` has finished the refinement.
+ *   seeds [n_seeds][W] uint64 DEVICE; best_seq [W] uint64 DEVICE; best_E int32 DEVICE; stats DEVICE.
+ *   Workspace: two open-set buffers (cap * (12 + 8W) bytes each), the visited set (8 * 2^H_log2 bytes),
+ *   survivor and sort buffers (about 60 * B * L bytes).
+ * Errors: LABS_ERR_INVALID_ARG on a bad configuration (T_r != 0 included), LABS_ERR_NOMEM if the
+ * workspace cannot be allocated.
+ */
+int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
+                   int32_t* best_E, labs_pq_stats* stats, void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

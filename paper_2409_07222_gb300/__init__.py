@@ -17,11 +17,16 @@ from ._lib import (INT32_MAX, INT32_MIN, LABS_AUTO_THRESHOLD, LABS_MAX_L, LABS_M
 CANDIDATE_DTYPE = np.dtype(
     [("E", "<i4"), ("walk", "<u4"), ("step", "<u4"), ("pad", "<u4"), ("fp", "<u8"), ("seq", "<u8", (LABS_MAX_W,))]
 )
+PQ_STATS_DTYPE = np.dtype(
+    [("expansions", "<i8"), ("rounds", "<i8"), ("survivors", "<i8"), ("admitted", "<i8"), ("evicted", "<i8"),
+     ("h_size", "<i8"), ("improvements", "<i8"), ("best_fp", "<u8"), ("stop_reason", "<i4"), ("status", "<i4")]
+)
 WALK_STATS_DTYPE = np.dtype(
     [("flips", "<i8"), ("segments", "<i8"), ("bloom_skips", "<i8"), ("dead_ends", "<i8"), ("E_thr", "<i4"),
      ("best_E", "<i4"), ("status", "<i4"), ("reserved", "<i4")]
 )
 assert CANDIDATE_DTYPE.itemsize == _lib.CANDIDATE_BYTES and WALK_STATS_DTYPE.itemsize == _lib.WALK_STATS_BYTES
+assert PQ_STATS_DTYPE.itemsize == _lib.PQ_STATS_BYTES
 
 _ctxs = {}
 
@@ -191,6 +196,28 @@ def labs_batched_search(cfg, lengths, walks, prefixes, device=None, out=None, wa
                                           ctypes.c_void_p(Ws.ctypes.data), _ptr(pre), pre.shape[0], _ptr(cand),
                                           _ptr(ws), _ptr(thr), _ptr(st), _stream(dev)), "labs_batched_search")
     return out
+
+
+def labs_pq_refine(L, seeds, B=4096, cap=1 << 22, H_log2=24, max_expansions=10**7, T_u=0, device=None):
+    """Algorithm 2 on the device from packed seed sequences (device int64 [n, W]).
+
+    Returns (best words int64 [W], best E int32 [1], stats uint8 [72]); ``pq_stats_numpy`` decodes stats.
+    """
+    s = _dev_words(seeds, L)
+    dev = s.device
+    cfg = _lib.PqCfg()
+    cfg.L, cfg.B, cfg.cap, cfg.H_log2, cfg.T_r = L, B, cap, H_log2, 0
+    cfg.max_expansions, cfg.T_u = max_expansions, T_u
+    best = torch.empty(words_per_seq(L), dtype=torch.int64, device=dev)
+    bE = torch.empty(1, dtype=torch.int32, device=dev)
+    st = torch.empty(_lib.PQ_STATS_BYTES, dtype=torch.uint8, device=dev)
+    _lib.check(load().labs_pq_refine(context(dev.index), ctypes.byref(cfg), _ptr(s), s.shape[0], _ptr(best), _ptr(bE),
+                                     _ptr(st), _stream(dev)), "labs_pq_refine")
+    return best, bE, st
+
+
+def pq_stats_numpy(st):
+    return st.cpu().numpy().view(PQ_STATS_DTYPE)[0]
 
 
 def labs_skew_search_host(cfg, prefixes_host, device=None):

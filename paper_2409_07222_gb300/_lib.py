@@ -35,6 +35,7 @@ SIGNATURES = {
     "labs_skew_exhaustive": (_ci, [_P, _ci, _ci, _u64, _P, _P, _P, _P, _P]),
     "labs_sample_threshold_noalloc": (_ci, [_ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P]),
     "labs_batched_search": (_ci, [_P, _P, _P, _P, _P, _ci, _P, _P, _P, _P, _P]),
+    "labs_pq_refine": (_ci, [_P, _P, _P, _ci, _P, _P, _P, _P]),
 }
 
 
@@ -63,7 +64,17 @@ class BatchCfg(ctypes.Structure):
     ]
 
 
+class PqCfg(ctypes.Structure):
+    """labs_pq_cfg (include/labs.h)."""
+
+    _fields_ = [
+        ("L", _i32), ("B", _i32), ("cap", _i64), ("H_log2", _i32), ("T_r", _i32),
+        ("max_expansions", _i64), ("T_u", _i64),
+    ]
+
+
 WALK_STATS_BYTES = 48  # labs_walk_stats
+PQ_STATS_BYTES = 72    # labs_pq_stats
 CANDIDATE_BYTES = 96   # labs_candidate
 
 _lib = None

@@ -185,6 +185,20 @@ int labs_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t*
                                       (cudaStream_t)stream);
 }
 
+int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
+                   int32_t* best_E, labs_pq_stats* stats, void* stream) {
+  if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->B < 1 || cfg->B > 8192 || cfg->cap < 1 ||
+      cfg->cap > (1ll << 24) || cfg->H_log2 < 10 || cfg->H_log2 > 31 || cfg->T_r != 0 || cfg->max_expansions < 0 ||
+      n_seeds < 1)
+    return LABS_ERR_INVALID_ARG;
+  if (!seeds || !aligned8(seeds) || !best_seq || !aligned8(best_seq) || !best_E || !aligned4(best_E) || !stats ||
+      !aligned8(stats))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_pq_refine(ctx, cfg, seeds, n_seeds, best_seq, best_E, stats, (cudaStream_t)stream);
+}
+
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
   if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;

@@ -47,6 +47,8 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
 int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
                           const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
                           int32_t* E_thr_out, labs_walk_stats* stats, cudaStream_t st);
+int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
+                     int32_t* best_E, labs_pq_stats* stats, cudaStream_t st);
 int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                            uint64_t* out_argmin_free, uint64_t* out_argmin_seq, cudaStream_t st);
 

@@ -1,0 +1,680 @@
+// pq.cu -- step 2 of the dual-step search: Algorithm 2's priority-queue refinement over the unrestricted
+// space, in batch-synchronous form (labs_pq_refine).
+//
+// GB300 mapping.  The paper runs one priority queue per candidate in Rust on CPU cores; here one open
+// set of the cap smallest (E, fp) keys lives in HBM as a sorted array (double-buffered), and a round
+//   expand   -- one warp per popped node: its correlation table, the all-position dp4a scan and a
+//               visited-set lookup per neighbour, written to a dense [pop][position] survivor array;
+//   compact  -- stable compaction of the survivors (pop order, position);
+//   sort     -- stable LSD radix sort by fingerprint bytes then energy bytes: order (E', fp', pop, pos);
+//   dedup    -- stable compaction keeping the first of equal (E', fp');
+//   best     -- strict improvement test on the smallest survivor;
+//   merge    -- merge path of (open set minus the pops) with the survivors into the other buffer, cut at
+//               cap; admitted survivors enter the visited set (open addressing, atomicCAS);
+// keeps every result identical to the sequential definition whatever order threads run in.
+#include <algorithm>
+#include <new>
+
+#include "labs_core.cuh"
+#include "labs_internal.h"
+
+namespace labsg {
+namespace {
+
+constexpr uint64_t kEmptyKey = ~0ull;  // free slot of the visited set (fp == ~0 is tracked by a flag)
+constexpr int kPqWarps = 4;
+constexpr int kPqM = 8;
+constexpr int kTile = 1024;  // elements per block in the compaction and sort kernels (256 threads x 4)
+constexpr int kMaxProbe = 1 << 20;
+
+struct PqState {
+  long long nP, nS, nU, n_dense;
+  long long expansions, rounds, survivors, admitted, evicted, h_size, improvements, u;
+  unsigned long long best_fp;
+  int b, cur, stop, best_E, error, h_has_empty, pad0, pad1;
+};
+
+struct PqBufs {
+  int L, W, B, H_log2;
+  long long cap, max_exp, T_u;
+  int32_t* PE[2];
+  uint64_t* Pfp[2];
+  uint64_t* Pseq[2];
+  int32_t* dE;  // dense survivors [B * L] (or seeds)
+  uint64_t* dfp;
+  int32_t* sE[2];  // sort ping-pong
+  uint64_t* sfp[2];
+  int32_t* sidx[2];
+  int32_t* uE;  // unique survivors
+  uint64_t* ufp;
+  int32_t* uidx;
+  unsigned* counts;  // 256 * blocks
+  unsigned* bsum;    // per-block counts (+ total)
+  uint64_t* H;
+  uint64_t* ztab;
+  PqState* st;
+  uint64_t* best_seq;
+  const uint64_t* seeds;
+};
+
+__device__ __forceinline__ uint64_t h_slot(uint64_t fp, int log2) { return (fp * kGamma) >> (64 - log2); }
+
+__device__ __forceinline__ bool h_contains(const PqBufs& b, uint64_t fp) {
+  if (fp == kEmptyKey) return b.st->h_has_empty != 0;
+  const uint64_t mask = (1ull << b.H_log2) - 1;
+  uint64_t s = h_slot(fp, b.H_log2);
+  for (int it = 0; it < kMaxProbe; it++) {
+    const uint64_t v = b.H[s];
+    if (v == fp) return true;
+    if (v == kEmptyKey) return false;
+    s = (s + 1) & mask;
+  }
+  atomicExch(&b.st->error, 1);  // probe limit: the set is too full (reported as a capacity error)
+  return true;
+}
+
+__device__ __forceinline__ void h_insert(const PqBufs& b, uint64_t fp) {
+  if (fp == kEmptyKey) {
+    if (atomicExch(&b.st->h_has_empty, 1) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), 1ull);
+    return;
+  }
+  const uint64_t mask = (1ull << b.H_log2) - 1;
+  uint64_t s = h_slot(fp, b.H_log2);
+  for (int it = 0; it < kMaxProbe; it++) {
+    const unsigned long long old =
+        atomicCAS(reinterpret_cast<unsigned long long*>(&b.H[s]), (unsigned long long)kEmptyKey, fp);
+    if (old == kEmptyKey) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), 1ull);
+      return;
+    }
+    if (old == fp) return;
+    s = (s + 1) & mask;
+  }
+  atomicExch(&b.st->error, 1);
+}
+
+__device__ __forceinline__ bool key_lt(int Ea, uint64_t fa, int Eb, uint64_t fb) {
+  return Ea < Eb || (Ea == Eb && fa < fb);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Set-up kernels
+// ---------------------------------------------------------------------------------------------
+__global__ void pq_ztab_kernel(uint64_t* ztab, int L) {
+  const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)L, 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) ztab[i] = zobrist(zk, i + 1);
+}
+
+__global__ void pq_state_init_kernel(PqState* st, long long n_seeds) {
+  PqState z{};
+  z.n_dense = n_seeds;
+  z.best_E = INT32_MAX;
+  z.best_fp = ~0ull;
+  *st = z;
+}
+
+// One warp per seed: energy over all lags and the fingerprint, into the dense arrays.
+__global__ void __launch_bounds__(32 * kPqWarps) pq_seed_kernel(PqBufs b, int n_seeds) {
+  __shared__ uint32_t bits_all[kPqWarps][kBitWords];
+  uint32_t* bits = bits_all[threadIdx.x >> 5];
+  const int lane = lane_id();
+  for (int q = blockIdx.x * kPqWarps + (threadIdx.x >> 5); q < n_seeds; q += gridDim.x * kPqWarps) {
+    const uint64_t* src = b.seeds + (size_t)q * b.W;
+    if (lane < kBitWords) {
+      const int W32 = (b.L + 31) >> 5;
+      uint32_t v = 0;
+      if (lane < W32) {
+        uint64_t x = src[lane >> 1];
+        v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+        int rem = b.L - 32 * lane;
+        if (rem < 32) v &= (1u << rem) - 1u;
+      }
+      bits[lane] = v;
+    }
+    __syncwarp();
+    int e = 0;
+    for (int k = lane + 1; k < b.L; k += 32) {
+      const int c = corr_lag(bits, b.L, k);
+      e += c * c;
+    }
+    e = warp_sum_i32(e);
+    uint64_t h = 0;
+    for (int i = lane + 1; i <= b.L; i += 32)
+      if (!((bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u)) h ^= b.ztab[i - 1];
+    h = warp_xor_u64(h);
+    if (lane == 0) {
+      b.dE[q] = e;
+      b.dfp[q] = h;
+    }
+    __syncwarp();
+  }
+}
+
+// Admits the sorted, de-duplicated seeds: the cap smallest become the open set and enter H.
+__global__ void pq_seed_admit_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = min((long long)st->nU, b.cap);
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    const int q = b.uidx[o];
+    b.PE[0][o] = b.uE[o];
+    b.Pfp[0][o] = b.ufp[o];
+    for (int t = 0; t < b.W; t++) b.Pseq[0][o * b.W + t] = b.seeds[(size_t)q * b.W + t];
+    h_insert(b, b.ufp[o]);
+  }
+}
+
+__global__ void pq_seed_finish_kernel(PqBufs b) {
+  PqState* st = b.st;
+  st->nP = min((long long)st->nU, b.cap);
+  st->cur = 0;
+  if (st->nU > 0) {
+    st->best_E = b.uE[0];
+    st->best_fp = b.ufp[0];
+    const int q = b.uidx[0];
+    for (int t = 0; t < b.W; t++) b.best_seq[t] = b.seeds[(size_t)q * b.W + t];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Round kernels
+// ---------------------------------------------------------------------------------------------
+__global__ void pq_round_begin_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (!st->stop) {
+    if (st->error)
+      st->stop = 4;
+    else if (st->expansions >= b.max_exp)
+      st->stop = 1;
+    else if (st->nP == 0)
+      st->stop = 2;
+    else if (b.T_u > 0 && st->u >= b.T_u)
+      st->stop = 3;
+  }
+  if (st->stop) {
+    st->b = 0;
+    st->n_dense = 0;
+    return;
+  }
+  long long bb = min((long long)b.B, st->nP);
+  bb = min(bb, b.max_exp - st->expansions);
+  st->b = (int)bb;
+  st->n_dense = bb * b.L;
+}
+
+// One warp per popped node: Delta E of all L single flips, visited-set test, dense survivor output.
+__global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layout ly) {
+  __shared__ ScanSmem slabs[kPqWarps];
+  ScanSmem& sm = slabs[threadIdx.x >> 5];
+  const int lane = lane_id();
+  const PqState* st = b.st;
+  const int nb = st->b;
+  const int cur = st->cur;
+  const int32_t* PE = b.PE[cur];
+  const uint64_t* Pfp = b.Pfp[cur];
+  const uint64_t* Pseq = b.Pseq[cur];
+  for (int q = blockIdx.x * kPqWarps + (threadIdx.x >> 5); q < nb; q += gridDim.x * kPqWarps) {
+    load_bits(sm, Pseq + (size_t)q * b.W, b.L);
+    build_table(sm, ly);
+    const bool fast = pack_c8(sm);
+    const int SC = table_sum(sm);
+    build_bytes(sm, ly);
+    const int E = PE[q];
+    const uint64_t fp = Pfp[q];
+    for (int base = 0; base < ly.n_tiles; base += 32) {
+      const int tau = base + lane;
+      if (tau < ly.n_tiles) {
+        int cls, q0;
+        tile_of(ly, tau, cls, q0);
+        int acc[kPqM];
+        if (fast)
+          scan_tile<kPqM, false>(sm, ly, cls, q0, acc);
+        else
+          scan_tile<kPqM, true>(sm, ly, cls, q0, acc);
+#pragma unroll
+        for (int j = 0; j < kPqM; j++) {
+          const SlotInfo si = slot_info(ly, cls, q0 + j);
+          if (!si.active) continue;
+          const int P = p_from_scratch(sm, ly, cls, q0 + j, si);
+          const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
+          const uint64_t nfp = fp ^ b.ztab[si.m - 1];
+          const size_t di = (size_t)q * b.L + (si.m - 1);
+          b.dE[di] = h_contains(b, nfp) ? INT32_MAX : E + d;
+          b.dfp[di] = nfp;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Stable compaction (MODE 0: dense survivors -> sort input; MODE 1: sorted -> first of equal keys)
+// and stable LSD radix sort.  Element e of block k is k*1024 + w*128 + r*32 + lane (warp w, round r):
+// increasing e is increasing (w, r, lane), so block-local ranks built warp by warp, round by round,
+// are stable.
+// ---------------------------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ long long compact_n(const PqBufs& b) {
+  return MODE == 0 ? b.st->n_dense : b.st->nS;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool compact_flag(const PqBufs& b, long long e) {
+  if (MODE == 0) return b.dE[e] != INT32_MAX;
+  return e == 0 || b.sE[0][e] != b.sE[0][e - 1] || b.sfp[0][e] != b.sfp[0][e - 1];
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) compact_count_kernel(PqBufs b) {
+  const long long n = compact_n<MODE>(b);
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= n) {  // blocks past this round's count still publish a zero for the scan
+    if (threadIdx.x == 0) b.bsum[blockIdx.x] = 0;
+    return;
+  }
+  int c = 0;
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
+    if (e < n && compact_flag<MODE>(b, e)) c++;
+  }
+  c = __reduce_add_sync(kFull, c);
+  __shared__ int ws[8];
+  if (lane_id() == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < 8; w++) t += ws[w];
+    b.bsum[blockIdx.x] = t;
+  }
+}
+
+// Single block: exclusive scan of a[0..n) in place; *total receives the sum.
+__global__ void __launch_bounds__(1024) scan_kernel(unsigned* a, long long n, long long* total) {
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const long long chunk = (n + 1023) / 1024;
+  const long long lo = t * chunk, hi = min(n, lo + chunk);
+  unsigned long long s = 0;
+  for (long long i = lo; i < hi; i++) s += a[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
+    unsigned long long v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = t ? part[t - 1] : 0;
+  for (long long i = lo; i < hi; i++) {
+    const unsigned v = a[i];
+    a[i] = (unsigned)run;
+    run += v;
+  }
+  if (t == 1023 && total) *total = (long long)part[1023];
+}
+
+// Number of blocks a compaction or sort over n elements uses.
+__device__ __forceinline__ long long tiles_of(long long n) { return (n + kTile - 1) / kTile; }
+
+template <int MODE>
+__global__ void __launch_bounds__(256) compact_scatter_kernel(PqBufs b) {
+  const long long n = compact_n<MODE>(b);
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= n) return;
+  __shared__ int wcount[8][4];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  bool fl[4];
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + w * 128 + r * 32 + lane;
+    fl[r] = e < n && compact_flag<MODE>(b, e);
+    const unsigned m = __ballot_sync(kFull, fl[r]);
+    if (lane == 0) wcount[w][r] = __popc(m);
+  }
+  __syncthreads();
+  int off = b.bsum[blockIdx.x];
+  for (int ww = 0; ww < w; ww++)
+    for (int r = 0; r < 4; r++) off += wcount[ww][r];
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + w * 128 + r * 32 + lane;
+    const unsigned m = __ballot_sync(kFull, fl[r]);
+    if (fl[r]) {
+      const long long o = off + __popc(m & ((1u << lane) - 1u));
+      if (MODE == 0) {
+        b.sE[0][o] = b.dE[e];
+        b.sfp[0][o] = b.dfp[e];
+        b.sidx[0][o] = (int32_t)e;
+      } else {
+        b.uE[o] = b.sE[0][e];
+        b.ufp[o] = b.sfp[0][e];
+        b.uidx[o] = b.sidx[0][e];
+      }
+    }
+    off += __popc(m);
+  }
+}
+
+// Radix digit of element e of buffer `src` at pass `pass` (0..7: fingerprint bytes, 8..11: energy bytes).
+__device__ __forceinline__ unsigned radix_digit(const PqBufs& b, int src, long long e, int pass) {
+  if (pass < 8) return (unsigned)(b.sfp[src][e] >> (8 * pass)) & 255u;
+  return ((unsigned)b.sE[src][e] >> (8 * (pass - 8))) & 255u;
+}
+
+__global__ void __launch_bounds__(256) radix_hist_kernel(PqBufs b, int pass) {
+  const long long n = b.st->nS;
+  const long long nblk = tiles_of(n);
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= n) return;
+  __shared__ unsigned h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int src = pass & 1;
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
+    if (e < n) atomicAdd(&h[radix_digit(b, src, e, pass)], 1u);
+  }
+  __syncthreads();
+  b.counts[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) radix_scan_kernel(PqBufs b) {
+  // exclusive scan over the digit-major counts of this round's block count
+  const long long n = 256 * tiles_of(b.st->nS);
+  __shared__ unsigned long long part[1024];
+  const int t = threadIdx.x;
+  const long long chunk = (n + 1023) / 1024;
+  const long long lo = t * chunk, hi = min(n, lo + chunk);
+  unsigned long long s = 0;
+  for (long long i = lo; i < hi; i++) s += b.counts[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    unsigned long long v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  unsigned long long run = t ? part[t - 1] : 0;
+  for (long long i = lo; i < hi; i++) {
+    const unsigned v = b.counts[i];
+    b.counts[i] = (unsigned)run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) {
+  const long long n = b.st->nS;
+  const long long nblk = tiles_of(n);
+  const long long base = (long long)blockIdx.x * kTile;
+  if (base >= n) return;
+  __shared__ unsigned cnt[8][256];
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  const int src = pass & 1, dst = src ^ 1;
+  for (int d = threadIdx.x; d < 8 * 256; d += 256) (&cnt[0][0])[d] = 0;
+  __syncthreads();
+  unsigned dig[4];
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + w * 128 + r * 32 + lane;
+    dig[r] = e < n ? radix_digit(b, src, e, pass) : 256u;
+    const unsigned peers = __match_any_sync(kFull, dig[r]);
+    if (dig[r] < 256u && lane == __ffs(peers) - 1) cnt[w][dig[r]] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // per digit: exclusive prefix over warps, plus the block's global offset
+    const int d = threadIdx.x;
+    unsigned run = b.counts[(long long)d * nblk + blockIdx.x];
+    for (int ww = 0; ww < 8; ww++) {
+      const unsigned v = cnt[ww][d];
+      cnt[ww][d] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int r = 0; r < 4; r++) {
+    const long long e = base + w * 128 + r * 32 + lane;
+    const unsigned peers = __match_any_sync(kFull, dig[r]);
+    if (dig[r] < 256u) {
+      const unsigned o = cnt[w][dig[r]] + __popc(peers & ((1u << lane) - 1u));
+      b.sE[dst][o] = b.sE[src][e];
+      b.sfp[dst][o] = b.sfp[src][e];
+      b.sidx[dst][o] = b.sidx[src][e];
+    }
+    __syncwarp();
+    if (dig[r] < 256u && lane == __ffs(peers) - 1) cnt[w][dig[r]] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Best, merge, round end
+// ---------------------------------------------------------------------------------------------
+__global__ void pq_best_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (st->b == 0) return;
+  st->survivors += st->nU;
+  if (st->nU > 0 && b.uE[0] < st->best_E) {
+    st->best_E = b.uE[0];
+    st->best_fp = b.ufp[0];
+    const int q = b.uidx[0] / b.L, pos = b.uidx[0] % b.L;
+    const uint64_t* src = b.Pseq[st->cur] + (size_t)q * b.W;
+    for (int t = 0; t < b.W; t++) {
+      uint64_t v = src[t];
+      if (t == (pos >> 6)) v ^= 1ull << (pos & 63);
+      b.best_seq[t] = v;
+    }
+    st->improvements++;
+    st->u = 0;
+  } else {
+    st->u += st->b;
+  }
+}
+
+// Number of open-set (rest) entries among the first o merged outputs.
+__device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
+                                                 const uint64_t* Ufp, long long nU, long long o) {
+  long long lo = max(0ll, o - nU), hi = min(o, nR);
+  while (lo < hi) {
+    const long long mid = (lo + hi) >> 1;
+    const long long ui = o - mid - 1;
+    if (key_lt(RE[mid], Rfp[mid], UE[ui], Ufp[ui]))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
+  const PqState* st = b.st;
+  if (st->b == 0) return;
+  const int cur = st->cur, nxt = cur ^ 1;
+  const long long nb = st->b, nR = st->nP - nb, nU = st->nU;
+  const long long nOut = min(b.cap, nR + nU);
+  const int32_t* RE = b.PE[cur] + nb;
+  const uint64_t* Rfp = b.Pfp[cur] + nb;
+  const uint64_t* Rseq = b.Pseq[cur] + nb * b.W;
+  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nOut; o += (long long)gridDim.x * blockDim.x) {
+    const long long a = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o);
+    const long long ui = o - a;
+    const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
+    if (from_rest) {
+      b.PE[nxt][o] = RE[a];
+      b.Pfp[nxt][o] = Rfp[a];
+      for (int t = 0; t < b.W; t++) b.Pseq[nxt][o * b.W + t] = Rseq[a * b.W + t];
+    } else {
+      const int q = b.uidx[ui] / b.L, pos = b.uidx[ui] % b.L;
+      b.PE[nxt][o] = b.uE[ui];
+      b.Pfp[nxt][o] = b.ufp[ui];
+      const uint64_t* src = b.Pseq[cur] + (size_t)q * b.W;
+      for (int t = 0; t < b.W; t++) {
+        uint64_t v = src[t];
+        if (t == (pos >> 6)) v ^= 1ull << (pos & 63);
+        b.Pseq[nxt][o * b.W + t] = v;
+      }
+      h_insert(b, b.ufp[ui]);
+    }
+  }
+}
+
+__global__ void pq_round_end_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (st->b == 0) return;
+  const int cur = st->cur;
+  const long long nb = st->b, nR = st->nP - nb, nU = st->nU;
+  const long long nOut = min(b.cap, nR + nU);
+  const long long a = merge_split(b.PE[cur] + nb, b.Pfp[cur] + nb, nR, b.uE, b.ufp, nU, nOut);
+  st->admitted += nOut - a;
+  st->evicted += nR - a;
+  st->nP = nOut;
+  st->expansions += nb;
+  st->rounds++;
+  st->cur = cur ^ 1;
+  const long long slots = 1ll << b.H_log2;
+  if (st->h_size * 4 > slots * 3) st->error = 1;
+}
+
+__global__ void pq_write_stats_kernel(PqBufs b, int32_t* best_E, labs_pq_stats* out) {
+  const PqState* st = b.st;
+  *best_E = st->best_E;
+  out->expansions = st->expansions;
+  out->rounds = st->rounds;
+  out->survivors = st->survivors;
+  out->admitted = st->admitted;
+  out->evicted = st->evicted;
+  out->h_size = st->h_size;
+  out->improvements = st->improvements;
+  out->best_fp = st->best_fp;
+  out->stop_reason = st->stop == 4 ? 0 : st->stop;
+  out->status = st->error ? LABS_ERR_CAPACITY : LABS_OK;
+}
+
+// Issues compaction (MODE) over at most `max_n` elements.
+template <int MODE>
+void issue_compact(const PqBufs& b, long long max_n, long long* total, cudaStream_t st) {
+  const long long nblk = std::max(1ll, (max_n + kTile - 1) / kTile);
+  compact_count_kernel<MODE><<<(unsigned)nblk, 256, 0, st>>>(b);
+  scan_kernel<<<1, 1024, 0, st>>>(b.bsum, nblk, total);
+  compact_scatter_kernel<MODE><<<(unsigned)nblk, 256, 0, st>>>(b);
+}
+
+}  // namespace
+
+int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
+                     int32_t* best_E, labs_pq_stats* stats, cudaStream_t st) {
+  const int L = cfg->L, W = (L + 63) / 64;
+  Layout ly;
+  if (!make_layout(ly, L, 0, 0, kPqM)) return LABS_ERR_INVALID_ARG;
+  const long long nmax = std::max<long long>((long long)cfg->B * L, n_seeds);
+  const long long nblk = (nmax + kTile - 1) / kTile;
+  // workspace layout (one region, 256-byte aligned pieces)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t oPE0 = take(4 * cfg->cap), oPE1 = take(4 * cfg->cap);
+  const size_t oPf0 = take(8 * cfg->cap), oPf1 = take(8 * cfg->cap);
+  const size_t oPs0 = take(8 * cfg->cap * W), oPs1 = take(8 * cfg->cap * W);
+  const size_t odE = take(4 * nmax), odf = take(8 * nmax);
+  const size_t osE0 = take(4 * nmax), osE1 = take(4 * nmax), osf0 = take(8 * nmax), osf1 = take(8 * nmax);
+  const size_t osi0 = take(4 * nmax), osi1 = take(4 * nmax);
+  const size_t ouE = take(4 * nmax), ouf = take(8 * nmax), oui = take(4 * nmax);
+  const size_t ocnt = take(4 * 256 * nblk), obs = take(4 * (nblk + 1));
+  const size_t ozt = take(8 * L), ost = take(sizeof(PqState)), obest = take(8 * W);
+  const size_t oH = take(8ull << cfg->H_log2);
+  char* base = static_cast<char*>(ws_get(ctx, kWsPq0, off));
+  if (!base) return LABS_ERR_NOMEM;
+  PqBufs b{};
+  b.L = L;
+  b.W = W;
+  b.B = cfg->B;
+  b.H_log2 = cfg->H_log2;
+  b.cap = cfg->cap;
+  b.max_exp = cfg->max_expansions;
+  b.T_u = cfg->T_u;
+  b.PE[0] = reinterpret_cast<int32_t*>(base + oPE0);
+  b.PE[1] = reinterpret_cast<int32_t*>(base + oPE1);
+  b.Pfp[0] = reinterpret_cast<uint64_t*>(base + oPf0);
+  b.Pfp[1] = reinterpret_cast<uint64_t*>(base + oPf1);
+  b.Pseq[0] = reinterpret_cast<uint64_t*>(base + oPs0);
+  b.Pseq[1] = reinterpret_cast<uint64_t*>(base + oPs1);
+  b.dE = reinterpret_cast<int32_t*>(base + odE);
+  b.dfp = reinterpret_cast<uint64_t*>(base + odf);
+  b.sE[0] = reinterpret_cast<int32_t*>(base + osE0);
+  b.sE[1] = reinterpret_cast<int32_t*>(base + osE1);
+  b.sfp[0] = reinterpret_cast<uint64_t*>(base + osf0);
+  b.sfp[1] = reinterpret_cast<uint64_t*>(base + osf1);
+  b.sidx[0] = reinterpret_cast<int32_t*>(base + osi0);
+  b.sidx[1] = reinterpret_cast<int32_t*>(base + osi1);
+  b.uE = reinterpret_cast<int32_t*>(base + ouE);
+  b.ufp = reinterpret_cast<uint64_t*>(base + ouf);
+  b.uidx = reinterpret_cast<int32_t*>(base + oui);
+  b.counts = reinterpret_cast<unsigned*>(base + ocnt);
+  b.bsum = reinterpret_cast<unsigned*>(base + obs);
+  b.ztab = reinterpret_cast<uint64_t*>(base + ozt);
+  b.st = reinterpret_cast<PqState*>(base + ost);
+  b.best_seq = reinterpret_cast<uint64_t*>(base + obest);
+  b.H = reinterpret_cast<uint64_t*>(base + oH);
+  b.seeds = seeds;
+  PqState* dst = b.st;
+
+  // ---- set-up: visited set, Zobrist keys, seeds sorted by (E, fp, index), de-duplicated, admitted
+  if (cudaMemsetAsync(b.H, 0xff, 8ull << cfg->H_log2, st) != cudaSuccess) return LABS_ERR_CUDA;
+  pq_ztab_kernel<<<(L + 255) / 256, 256, 0, st>>>(b.ztab, L);
+  pq_state_init_kernel<<<1, 1, 0, st>>>(dst, n_seeds);
+  pq_seed_kernel<<<(unsigned)std::min<long long>((n_seeds + kPqWarps - 1) / kPqWarps, ctx->num_sms * 16), 32 * kPqWarps,
+                   0, st>>>(b, n_seeds);
+  auto sort_and_dedup = [&](long long max_n) {
+    const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
+    issue_compact<0>(b, max_n, &dst->nS, st);
+    for (int pass = 0; pass < 12; pass++) {
+      radix_hist_kernel<<<nb, 256, 0, st>>>(b, pass);
+      radix_scan_kernel<<<1, 1024, 0, st>>>(b);
+      radix_scatter_kernel<<<nb, 256, 0, st>>>(b, pass);
+    }
+    issue_compact<1>(b, max_n, &dst->nU, st);
+  };
+  sort_and_dedup(n_seeds);
+  pq_seed_admit_kernel<<<(unsigned)std::min<long long>((std::min<long long>(n_seeds, cfg->cap) + 255) / 256, 4096), 256, 0,
+                         st>>>(b);
+  pq_seed_finish_kernel<<<1, 1, 0, st>>>(b);
+
+  // ---- rounds
+  const long long max_rounds = (cfg->max_expansions + cfg->B - 1) / cfg->B + 1;
+  const unsigned exp_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->B + kPqWarps - 1) / kPqWarps,
+                                                                        (long long)ctx->num_sms * 8));
+  const unsigned merge_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->cap + 255) / 256, 65535));
+  int* hstop = nullptr;
+  if (cudaMallocHost(&hstop, sizeof(int)) != cudaSuccess) return LABS_ERR_NOMEM;
+  int status = LABS_OK;
+  for (long long r = 0; r < max_rounds; r++) {
+    pq_round_begin_kernel<<<1, 1, 0, st>>>(b);
+    pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, st>>>(b, ly);
+    sort_and_dedup((long long)cfg->B * L);
+    pq_best_kernel<<<1, 1, 0, st>>>(b);
+    pq_merge_kernel<<<merge_blocks, 256, 0, st>>>(b);
+    pq_round_end_kernel<<<1, 1, 0, st>>>(b);
+    if (cudaGetLastError() != cudaSuccess) {
+      status = LABS_ERR_CUDA;
+      break;
+    }
+    if ((r & 31) == 31 || r + 1 == max_rounds) {  // poll the stop flag
+      if (cudaMemcpyAsync(hstop, &dst->stop, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) {
+        status = LABS_ERR_CUDA;
+        break;
+      }
+      if (*hstop) break;
+    }
+  }
+  // the last round may end on the budget without a following begin: settle the stop reason
+  pq_round_begin_kernel<<<1, 1, 0, st>>>(b);
+  pq_write_stats_kernel<<<1, 1, 0, st>>>(b, best_E, stats);
+  if (cudaMemcpyAsync(best_seq, b.best_seq, 8 * W, cudaMemcpyDeviceToDevice, st) != cudaSuccess) status = LABS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) status = LABS_ERR_CUDA;
+  cudaFreeHost(hstop);
+  return status;
+}
+
+}  // namespace labsg

@@ -262,3 +262,40 @@ def test_batched_target_hits(lg):
     hit = ws[:, 5]
     assert np.all((hit == -1) | ((hit >= 1) & (hit <= 400)))
     assert np.all((hit >= 0) == (ost[:, 4] <= 700))
+
+
+# ------------------------------------------------------------------------------------------------
+# labs_pq_refine (Algorithm 2, batch-synchronous)
+# ------------------------------------------------------------------------------------------------
+def _pq_compare(lg, L, seeds, cap, B, max_exp, T_u=0, H_log2=20):
+    best, bE, st = lg.labs_pq_refine(L, dev_words(seeds), B=B, cap=cap, H_log2=H_log2, max_expansions=max_exp,
+                                     T_u=T_u)
+    torch.cuda.synchronize()
+    ob, oE, ofp, ost = oracle.pq_refine(L, seeds, cap, B, max_exp, T_u)
+    gs = lg.pq_stats_numpy(st)
+    assert int(bE.cpu()[0]) == oE
+    assert int(gs["best_fp"]) == ofp
+    assert np.array_equal(host_words(best.cpu()), ob)
+    for k in ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements", "stop_reason"):
+        assert int(gs[k]) == ost[k], (k, int(gs[k]), ost[k])
+    assert int(gs["status"]) == 0
+
+
+@pytest.mark.parametrize("L,n_seeds,cap,B,max_exp", [(13, 2, 1 << 14, 1, 200), (13, 3, 1 << 14, 16, 8192),
+                                                     (31, 8, 64, 8, 400), (64, 5, 300, 7, 333), (101, 16, 5000, 32, 700)])
+def test_pq_small(lg, L, n_seeds, cap, B, max_exp):
+    seeds = inp.random_words(n_seeds, L, seed=L + n_seeds)
+    _pq_compare(lg, L, seeds, cap, B, max_exp)
+
+
+def test_pq_duplicate_seeds_and_tu_stop(lg):
+    L = 45
+    s = inp.random_words(6, L, seed=9)
+    seeds = np.concatenate([s, s[:3]])  # repeated seeds are admitted once
+    _pq_compare(lg, L, seeds, 1 << 12, 4, 10**6, T_u=40)
+
+
+@pytest.mark.parametrize("L", [451, 527])
+def test_pq_paper_lengths(lg, L):
+    seeds = oracle.skew_fill(inp.random_words(24, L, seed=L), L) if L % 2 else inp.random_words(24, L, seed=L)
+    _pq_compare(lg, L, seeds, 4096, 64, 256)
