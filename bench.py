@@ -48,8 +48,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed"],
-                    help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch")
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq"],
+                    help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
+                         "pq: step-2 refinement from step-1 candidates")
+    ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
+    ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
+    ap.add_argument("--pq-hlog2", type=int, default=28)
     return ap.parse_args()
 
 
@@ -246,6 +250,63 @@ def run_mixed(args, ws, rank, local):
     return 0
 
 
+def run_pq(args, ws, rank, local):
+    """Step 2 (Algorithm 2) at one length: 4,096 distinct seeds = the best states of a step-1 search at
+    that length (16,384 walks x 5,000 flips, p = 24 for odd L), open set 2^22, B = 4,096 pops per round."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lg.load()
+    S2 = inp.STEP2
+    L = args.L
+    skew = L % 2 == 1
+    p = W1["p"] if skew else 0
+    pre_h = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"]) if p else np.zeros(1, np.uint64)
+    n_w, R = 16384, 4
+    cfg = lg.make_walk_cfg(L, skew=skew, p=p, n_walks=n_w, flip_budget=5000, seed=W1["seed"], R=R,
+                           E_thr=lg.INT32_MAX)
+    out, _, _ = lg.labs_skew_search(cfg, pre_h, with_walk_stats=False)
+    cand = lg.candidates_numpy(out, n_w, R).reshape(-1)
+    cand = cand[cand["E"] != lg.INT32_MAX]
+    order = np.lexsort((cand["fp"], cand["E"]))
+    _, first = np.unique(cand["fp"][order], return_index=True)
+    pick = order[np.sort(first)][: S2["n_seeds"]]
+    pick = pick[np.lexsort((cand["fp"][pick], cand["E"][pick]))]
+    W = (L + 63) // 64
+    seeds = torch.from_numpy(np.ascontiguousarray(cand["seq"][pick][:, :W]).view(np.int64)).to(dev)
+    seed_best = int(cand["E"][pick].min())
+    times = []
+    for it in range(max(1, args.warmup) + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, bE, st = lg.labs_pq_refine(L, seeds, B=S2["B"], cap=S2["cap"], H_log2=args.pq_hlog2,
+                                         max_expansions=args.pq_expansions, T_u=S2["T_u"])
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times[-args.steps:])
+    s2 = lg.pq_stats_numpy(st)
+    exps = int(s2["expansions"])
+    terms = exps * L * (L - 1)
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    line = {"metric": "expansions/s", "value": exps / t, "unit": "expansions/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "step2_pq_L%d_4096seeds_cap2^22_B4096" % L, "L": L, "seeds": int(len(pick)),
+                       "max_expansions": args.pq_expansions, "H_slots_log2": args.pq_hlog2,
+                       "seed_best_E": seed_best, "best_E": int(bE.cpu()[0]), "stats": {k: int(s2[k]) for k in
+                       ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements",
+                        "stop_reason", "status")}},
+            "neighbour_evaluations_per_s": exps * L / t,
+            "roofline": {"bound": "alu", "achieved": terms / t / 1e9, "peak": peak, "unit": "Gop/s",
+                         "frac": terms / t / 1e9 / peak, "traffic": None,
+                         "work": "per expansion L(L-1) neighbour-lag multiply-adds (whole step timed, host-driven)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -253,6 +314,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "mixed":
         return run_mixed(args, ws, rank, local)
+    if args.workload == "pq":
+        return run_pq(args, ws, rank, local)
 
     import torch
 

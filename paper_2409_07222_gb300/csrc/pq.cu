@@ -376,29 +376,83 @@ __global__ void __launch_bounds__(256) radix_hist_kernel(PqBufs b, int pass) {
   b.counts[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) radix_scan_kernel(PqBufs b) {
-  // exclusive scan over the digit-major counts of this round's block count
-  const long long n = 256 * tiles_of(b.st->nS);
-  __shared__ unsigned long long part[1024];
+// Exclusive scan of the digit-major radix counts (256 x blocks of this round), in three phases over
+// segments of kSeg entries: segment sums, a scan of the sums, then each segment with its offset.
+constexpr int kSeg = 4096;
+
+__device__ __forceinline__ long long radix_count_len(const PqBufs& b) { return 256 * tiles_of(b.st->nS); }
+
+__global__ void __launch_bounds__(256) seg_reduce_kernel(PqBufs b) {
+  const long long n = radix_count_len(b);
+  const long long lo = (long long)blockIdx.x * kSeg;
+  unsigned s = 0;
+  if (lo < n)
+    for (long long i = lo + threadIdx.x; i < min(n, lo + kSeg); i += 256) s += b.counts[i];
+  s = __reduce_add_sync(kFull, s);
+  __shared__ unsigned w[8];
+  if (lane_id() == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int i = 0; i < 8; i++) t += w[i];
+    b.bsum[blockIdx.x] = t;  // zero for segments past this round's length
+  }
+}
+
+__global__ void __launch_bounds__(1024) seg_scan_sums_kernel(unsigned* a, int n) {
+  __shared__ unsigned part[1024];
   const int t = threadIdx.x;
-  const long long chunk = (n + 1023) / 1024;
-  const long long lo = t * chunk, hi = min(n, lo + chunk);
-  unsigned long long s = 0;
-  for (long long i = lo; i < hi; i++) s += b.counts[i];
+  const int chunk = (n + 1023) / 1024;
+  const int lo = t * chunk, hi = min(n, lo + chunk);
+  unsigned s = 0;
+  for (int i = lo; i < hi; i++) s += a[i];
   part[t] = s;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {
-    unsigned long long v = t >= off ? part[t - off] : 0;
+    unsigned v = t >= off ? part[t - off] : 0;
     __syncthreads();
     part[t] += v;
     __syncthreads();
   }
-  unsigned long long run = t ? part[t - 1] : 0;
-  for (long long i = lo; i < hi; i++) {
-    const unsigned v = b.counts[i];
-    b.counts[i] = (unsigned)run;
+  unsigned run = t ? part[t - 1] : 0;
+  for (int i = lo; i < hi; i++) {
+    const unsigned v = a[i];
+    a[i] = run;
     run += v;
   }
+}
+
+__global__ void __launch_bounds__(256) seg_down_kernel(PqBufs b) {
+  const long long n = radix_count_len(b);
+  const long long lo = (long long)blockIdx.x * kSeg;
+  if (lo >= n) return;
+  // thread t owns entries lo + 16t .. lo + 16t + 15
+  const long long first = lo + 16 * threadIdx.x;
+  unsigned v[16], s = 0;
+#pragma unroll
+  for (int i = 0; i < 16; i++) {
+    v[i] = first + i < n ? b.counts[first + i] : 0u;
+    s += v[i];
+  }
+  // block exclusive scan of the thread sums
+  unsigned incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned x = __shfl_up_sync(kFull, incl, o);
+    if (lane_id() >= o) incl += x;
+  }
+  __shared__ unsigned wsum[8];
+  if (lane_id() == 31) wsum[threadIdx.x >> 5] = incl;
+  __syncthreads();
+  unsigned wofs = 0;
+  for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wofs += wsum[w];
+  unsigned run = b.bsum[blockIdx.x] + wofs + incl - s;
+#pragma unroll
+  for (int i = 0; i < 16; i++)
+    if (first + i < n) {
+      b.counts[first + i] = run;
+      run += v[i];
+    }
 }
 
 __global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) {
@@ -628,9 +682,12 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   auto sort_and_dedup = [&](long long max_n) {
     const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
     issue_compact<0>(b, max_n, &dst->nS, st);
+    const int nseg = (int)((256ll * nb + kSeg - 1) / kSeg);
     for (int pass = 0; pass < 12; pass++) {
       radix_hist_kernel<<<nb, 256, 0, st>>>(b, pass);
-      radix_scan_kernel<<<1, 1024, 0, st>>>(b);
+      seg_reduce_kernel<<<nseg, 256, 0, st>>>(b);
+      seg_scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nseg);
+      seg_down_kernel<<<nseg, 256, 0, st>>>(b);
       radix_scatter_kernel<<<nb, 256, 0, st>>>(b, pass);
     }
     issue_compact<1>(b, max_n, &dst->nU, st);
