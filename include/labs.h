@@ -264,6 +264,37 @@ int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds,
                    int32_t* best_E, labs_pq_stats* stats, void* stream);
 
 /*
+ * Learned flip proposal (library extension; the paper has no learned component).  A small network --
+ * features (s_i, C_k / sqrt(L-k)), three Conv1d(64, kernel 9) layers, Linear(64L -> 256), Linear(256 -> L)
+ * -- scores the L positions of a sequence; walks may bias their neighbour choice with it while the exact
+ * energy scan stays the judge.  Weights are BF16 with an FP32 master copy; sums accumulate in FP32.
+ * Parameters are one flat FP32 array in the order w1 [64][2][9], b1 [64], w2 [64][64][9], b2, w3, b3,
+ * W4 [256][64 L], b4 [256], W5 [L][256], b5 [L].
+ */
+typedef struct labs_policy labs_policy;
+
+/* Number of parameters for length L. */
+int labs_policy_param_count(int L, int64_t* n_out);
+/* Creates a network for length L with He-uniform weights drawn from SplitMix64 stream (seed, 4, layer). */
+int labs_policy_create(labs_ctx* ctx, int L, uint64_t seed, labs_policy** out);
+void labs_policy_destroy(labs_policy* policy);
+/* Replaces the parameters (device FP32 [n]) and resets the optimizer state. */
+int labs_policy_set_params(labs_policy* policy, const float* params, void* stream);
+/* Copies the FP32 master parameters to device memory [n]. */
+int labs_policy_get_params(labs_policy* policy, float* params, void* stream);
+/* logits [n][L] FP32 (device) of n packed sequences (device). */
+int labs_policy_forward(labs_policy* policy, const uint64_t* seqs, int64_t n, float* logits, void* stream);
+/*
+ * One training step on n samples: forward, weighted cross-entropy over the free positions
+ * [free_lo, free_hi] (0-based, the same for every sample) toward target[q] (0-based position), backward,
+ * and Adam (lr 0: no update).  loss_out (nullable, device FP32 [1]) receives the mean weighted loss,
+ * grads_out (nullable, device FP32 [n_params]) the gradient.  Device pointers throughout.
+ */
+int labs_policy_train_step(labs_policy* policy, const uint64_t* seqs, const int32_t* target, const float* weight,
+                           int64_t n, int free_lo, int free_hi, float lr, float* loss_out, float* grads_out,
+                           void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

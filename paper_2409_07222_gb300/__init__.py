@@ -220,6 +220,54 @@ def pq_stats_numpy(st):
     return st.cpu().numpy().view(PQ_STATS_DTYPE)[0]
 
 
+class Policy:
+    """The learned flip-proposal network (labs_policy_*): BF16 weights, FP32 accumulation."""
+
+    def __init__(self, L, seed=0, device=None):
+        self.dev = _device(device)
+        self.L = L
+        n = ctypes.c_int64()
+        _lib.check(load().labs_policy_param_count(L, ctypes.byref(n)), "labs_policy_param_count")
+        self.n_params = n.value
+        h = ctypes.c_void_p()
+        _lib.check(load().labs_policy_create(context(self.dev.index), L, seed, ctypes.byref(h)), "labs_policy_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib._lib is not None:
+            _lib._lib.labs_policy_destroy(self.h)
+            self.h = None
+
+    def set_params(self, flat):
+        t = torch.as_tensor(flat, dtype=torch.float32).to(self.dev).contiguous()
+        assert t.numel() == self.n_params
+        _lib.check(load().labs_policy_set_params(self.h, _ptr(t), _stream(self.dev)), "labs_policy_set_params")
+        torch.cuda.current_stream(self.dev).synchronize()
+
+    def get_params(self):
+        t = torch.empty(self.n_params, dtype=torch.float32, device=self.dev)
+        _lib.check(load().labs_policy_get_params(self.h, _ptr(t), _stream(self.dev)), "labs_policy_get_params")
+        return t
+
+    def forward(self, seqs):
+        s = _dev_words(seqs, self.L)
+        out = torch.empty((s.shape[0], self.L), dtype=torch.float32, device=self.dev)
+        _lib.check(load().labs_policy_forward(self.h, _ptr(s), s.shape[0], _ptr(out), _stream(self.dev)),
+                   "labs_policy_forward")
+        return out
+
+    def train_step(self, seqs, target, weight, free_lo, free_hi, lr, want_grads=False):
+        s = _dev_words(seqs, self.L)
+        tg = torch.as_tensor(target, dtype=torch.int32).to(self.dev).contiguous()
+        wt = torch.as_tensor(weight, dtype=torch.float32).to(self.dev).contiguous()
+        loss = torch.empty(1, dtype=torch.float32, device=self.dev)
+        grads = torch.empty(self.n_params, dtype=torch.float32, device=self.dev) if want_grads else None
+        _lib.check(load().labs_policy_train_step(self.h, _ptr(s), _ptr(tg), _ptr(wt), s.shape[0], free_lo, free_hi,
+                                                 float(lr), _ptr(loss), _ptr(grads), _stream(self.dev)),
+                   "labs_policy_train_step")
+        return loss, grads
+
+
 def labs_skew_search_host(cfg, prefixes_host, device=None):
     """End-to-end form: host prefixes in, host candidates/stats out (copies included)."""
     dev = _device(device)
