@@ -295,6 +295,25 @@ int labs_policy_train_step(labs_policy* policy, const uint64_t* seqs, const int3
                            void* stream);
 
 /*
+ * labs_chunked_search -- labs_skew_search's walks run in chunks of `chunk` accepted flips per walk, with
+ * each walk's state saved between launches.  With a policy, every walk's current sequence is scored before
+ * each chunk (and before the first) and the neighbour choice becomes the smallest
+ *     (fmaf(-lambda, logit[m-1], (float) Delta E_m), m)        (FP32; a non-finite logit counts as 0)
+ * among the unexplored neighbours -- the energies stay exact, only the order of the choice changes.
+ * Without a policy (or lambda = 0) the results are identical to labs_skew_search.  The paper has no
+ * counterpart: this is the library's learned proposal.
+ *   Arguments as in labs_skew_search, plus (all nullable, DEVICE, n_chunks = ceil(flip_budget / chunk)):
+ *   logits_log [n_chunks][n_walks][L] FP32: the logits each chunk used;
+ *   state_log  [n_chunks][n_walks][W] uint64: every walk's sequence when its chunk began;
+ *   move_log   [n_chunks][n_walks][2] int32: the chunk's first move (position, Delta E), (-1, 0) if none.
+ *   Workspace: about 5.5 KB per walk.
+ */
+int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* policy, float lambda, int chunk,
+                        const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                        labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
+                        void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

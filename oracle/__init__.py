@@ -53,6 +53,8 @@ def lib():
             "oracle_fingerprint_batch": (ci, [P, ci, i64, P]),
             "oracle_make_starts": (ci, [ci, ci, ci, P, ci, ci, u64, u64, i64, i64, u64, P]),
             "oracle_walk_search": (ci, [ci, ci, ci, P, ci, ci, i64, i64, i64, ci, u64, ci, ci, ci, i32, P, P, ci]),
+            "oracle_walk_search_biased": (ci, [ci, ci, ci, P, ci, ci, i64, i64, i64, ci, u64, ci, ci, ci, i32, P, ci, ci,
+                                               ctypes.c_float, P, P, ci]),
             "oracle_threshold": (ci, [ci, ci, ci, P, ci, ci, u64, i64, i64, P, P]),
             "oracle_skew_exhaustive": (ci, [ci, ci, P, P, P, P, P]),
             "oracle_pq_refine": (ci, [ci, P, ci, i64, ci, i64, i64, P, P, P, P]),
@@ -200,16 +202,30 @@ def make_starts(L, skew, p, prefixes, seed, purpose, first, n, segment=0):
 # Algorithm 1 (walks), sieve threshold, exhaustive skew search, Algorithm 2
 # ---------------------------------------------------------------------------------------------
 def walk_search(L, skew, p, prefixes, n_walks, flip_budget, T_i, seed, R=16, bloom_log2=15, bloom_k=4,
-                E_thr=INT32_MAX, walk_begin=0, n_threads=1):
-    """Returns (candidates [n_walks, R] structured array, walk_stats [n_walks, 5] int64)."""
+                E_thr=INT32_MAX, walk_begin=0, n_threads=1, logits=None, chunk=64, lam=0.0):
+    """Returns (candidates [n_walks, R] structured array, walk_stats [n_walks, 5] int64).
+
+    logits (optional): float32 [n_walks, n_chunks, L] proposal logits, chunk c used for the moves made
+    while the walk's flip count is in [c*chunk, (c+1)*chunk); the choice key becomes the FP32 score
+    fmaf(-lam, logit, Delta E)."""
     pre, pw = _prefix_array(prefixes, p)
     out = np.zeros((n_walks, R), dtype=CANDIDATE_DTYPE)
     st = np.zeros((n_walks, 5), dtype=np.int64)
-    _check(
-        lib().oracle_walk_search(L, int(skew), p, _p(pre), pre.shape[0], pw, walk_begin, n_walks, flip_budget, T_i,
-                                 seed, R, bloom_log2, bloom_k, int(E_thr), _p(out), _p(st), n_threads),
-        "walk_search",
-    )
+    if logits is None:
+        _check(
+            lib().oracle_walk_search(L, int(skew), p, _p(pre), pre.shape[0], pw, walk_begin, n_walks, flip_budget,
+                                     T_i, seed, R, bloom_log2, bloom_k, int(E_thr), _p(out), _p(st), n_threads),
+            "walk_search",
+        )
+    else:
+        lg = np.ascontiguousarray(logits, dtype=np.float32)
+        assert lg.shape[0] == n_walks and lg.shape[2] == L
+        _check(
+            lib().oracle_walk_search_biased(L, int(skew), p, _p(pre), pre.shape[0], pw, walk_begin, n_walks,
+                                            flip_budget, T_i, seed, R, bloom_log2, bloom_k, int(E_thr), _p(lg),
+                                            lg.shape[1], chunk, float(lam), _p(out), _p(st), n_threads),
+            "walk_search_biased",
+        )
     return out, st
 
 

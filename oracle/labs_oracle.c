@@ -28,6 +28,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <pthread.h>
+#include <math.h>
 
 #define ORACLE_MAX_L 576
 #define ORACLE_MAX_W 9
@@ -408,6 +409,9 @@ typedef struct {
   int64_t walk_begin, n_walks, flip_budget;
   uint64_t seed;
   int32_t E_thr;
+  const float* logits; /* nullable: [n_walks][n_chunks][L] proposal logits */
+  int n_chunks, chunk;
+  float lambda;
   oracle_candidate* out;
   int64_t* walk_stats;
   int n_threads, thread_id;
@@ -448,6 +452,7 @@ static void run_one_walk(walk_job_t* job, int64_t w, bloom_t* bloom, const uint6
   int64_t C[ORACLE_MAX_L];
   int64_t dE[ORACLE_MAX_L + 1];
   int8_t in_bloom[ORACLE_MAX_L + 1];
+  double key[ORACLE_MAX_L + 1];
   oracle_candidate* slots = job->out + (w - job->walk_begin) * R;
   for (int r = 0; r < R; r++) {
     memset(&slots[r], 0, sizeof(oracle_candidate));
@@ -473,8 +478,26 @@ static void run_one_walk(walk_job_t* job, int64_t w, bloom_t* bloom, const uint6
         int nF = flip_set(L, skew, m, F);
         dE[m] = delta_linear(s, C, L, F, nF);
       }
+      /* choice key: Delta E, or with a proposal the FP32 score fmaf(-lambda, logit, Delta E) (a
+         non-finite logit counts as 0); ties go to the lower position */
+      const float* lg = NULL;
+      if (job->logits) {
+        int64_t ch = flips / job->chunk;
+        if (ch >= job->n_chunks) ch = job->n_chunks - 1;
+        lg = job->logits + ((w - job->walk_begin) * job->n_chunks + ch) * (int64_t)L;
+      }
+      for (int m = p + 1; m <= last; m++) {
+        if (lg) {
+          float l = lg[m - 1];
+          if (!isfinite(l)) l = 0.0f;
+          key[m] = (double)(fmaf(-job->lambda, l, (float)dE[m]) + 0.0f);
+        } else {
+          key[m] = (double)dE[m];
+        }
+      }
       int best = -1;
       int64_t best_d = 0;
+      double best_k = 0.0;
       for (int m = p + 1; m <= last; m++) {
         int F[2];
         int nF = flip_set(L, skew, m, F);
@@ -482,11 +505,11 @@ static void run_one_walk(walk_job_t* job, int64_t w, bloom_t* bloom, const uint6
         for (int a = 0; a < nF; a++) nfp ^= Z[F[a]];
         in_bloom[m] = (int8_t)bloom_contains(bloom, nfp);
         if (in_bloom[m]) continue;
-        if (best == -1 || dE[m] < best_d) { best = m; best_d = dE[m]; } /* ties keep the lower m */
+        if (best == -1 || key[m] < best_k) { best = m; best_d = dE[m]; best_k = key[m]; } /* ties keep the lower m */
       }
       /* statistics: explored neighbours that ranked ahead of the chosen one */
       for (int m = p + 1; m <= last; m++)
-        if (in_bloom[m] && (best == -1 || dE[m] < best_d || (dE[m] == best_d && m < best))) bloom_skips++;
+        if (in_bloom[m] && (best == -1 || key[m] < best_k || (key[m] == best_k && m < best))) bloom_skips++;
       if (best == -1) { dead_ends++; break; }
       int F[2];
       int nF = flip_set(L, skew, best, F);
@@ -522,19 +545,17 @@ static void* walk_thread(void* arg) {
   return NULL;
 }
 
-/* Runs walks walk_begin .. walk_begin+n_walks-1 (global walk ids; walk w uses prefix w mod n_prefix).
- * out: [n_walks][R] candidates sorted by (E, fp), empty slots E = INT32_MAX, fp = ~0.
- * walk_stats (nullable): [n_walks][5] = flips, segments, bloom_skips, dead_ends, best_E, where
- * bloom_skips counts Bloom-positive neighbours whose (Delta E, m) ranked ahead of the chosen move and
- * best_E is the lowest energy reached by a flip (INT32_MAX if none). */
-int oracle_walk_search(int L, int skew, int p, const uint64_t* prefixes, int n_prefix, int prefix_words,
-                       int64_t walk_begin, int64_t n_walks, int64_t flip_budget, int T_i, uint64_t seed, int R,
-                       int bloom_log2, int bloom_k, int32_t E_thr, oracle_candidate* out, int64_t* walk_stats, int n_threads) {
+/* Algorithm 1 walks with an optional proposal bias (see oracle_walk_search below). */
+int oracle_walk_search_biased(int L, int skew, int p, const uint64_t* prefixes, int n_prefix, int prefix_words,
+                              int64_t walk_begin, int64_t n_walks, int64_t flip_budget, int T_i, uint64_t seed, int R,
+                              int bloom_log2, int bloom_k, int32_t E_thr, const float* logits, int n_chunks, int chunk,
+                              float lambda, oracle_candidate* out, int64_t* walk_stats, int n_threads) {
   if (L < 2 || L > ORACLE_MAX_L || n_prefix < 1 || p < 0 || p > 64 * prefix_words || R < 1 || T_i < 1)
     return ORC_ERR_ARG;
   if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return ORC_ERR_ARG;
   if (!skew && p >= L) return ORC_ERR_ARG;
   if (bloom_log2 < 5 || bloom_log2 > 31 || bloom_k < 1 || n_threads < 1) return ORC_ERR_ARG;
+  if (logits && (n_chunks < 1 || chunk < 1)) return ORC_ERR_ARG;
   walk_job_t* jobs = (walk_job_t*)calloc((size_t)n_threads, sizeof(walk_job_t));
   pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
   if (!jobs || !th) { free(jobs); free(th); return ORC_ERR_NOMEM; }
@@ -543,7 +564,8 @@ int oracle_walk_search(int L, int skew, int p, const uint64_t* prefixes, int n_p
     j->L = L; j->skew = skew; j->p = p; j->prefix_words = prefix_words; j->n_prefix = n_prefix;
     j->T_i = T_i; j->R = R; j->bloom_log2 = bloom_log2; j->bloom_k = bloom_k; j->prefixes = prefixes;
     j->walk_begin = walk_begin; j->n_walks = n_walks; j->flip_budget = flip_budget; j->seed = seed;
-    j->E_thr = E_thr; j->out = out; j->walk_stats = walk_stats;
+    j->E_thr = E_thr; j->out = out; j->logits = logits; j->n_chunks = n_chunks; j->chunk = chunk;
+    j->lambda = lambda; j->walk_stats = walk_stats;
     j->n_threads = n_threads; j->thread_id = t; j->status = ORC_OK;
   }
   int status = ORC_OK;
@@ -558,6 +580,20 @@ int oracle_walk_search(int L, int skew, int p, const uint64_t* prefixes, int n_p
   free(jobs);
   free(th);
   return status;
+}
+
+/* Runs walks walk_begin .. walk_begin+n_walks-1 (global walk ids; walk w uses prefix w mod n_prefix).
+ * out: [n_walks][R] candidates sorted by (E, fp), empty slots E = INT32_MAX, fp = ~0.
+ * walk_stats (nullable): [n_walks][5] = flips, segments, bloom_skips, dead_ends, best_E, where
+ * bloom_skips counts Bloom-positive neighbours whose key ranked ahead of the chosen move and best_E is
+ * the lowest energy reached by a flip (INT32_MAX if none).  The _biased form takes the proposal logits
+ * of each walk's chunks (a chunk is `chunk` accepted flips). */
+int oracle_walk_search(int L, int skew, int p, const uint64_t* prefixes, int n_prefix, int prefix_words,
+                       int64_t walk_begin, int64_t n_walks, int64_t flip_budget, int T_i, uint64_t seed, int R,
+                       int bloom_log2, int bloom_k, int32_t E_thr, oracle_candidate* out, int64_t* walk_stats,
+                       int n_threads) {
+  return oracle_walk_search_biased(L, skew, p, prefixes, n_prefix, prefix_words, walk_begin, n_walks, flip_budget, T_i,
+                                   seed, R, bloom_log2, bloom_k, E_thr, NULL, 0, 0, 0.0f, out, walk_stats, n_threads);
 }
 
 /* ------------------------------------------------------------------------------------------------

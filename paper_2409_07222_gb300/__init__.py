@@ -268,6 +268,33 @@ class Policy:
         return loss, grads
 
 
+def labs_chunked_search(cfg, prefixes, policy=None, lam=0.0, chunk=64, device=None, log_logits=False,
+                        log_states=False, log_moves=False, with_walk_stats=True):
+    """Algorithm 1 walks in chunks of `chunk` flips, optionally biased by a Policy (learned proposal).
+
+    Returns dict: out, walk_stats, stats (as labs_skew_search) and, when asked, logits [n_chunks, n, L],
+    states [n_chunks, n, W] (int64 words), moves [n_chunks, n, 2].
+    """
+    dev = _device(device)
+    pre = _prefix_tensor(prefixes, cfg.p, dev)
+    n, L = cfg.n_walks, cfg.L
+    nch = (cfg.flip_budget + chunk - 1) // chunk
+    res = {
+        "out": torch.empty(max(1, n * cfg.R * _lib.CANDIDATE_BYTES), dtype=torch.uint8, device=dev),
+        "walk_stats": torch.empty((max(1, n), 6), dtype=torch.int64, device=dev) if with_walk_stats else None,
+        "stats": torch.empty(_lib.WALK_STATS_BYTES, dtype=torch.uint8, device=dev),
+        "logits": torch.empty((nch, n, L), dtype=torch.float32, device=dev) if log_logits else None,
+        "states": torch.empty((nch, n, words_per_seq(L)), dtype=torch.int64, device=dev) if log_states else None,
+        "moves": torch.empty((nch, n, 2), dtype=torch.int32, device=dev) if log_moves else None,
+    }
+    _lib.check(load().labs_chunked_search(context(dev.index), ctypes.byref(cfg), policy.h if policy else None,
+                                          float(lam), int(chunk), _ptr(pre), pre.shape[0], _ptr(res["out"]),
+                                          _ptr(res["walk_stats"]), _ptr(res["stats"]), _ptr(res["logits"]),
+                                          _ptr(res["states"]), _ptr(res["moves"]), _stream(dev)),
+               "labs_chunked_search")
+    return res
+
+
 def labs_skew_search_host(cfg, prefixes_host, device=None):
     """End-to-end form: host prefixes in, host candidates/stats out (copies included)."""
     dev = _device(device)

@@ -185,6 +185,31 @@ int labs_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t*
                                       (cudaStream_t)stream);
 }
 
+int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* policy, float lambda, int chunk,
+                        const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                        labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
+                        void* stream) {
+  if (!ctx || !cfg || chunk < 1 || !(lambda == lambda)) return LABS_ERR_INVALID_ARG;
+  int s = check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
+  if (s != LABS_OK) return s;
+  if (cfg->n_walks < 0 || cfg->walk_begin < 0 || cfg->flip_budget < 0 || cfg->R < 1 || cfg->R > labsg::kMaxR ||
+      cfg->bloom_log2 < 5 || cfg->bloom_log2 > 15 || cfg->bloom_k < 1 || cfg->bloom_k > 8)
+    return LABS_ERR_INVALID_ARG;
+  if (cfg->walk_begin + cfg->n_walks > 0xffffffffLL || cfg->flip_budget > 0x7fffffffLL) return LABS_ERR_INVALID_ARG;
+  if (cfg->tile_m != 0 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16) return LABS_ERR_INVALID_ARG;
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
+  if (!cfg->E_thr_dev && cfg->E_thr == LABS_AUTO_THRESHOLD &&
+      (cfg->n_thresh_samples < 1 || cfg->thresh_rank < 0 || cfg->thresh_rank >= cfg->n_thresh_samples))
+    return LABS_ERR_INVALID_ARG;
+  if (!stats || !aligned8(stats) || (cfg->n_walks > 0 && (!out || !aligned8(out))))
+    return LABS_ERR_INVALID_ARG;
+  if (policy && labsg::policy_length(policy) != cfg->L) return LABS_ERR_INVALID_ARG;
+  s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_chunked_search(ctx, cfg, policy, lambda, chunk, prefixes, n_prefix, out, walk_stats, stats,
+                                      logits_log, state_log, move_log, (cudaStream_t)stream);
+}
+
 int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                    int32_t* best_E, labs_pq_stats* stats, void* stream) {
   if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->B < 1 || cfg->B > 8192 || cfg->cap < 1 ||

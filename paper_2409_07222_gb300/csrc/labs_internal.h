@@ -27,10 +27,20 @@ struct labs_ctx {
 
 namespace labsg {
 
-enum WsSlot { kWsThreshSamples = 0, kWsThreshHist = 1, kWsWalkCounters = 2, kWsBatchThresholds = 3, kWsPq0 = 4 };
+enum WsSlot {
+  kWsThreshSamples = 0,
+  kWsThreshHist = 1,
+  kWsWalkCounters = 2,
+  kWsBatchThresholds = 3,
+  kWsPq0 = 4,
+  kWsChunkState = 5,
+  kWsChunkIo = 6
+};
 
 // Returns a device region of at least `bytes` for `slot`, growing it if needed (not capturable).
 void* ws_get(labs_ctx* ctx, int slot, size_t bytes);
+
+int policy_length(const labs_policy* P);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LABS_OK : LABS_ERR_CUDA; }
 
@@ -47,6 +57,10 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
 int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
                           const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
                           int32_t* E_thr_out, labs_walk_stats* stats, cudaStream_t st);
+int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* policy, float lambda, int chunk,
+                          const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                          labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
+                          cudaStream_t st);
 int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                      int32_t* best_E, labs_pq_stats* stats, cudaStream_t st);
 int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,

@@ -417,6 +417,9 @@ void forward(labs_policy* P, long long n, float* logits, cudaStream_t st) {
 }
 
 }  // namespace
+
+int policy_length(const labs_policy* P) { return P->L; }
+
 }  // namespace labsg
 
 using namespace labsg;

@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kMaxLens = 96;    // lengths in one launch (kernel parameter table)
 constexpr int kMaxPasses = 3;   // lane passes over the tasks of one walk
+constexpr int kSlotBytes = 12;  // per slot and lane: Delta E, choice key (int32), P_m, s_m * m (int16)
 
 struct WalkSmem {
   ScanSmem s;
@@ -51,8 +52,33 @@ struct WalkParams {
   int64_t* walk_stats;       // nullable: [n_items][6]
   labs_walk_stats* stats;
   unsigned long long* counter;
+  // resumable chunks (learned proposal); all nullable / zero for a plain run to the end
+  unsigned char* state;  // [n_items][state_stride] walk states between launches
+  int state_stride;
+  int chunk;             // > 0: at most `chunk` accepted flips per walk and launch; < 0: set-up only
+  const float* bias;     // [n_items][L] proposal logits biasing the choice (null: plain walk)
+  float lambda;
+  uint64_t* seq_out;     // [n_items][W]: the walk's sequence when the launch leaves it
+  int32_t* move_log;     // [n_items][2]: first move of the launch (position, Delta E), (-1, 0) if none
   LenEntry len[kMaxLens];
 };
+
+// Header of a saved walk state; followed by the sequence bits, the int16 table and the Bloom filter.
+struct WalkStateHdr {
+  unsigned long long fp;
+  long long skips;
+  int E, flips, segs, dead, it, mprev, first_hit, bestE, need_start, started, done, pad[5];
+};
+constexpr int kStateBits = sizeof(WalkStateHdr);
+constexpr int kStateC = kStateBits + 4 * kBitWords;
+constexpr int kStateBloom = kStateC + 2 * kCLen;
+constexpr int kStateBytes = kStateBloom + 4 * 1024;
+
+// Order-preserving int32 image of a float (-0 folded onto +0 first).
+__device__ __forceinline__ int float_key(float f) {
+  const int i = __float_as_int(f + 0.0f);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
 
 __device__ __forceinline__ uint32_t bloom_idx(uint64_t fp, int j, uint32_t mask) {
   uint32_t lo = (uint32_t)fp, hi = (uint32_t)(fp >> 32);
@@ -137,8 +163,10 @@ __device__ __forceinline__ bool lane_task(const Layout& ly, int H, int ps, int l
 
 // One walk-step kernel for every length of the launch.  Template: tile size M and lag ranges per tile H
 // (the autotuned "words per thread"); the number of lane passes is per length (<= kMaxPasses).
-// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): Delta E (int32),
-// P_m (int16, |P| <= L/2) and s_m * m (int16).
+// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): Delta E and the choice
+// key (int32), P_m (int16, |P| <= L/2) and s_m * m (int16).  With `state` the walk runs in chunks of
+// accepted flips and is saved between launches (bits, table, Bloom filter, counters); the sieve slots
+// stay in the output records meanwhile.
 // ONE: a single-length launch -- the length's entry is read at a fixed parameter offset and its
 // Zobrist keys are tabulated once per block in shared memory.
 template <int M, int H, bool ONE>
@@ -149,15 +177,16 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
   const int nwarps = blockDim.x >> 5;
   WalkSmem& ws = reinterpret_cast<WalkSmem*>(smem_raw)[wid];
   ScanSmem& sm = ws.s;
-  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * 8) * nwarps);
+  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * kSlotBytes) * nwarps);
   if (ONE) {
     const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)P.len[0].ly.L, 0);
     for (int i = threadIdx.x; i < P.len[0].ly.L; i += blockDim.x) ztab[i] = zobrist(zk, i + 1);
     __syncthreads();
   }
-  unsigned char* slot_base = smem_raw + sizeof(WalkSmem) * nwarps + (size_t)wid * P.slot_stride * 32 * 8;
+  unsigned char* slot_base = smem_raw + sizeof(WalkSmem) * nwarps + (size_t)wid * P.slot_stride * 32 * kSlotBytes;
   int* sl_d = reinterpret_cast<int*>(slot_base);
-  int16_t* sl_P = reinterpret_cast<int16_t*>(slot_base + (size_t)P.slot_stride * 32 * 4);
+  int* sl_k = sl_d + P.slot_stride * 32;
+  int16_t* sl_P = reinterpret_cast<int16_t*>(sl_k + P.slot_stride * 32);
   int16_t* sl_ms = sl_P + P.slot_stride * 32;
   const int lane = lane_id();
   const uint32_t bmask = (1u << P.bloom_log2) - 1u;
@@ -186,6 +215,10 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     const int NP = (ly.n_tasks + 31) >> 5;
     const int S = NP * MH;
     labs_candidate* rec = P.out + (int64_t)item * R;
+    const float* bias = P.bias ? P.bias + (long long)item * ly.L : nullptr;
+    WalkStateHdr* gh = P.state ? reinterpret_cast<WalkStateHdr*>(P.state + (size_t)item * P.state_stride) : nullptr;
+    if (gh && gh->done) continue;
+    const bool resumed = gh && gh->started;
 
     // slot positions of this length
     for (int ps = 0; ps < NP; ps++) {
@@ -197,36 +230,24 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         sl_ms[(ps * MH + k) * 32 + lane] = (int16_t)((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0);
       }
     }
-    // empty sieve slots
-    for (int r = lane; r < R; r += 32) {
-      rec[r].E = INT32_MAX;
-      rec[r].walk = 0;
-      rec[r].step = 0;
-      rec[r].pad = 0;
-      rec[r].fp = ~0ull;
-#pragma unroll
-      for (int t = 0; t < LABS_MAX_W; t++) rec[r].seq[t] = 0;
-    }
     int cE = INT32_MAX;
     uint64_t cfp = ~0ull;
     int wE = INT32_MAX;
     uint64_t wfp = ~0ull;
     int wlane = 0;
-
     unsigned flips = 0, segs = 0, dead = 0;
     long long skips = 0;
     int first_hit = -1;
     int bestE = INT32_MAX;
+    int E = 0, SC = 0, it = 0;
+    int mprev = 0;  // free position flipped by the previous move of this segment
+    uint64_t fp = 0;
+    bool fast = true, need_start = true;
 
-    while (flips < budget) {
-      for (int t = lane; t < bwords; t += 32) ws.bloom[t] = 0u;
-      build_start(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
-      segs++;
-      uint64_t fp = fingerprint(sm, ly.L, zkey);
-      bloom_add(ws.bloom, fp, P.bloom_k, bmask);
-      int E = build_table(sm, ly);
-      int SC = table_sum(sm);
-      bool fast = pack_c8(sm);
+    // rebuilds everything derived from the bits and the table: windows, int8 table, slot P and signs
+    auto derive = [&]() {
+      SC = table_sum(sm);
+      fast = pack_c8(sm);
       build_bytes(sm, ly);
       for (int t = 0; t < S; t++) {
         int m = sl_ms[t * 32 + lane];
@@ -239,186 +260,302 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         }
         sl_P[t * 32 + lane] = (int16_t)Pm;
       }
+    };
+    // INIT_PARTITIONED_SEQUENCE of a new segment (Algorithm 1)
+    auto start_segment = [&]() {
+      for (int t = lane; t < bwords; t += 32) ws.bloom[t] = 0u;
+      build_start(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
+      segs++;
+      fp = fingerprint(sm, ly.L, zkey);
+      bloom_add(ws.bloom, fp, P.bloom_k, bmask);
+      E = build_table(sm, ly);
+      derive();
+      it = 0;
+      mprev = 0;
+      need_start = false;
+    };
+    // new worst sieve slot: largest (E, fp), lowest lane among equals
+    auto find_worst = [&]() {
+      int mE = warp_max_i32(lane < R ? cE : INT32_MIN);
+      uint64_t mf = (lane < R && cE == mE) ? cfp : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        uint64_t other = __shfl_xor_sync(kFull, mf, o);
+        mf = other > mf ? other : mf;
+      }
+      unsigned who = __ballot_sync(kFull, lane < R && cE == mE && cfp == mf);
+      wE = mE;
+      wfp = mf;
+      wlane = __ffs(who) - 1;
+    };
 
-      int it = 0;
-      int mprev = 0;  // free position flipped by the previous move of this segment
-      while (it < le.T_i && flips < budget) {
-        it++;
-        // ---- scan; each lane keeps its best (Delta E, m)
-        int bd = INT32_MAX, bm = INT32_MAX;
-        int dprev = INT32_MAX;  // this lane's Delta E of the move back (only its owner sets it)
-        for (int ps = 0; ps < NP; ps++) {
-          int cls, q0, h;
-          const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
-          int acc[M];
+    if (!resumed) {
+      for (int r = lane; r < R; r += 32) {  // empty sieve slots
+        rec[r].E = INT32_MAX;
+        rec[r].walk = 0;
+        rec[r].step = 0;
+        rec[r].pad = 0;
+        rec[r].fp = ~0ull;
 #pragma unroll
-          for (int j = 0; j < M; j++) acc[j] = 0;
-          if (has) {
-            const int u_begin = h ? ly.NGh : 0;
-            const int u_end = h ? ly.NGend : ly.NGh;
-            if (fast)
-              scan_range<M, false>(sm, ly, cls, q0, u_begin, u_end, acc);
-            else
-              scan_range<M, true>(sm, ly, cls, q0, u_begin, u_end, acc);
-          }
-          if (H == 2) {
-#pragma unroll
-            for (int j = 0; j < M; j++) acc[j] += __shfl_xor_sync(kFull, acc[j], 1);
-          }
-#pragma unroll
-          for (int k = 0; k < MH; k++) {
-            const int t = ps * MH + k;
-            const int ms = sl_ms[t * 32 + lane];
-            const int m = ms < 0 ? -ms : ms;
-            const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
-            int d = INT32_MAX;
-            if (m) {
-              const SlotConst kc = slot_const(ly, m);
-              const int s_m = ms < 0 ? -1 : 1;
-              d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * (int)sl_P[t * 32 + lane];
-              if (kc.alpha == 4) d += 8 * kc.sigma * (int)sm.C16[kc.gd - 1];
-              if (m == mprev) {
-                dprev = d;  // the state just left: certainly in the Bloom filter
-                d = INT32_MAX;
-              } else if (d < bd || (d == bd && m < bm)) {
-                bd = d;
-                bm = m;
-              }
-            }
-            sl_d[t * 32 + lane] = d;
-          }
-        }
-        // ---- select: smallest (Delta E, m) whose neighbour is not in the Bloom filter
-        int mstar = -1, dstar = 0;
-        uint64_t nfp = 0;
-        for (int guard = 0; guard <= S * 32; guard++) {
-          const int dmin = warp_min_i32(bd);
-          if (dmin == INT32_MAX) break;
-          const int mm = (int)warp_min_u32(bd == dmin ? (unsigned)bm : 0xffffffffu);
-          uint64_t cand = fp ^ (ONE ? ztab[mm - 1] : zobrist(zkey, mm));
-          if (ly.skew && mm != ly.c) cand ^= ONE ? ztab[ly.L - mm] : zobrist(zkey, ly.L + 1 - mm);
-          if (!bloom_test(ws.bloom, cand, P.bloom_k, bmask)) {
-            mstar = mm;
-            dstar = dmin;
-            nfp = cand;
-            break;
-          }
-          skips++;
-          if (bd == dmin && bm == mm) {
-            // the owner lane's next best: smallest key ranked after (dmin, mm); keys ranked ahead were
-            // dropped earlier in this step
-            bd = INT32_MAX;
-            int nbm = INT32_MAX;
-            for (int t = 0; t < S; t++) {
-              const int d = sl_d[t * 32 + lane];
-              const int ms = sl_ms[t * 32 + lane];
-              const int m = ms < 0 ? -ms : ms;
-              if (d == INT32_MAX) continue;
-              if (d < dmin || (d == dmin && m <= mm)) continue;
-              if (d < bd || (d == bd && m < nbm)) {
-                bd = d;
-                nbm = m;
-              }
-            }
-            bm = nbm;
-          }
-        }
-        // the move back ranked ahead of the chosen move: count it as a Bloom skip
-        if (__any_sync(kFull, dprev != INT32_MAX && (mstar < 0 || dprev < dstar || (dprev == dstar && mprev < mstar))))
-          skips++;
-        if (mstar < 0) {
-          dead++;
-          break;
-        }
-        // ---- apply
-        const int f1 = (ly.skew && mstar != ly.c) ? ly.L + 1 - mstar : 0;
-        const int c0 = pos_cls(ly, mstar), q0f = pos_q(ly, mstar);
-        const int s0 = s_at(sm, ly, mstar);
-        const int q1f = f1 ? pos_q(ly, f1) : 0;  // the mirror has the class of m*
-        const int s1 = f1 ? s_at(sm, ly, f1) : 0;
-        for (int t = 0; t < S; t++) {
-          const int ms = sl_ms[t * 32 + lane];
-          const int m = ms < 0 ? -ms : ms;
-          if (m && !(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
-            const SlotConst kc = slot_const(ly, m);
-            const int cls = pos_cls(ly, m), q = pos_q(ly, m);
-            int Pm = sl_P[t * 32 + lane];
-            Pm = p_step(sm, cls, q, kc, Pm, c0, q0f, s0);
-            if (f1) Pm = p_step(sm, cls, q, kc, Pm, c0, q1f, s1);
-            sl_P[t * 32 + lane] = (int16_t)Pm;
-          }
-          if (m && m == mstar) sl_ms[t * 32 + lane] = (int16_t)(-ms);
-        }
-        mprev = mstar;
-        SC += table_update(sm, ly, mstar, &fast);
-        if (lane == 0) flip_position(sm, ly, mstar);
-        if (lane == 1 && f1) flip_position(sm, ly, f1);
+        for (int t = 0; t < LABS_MAX_W; t++) rec[r].seq[t] = 0;
+      }
+    } else {
+      flips = gh->flips;
+      segs = gh->segs;
+      dead = gh->dead;
+      skips = gh->skips;
+      first_hit = gh->first_hit;
+      bestE = gh->bestE;
+      need_start = gh->need_start;
+      it = gh->it;
+      mprev = gh->mprev;
+      E = gh->E;
+      fp = gh->fp;
+      if (lane < R) {
+        cE = rec[lane].E;
+        cfp = rec[lane].fp;
+      }
+      find_worst();
+      if (!need_start) {
+        const unsigned char* gb = reinterpret_cast<const unsigned char*>(gh);
+        for (int t = lane; t < kBitWords; t += 32) sm.bits[t] = reinterpret_cast<const uint32_t*>(gb + kStateBits)[t];
+        for (int t = lane; t < kCLen / 2; t += 32)
+          reinterpret_cast<uint32_t*>(sm.C16)[t] = reinterpret_cast<const uint32_t*>(gb + kStateC)[t];
+        for (int t = lane; t < bwords; t += 32) ws.bloom[t] = reinterpret_cast<const uint32_t*>(gb + kStateBloom)[t];
         __syncwarp();
-        E += dstar;
-        fp = nfp;
-        bloom_add(ws.bloom, fp, P.bloom_k, bmask);
-        flips++;
-        if (E < bestE) bestE = E;
-        if (first_hit < 0 && E <= P.E_target) first_hit = (int)flips;
-        // ---- sieve
-        if (E <= E_thr && key_less(E, fp, wE, wfp)) {
-          bool dup = __any_sync(kFull, lane < R && cE != INT32_MAX && cfp == fp);
-          if (!dup) {
-            if (lane == wlane) {
-              cE = E;
-              cfp = fp;
-            }
-            labs_candidate* rr = rec + wlane;
-            if (lane == 0) {
-              rr->E = E;
-              rr->walk = (uint32_t)w;
-              rr->step = (uint32_t)flips;
-              rr->fp = fp;
-            }
-            if (lane < W) rr->seq[lane] = (uint64_t)sm.bits[2 * lane] | ((uint64_t)sm.bits[2 * lane + 1] << 32);
-            // new worst slot: largest (E, fp), lowest lane among equals
-            int mE = warp_max_i32(lane < R ? cE : INT32_MIN);
-            uint64_t mf = (lane < R && cE == mE) ? cfp : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              uint64_t other = __shfl_xor_sync(kFull, mf, o);
-              mf = other > mf ? other : mf;
-            }
-            unsigned who = __ballot_sync(kFull, lane < R && cE == mE && cfp == mf);
-            wE = mE;
-            wfp = mf;
-            wlane = __ffs(who) - 1;
-          }
-        }
+        derive();
       }
     }
+    const unsigned flips0 = flips, segs0 = segs, dead0 = dead;
+    const long long skips0 = skips;
+    const unsigned chunk = P.chunk > 0 ? (unsigned)P.chunk : (P.chunk < 0 ? 0u : 0xffffffffu);
+    if (P.chunk < 0 && need_start && flips < budget) start_segment();  // set-up launch: first state only
+    unsigned taken = 0;
 
-    // ---- final: sort the R slots by (E, fp) (ties between empty slots by lane) and rewrite in place
-    int rank = 0;
-    for (int r = 0; r < R; r++) {
-      int oE = __shfl_sync(kFull, cE, r);
-      uint64_t of = __shfl_sync(kFull, cfp, r);
-      if (key_less(oE, of, cE, cfp) || (oE == cE && of == cfp && r < lane)) rank++;
+    while (flips < budget && taken < chunk) {
+      if (need_start) start_segment();
+      it++;
+      // ---- scan; each lane keeps its best (key, m) where key orders the choice: Delta E, or the
+      //      biased score Delta E - lambda * logit[m] mapped to an order-preserving integer
+      int bk = INT32_MAX, bm = INT32_MAX, bdE = 0;
+      int kprev = INT32_MAX;  // this lane's key of the move back (only its owner sets it)
+      for (int ps = 0; ps < NP; ps++) {
+        int cls, q0, h;
+        const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+        int acc[M];
+#pragma unroll
+        for (int j = 0; j < M; j++) acc[j] = 0;
+        if (has) {
+          const int u_begin = h ? ly.NGh : 0;
+          const int u_end = h ? ly.NGend : ly.NGh;
+          if (fast)
+            scan_range<M, false>(sm, ly, cls, q0, u_begin, u_end, acc);
+          else
+            scan_range<M, true>(sm, ly, cls, q0, u_begin, u_end, acc);
+        }
+        if (H == 2) {
+#pragma unroll
+          for (int j = 0; j < M; j++) acc[j] += __shfl_xor_sync(kFull, acc[j], 1);
+        }
+#pragma unroll
+        for (int k = 0; k < MH; k++) {
+          const int t = ps * MH + k;
+          const int ms = sl_ms[t * 32 + lane];
+          const int m = ms < 0 ? -ms : ms;
+          const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
+          int d = 0, key = INT32_MAX;
+          if (m) {
+            const SlotConst kc = slot_const(ly, m);
+            const int s_m = ms < 0 ? -1 : 1;
+            d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * (int)sl_P[t * 32 + lane];
+            if (kc.alpha == 4) d += 8 * kc.sigma * (int)sm.C16[kc.gd - 1];
+            key = d;
+            if (bias) {
+              float l = bias[m - 1];
+              if (!isfinite(l)) l = 0.f;  // a missing or broken proposal falls back to the plain choice
+              key = float_key(fmaf(-P.lambda, l, (float)d));
+            }
+            if (m == mprev) {
+              kprev = key;  // the state just left: certainly in the Bloom filter
+              key = INT32_MAX;
+            } else if (key < bk || (key == bk && m < bm)) {
+              bk = key;
+              bm = m;
+              bdE = d;
+            }
+          }
+          sl_d[t * 32 + lane] = d;
+          sl_k[t * 32 + lane] = key;
+        }
+      }
+      // ---- select: smallest (key, m) whose neighbour is not in the Bloom filter
+      int mstar = -1, kstar = 0, dstar = 0;
+      uint64_t nfp = 0;
+      for (int guard = 0; guard <= S * 32; guard++) {
+        const int kmin = warp_min_i32(bk);
+        if (kmin == INT32_MAX) break;
+        const int mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+        const unsigned owner = __ballot_sync(kFull, bk == kmin && bm == mm);
+        const int dmm = __shfl_sync(kFull, bdE, __ffs(owner) - 1);
+        uint64_t cand = fp ^ (ONE ? ztab[mm - 1] : zobrist(zkey, mm));
+        if (ly.skew && mm != ly.c) cand ^= ONE ? ztab[ly.L - mm] : zobrist(zkey, ly.L + 1 - mm);
+        if (!bloom_test(ws.bloom, cand, P.bloom_k, bmask)) {
+          mstar = mm;
+          kstar = kmin;
+          dstar = dmm;
+          nfp = cand;
+          break;
+        }
+        skips++;
+        if (bk == kmin && bm == mm) {
+          // the owner lane's next best: smallest key ranked after (kmin, mm); keys ranked ahead were
+          // dropped earlier in this step
+          bk = INT32_MAX;
+          int nbm = INT32_MAX, nbd = 0;
+          for (int t = 0; t < S; t++) {
+            const int key = sl_k[t * 32 + lane];
+            const int ms = sl_ms[t * 32 + lane];
+            const int m = ms < 0 ? -ms : ms;
+            if (key == INT32_MAX) continue;
+            if (key < kmin || (key == kmin && m <= mm)) continue;
+            if (key < bk || (key == bk && m < nbm)) {
+              bk = key;
+              nbm = m;
+              nbd = sl_d[t * 32 + lane];
+            }
+          }
+          bm = nbm;
+          bdE = nbd;
+        }
+      }
+      // the move back ranked ahead of the chosen move: count it as a Bloom skip
+      if (__any_sync(kFull, kprev != INT32_MAX && (mstar < 0 || kprev < kstar || (kprev == kstar && mprev < mstar))))
+        skips++;
+      if (mstar < 0) {
+        dead++;
+        need_start = true;
+        continue;
+      }
+      // ---- apply
+      const int f1 = (ly.skew && mstar != ly.c) ? ly.L + 1 - mstar : 0;
+      const int c0 = pos_cls(ly, mstar), q0f = pos_q(ly, mstar);
+      const int s0 = s_at(sm, ly, mstar);
+      const int q1f = f1 ? pos_q(ly, f1) : 0;  // the mirror has the class of m*
+      const int s1 = f1 ? s_at(sm, ly, f1) : 0;
+      for (int t = 0; t < S; t++) {
+        const int ms = sl_ms[t * 32 + lane];
+        const int m = ms < 0 ? -ms : ms;
+        if (m && !(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
+          const SlotConst kc = slot_const(ly, m);
+          const int cls = pos_cls(ly, m), q = pos_q(ly, m);
+          int Pm = sl_P[t * 32 + lane];
+          Pm = p_step(sm, cls, q, kc, Pm, c0, q0f, s0);
+          if (f1) Pm = p_step(sm, cls, q, kc, Pm, c0, q1f, s1);
+          sl_P[t * 32 + lane] = (int16_t)Pm;
+        }
+        if (m && m == mstar) sl_ms[t * 32 + lane] = (int16_t)(-ms);
+      }
+      mprev = mstar;
+      SC += table_update(sm, ly, mstar, &fast);
+      if (lane == 0) flip_position(sm, ly, mstar);
+      if (lane == 1 && f1) flip_position(sm, ly, f1);
+      __syncwarp();
+      E += dstar;
+      fp = nfp;
+      bloom_add(ws.bloom, fp, P.bloom_k, bmask);
+      flips++;
+      taken++;
+      if (taken == 1 && P.move_log && lane == 0) {
+        P.move_log[2 * item] = mstar;
+        P.move_log[2 * item + 1] = dstar;
+      }
+      if (E < bestE) bestE = E;
+      if (first_hit < 0 && E <= P.E_target) first_hit = (int)flips;
+      // ---- sieve
+      if (E <= E_thr && key_less(E, fp, wE, wfp)) {
+        bool dup = __any_sync(kFull, lane < R && cE != INT32_MAX && cfp == fp);
+        if (!dup) {
+          if (lane == wlane) {
+            cE = E;
+            cfp = fp;
+          }
+          labs_candidate* rr = rec + wlane;
+          if (lane == 0) {
+            rr->E = E;
+            rr->walk = (uint32_t)w;
+            rr->step = (uint32_t)flips;
+            rr->fp = fp;
+          }
+          if (lane < W) rr->seq[lane] = (uint64_t)sm.bits[2 * lane] | ((uint64_t)sm.bits[2 * lane + 1] << 32);
+          find_worst();
+        }
+      }
+      if (it >= le.T_i) need_start = true;
+    }
+    if (P.move_log && taken == 0 && lane == 0) {
+      P.move_log[2 * item] = -1;
+      P.move_log[2 * item + 1] = 0;
+    }
+    if (P.seq_out && lane < W)
+      P.seq_out[(size_t)item * W + lane] = (uint64_t)sm.bits[2 * lane] | ((uint64_t)sm.bits[2 * lane + 1] << 32);
+
+    if (flips < budget) {
+      // ---- leave the walk for the next launch
+      if (gh) {
+        unsigned char* gb = reinterpret_cast<unsigned char*>(gh);
+        for (int t = lane; t < kBitWords; t += 32) reinterpret_cast<uint32_t*>(gb + kStateBits)[t] = sm.bits[t];
+        for (int t = lane; t < kCLen / 2; t += 32)
+          reinterpret_cast<uint32_t*>(gb + kStateC)[t] = reinterpret_cast<const uint32_t*>(sm.C16)[t];
+        for (int t = lane; t < bwords; t += 32) reinterpret_cast<uint32_t*>(gb + kStateBloom)[t] = ws.bloom[t];
+        if (lane == 0) {
+          gh->fp = fp;
+          gh->skips = skips;
+          gh->E = E;
+          gh->flips = (int)flips;
+          gh->segs = (int)segs;
+          gh->dead = (int)dead;
+          gh->it = it;
+          gh->mprev = mprev;
+          gh->first_hit = first_hit;
+          gh->bestE = bestE;
+          gh->need_start = need_start ? 1 : 0;
+          gh->started = 1;
+          gh->done = 0;
+        }
+      }
+    } else {
+      // ---- final: sort the R slots by (E, fp) (ties between empty slots by lane) and rewrite in place
+      int rank = 0;
+      for (int r = 0; r < R; r++) {
+        int oE = __shfl_sync(kFull, cE, r);
+        uint64_t of = __shfl_sync(kFull, cfp, r);
+        if (key_less(oE, of, cE, cfp) || (oE == cE && of == cfp && r < lane)) rank++;
+      }
+      __syncwarp();
+      labs_candidate mine;
+      if (lane < R) mine = rec[lane];
+      __syncwarp();
+      if (lane < R) rec[rank] = mine;
+      __syncwarp();
+      if (P.walk_stats && lane == 0) {
+        int64_t* st = P.walk_stats + (int64_t)item * 6;
+        st[0] = (int64_t)flips;
+        st[1] = (int64_t)segs;
+        st[2] = skips;
+        st[3] = (int64_t)dead;
+        st[4] = bestE;
+        st[5] = first_hit;
+      }
+      if (gh && lane == 0) {
+        gh->done = 1;
+        gh->started = 1;
+      }
     }
     __syncwarp();
-    labs_candidate mine;
-    if (lane < R) mine = rec[lane];
-    __syncwarp();
-    if (lane < R) rec[rank] = mine;
-    __syncwarp();
-    if (P.walk_stats && lane == 0) {
-      int64_t* st = P.walk_stats + (int64_t)item * 6;
-      st[0] = (int64_t)flips;
-      st[1] = (int64_t)segs;
-      st[2] = skips;
-      st[3] = (int64_t)dead;
-      st[4] = bestE;
-      st[5] = first_hit;
-    }
-    agg_flips += flips;
-    agg_segs += segs;
-    agg_skips += skips;
-    agg_dead += dead;
+    agg_flips += flips - flips0;
+    agg_segs += segs - segs0;
+    agg_skips += skips - skips0;
+    agg_dead += dead - dead0;
     agg_best = min(agg_best, bestE);
   }
   if (lane == 0) {
@@ -542,7 +679,7 @@ static int passes_for(int L, int skew, int p, const Variant& v) {
 template <int M, int H>
 int walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st, bool configure, long long* blocks) {
   const bool one = P.n_len == 1;
-  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * 8) * (size_t)warps +
+  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * kSlotBytes) * (size_t)warps +
                       (one ? sizeof(uint64_t) * LABS_MAX_L : 0);
   auto kern = one ? walk_kernel<M, H, true> : walk_kernel<M, H, false>;
   if (configure) {
@@ -711,6 +848,87 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
     s = cuda_status(cudaGetLastError());
   }
   if (s == LABS_OK && P->n_items > 0) s = launch_walk(ctx, *P, v, cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8, st);
+  delete P;
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Chunked walks: the same Algorithm 1 walks run `chunk` accepted flips per launch and are saved in
+// between, so a proposal network can score every walk's current state before each chunk (learned mode).
+// Without a network the results equal labs_skew_search's.
+// ---------------------------------------------------------------------------------------------
+int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* policy, float lambda, int chunk,
+                          const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
+                          labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
+                          cudaStream_t st) {
+  std::vector<LenSpec> lens{{cfg->L, cfg->skew, cfg->p, cfg->T_i, cfg->n_walks, cfg->walk_begin}};
+  Variant v;
+  if (!choose_variant(lens, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
+  const long long n = cfg->n_walks;
+  const int L = cfg->L, W = (L + 63) / 64;
+  const long long n_chunks = (cfg->flip_budget + chunk - 1) / chunk;
+  char* w = static_cast<char*>(ws_get(ctx, kWsWalkCounters, 256));
+  unsigned char* state = static_cast<unsigned char*>(ws_get(ctx, kWsChunkState, (size_t)kStateBytes * (size_t)n));
+  char* io = static_cast<char*>(ws_get(ctx, kWsChunkIo, (size_t)n * (8 * W + 4 * L) + 256));
+  if (!w || !state || !io) return LABS_ERR_NOMEM;
+  uint64_t* seqbuf = reinterpret_cast<uint64_t*>(io);
+  float* logits = reinterpret_cast<float*>(io + (((size_t)n * 8 * W + 255) & ~size_t(255)));
+  WalkParams* P = new (std::nothrow) WalkParams();
+  if (!P) return LABS_ERR_NOMEM;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(w);
+  base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, cfg->flip_budget, cfg->seed, cfg->E_target,
+              prefixes, out, walk_stats, stats, counter);
+  fill_params(*P, lens, v);
+  int32_t* thr = reinterpret_cast<int32_t*>(w + 64);
+  int s = LABS_OK;
+  if (cfg->E_thr_dev) {
+    P->E_thr_dev = cfg->E_thr_dev;
+  } else if (cfg->E_thr == LABS_AUTO_THRESHOLD) {
+    s = launch_sample_threshold(ctx, cfg->L, cfg->skew, cfg->p, prefixes, n_prefix, P->prefix_words, cfg->seed,
+                                cfg->n_thresh_samples, cfg->thresh_rank, thr, nullptr, st);
+    P->E_thr_dev = thr;
+  } else {
+    P->len[0].E_thr_value = cfg->E_thr;
+  }
+  const int warps = cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8;
+  long long blocks = 0;
+  if (s == LABS_OK) s = walk_variant(ctx, *P, v, warps, st, true, &blocks);
+  if (s == LABS_OK && cudaMemsetAsync(state, 0, (size_t)kStateBytes * (size_t)n, st) != cudaSuccess) s = LABS_ERR_CUDA;
+  if (s == LABS_OK) {
+    walk_init_kernel<<<1, 1, 0, st>>>(stats, P->E_thr_dev, P->len[0].E_thr_value, counter);
+    s = cuda_status(cudaGetLastError());
+  }
+  P->state = state;
+  P->state_stride = kStateBytes;
+  P->seq_out = seqbuf;
+  // set-up launch: every walk's first state
+  P->chunk = -1;
+  if (s == LABS_OK && n > 0) s = walk_variant(ctx, *P, v, warps, st, false, &blocks);
+  for (long long c = 0; c < n_chunks && s == LABS_OK && n > 0; c++) {
+    if (policy) {
+      s = labs_policy_forward(policy, seqbuf, n, logits, st);
+      if (s != LABS_OK) break;
+      P->bias = logits;
+      P->lambda = lambda;
+      if (logits_log && cudaMemcpyAsync(logits_log + (size_t)c * n * L, logits, sizeof(float) * (size_t)n * L,
+                                        cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        s = LABS_ERR_CUDA;
+        break;
+      }
+    }
+    if (state_log && cudaMemcpyAsync(state_log + (size_t)c * n * W, seqbuf, 8 * (size_t)n * W,
+                                     cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      s = LABS_ERR_CUDA;
+      break;
+    }
+    P->chunk = chunk;
+    P->move_log = move_log ? move_log + (size_t)c * n * 2 : nullptr;
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st) != cudaSuccess) {
+      s = LABS_ERR_CUDA;
+      break;
+    }
+    s = walk_variant(ctx, *P, v, warps, st, false, &blocks);
+  }
   delete P;
   return s;
 }

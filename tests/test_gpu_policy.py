@@ -102,3 +102,46 @@ def test_adam_steps_reduce_the_loss(lg):
     seqs = torch.from_numpy(w.view(np.int64)).cuda()
     losses = [float(pol.train_step(seqs, target, weight, 0, 18, lr=1e-3)[0].cpu()[0]) for _ in range(40)]
     assert losses[-1] < 0.5 * losses[0]
+
+
+# ------------------------------------------------------------------------------------------------
+# Chunked and learned walks (labs_chunked_search)
+# ------------------------------------------------------------------------------------------------
+def _walk_cfg(lg, L, p, n, budget, T_i, seed, R):
+    return lg.make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n, flip_budget=budget, T_i=T_i, seed=seed, R=R,
+                            E_thr=2**31 - 1)
+
+
+@pytest.mark.parametrize("chunk", [64, 37, 1000])
+def test_chunked_without_policy_equals_plain_walks(lg, chunk):
+    L, p, n, budget, T_i = 451, 24, 24, 300, 128
+    pre = inp.distinct_prefixes(256, p, seed=2409)
+    cfg = _walk_cfg(lg, L, p, n, budget, T_i, 2409, 8)
+    out, ws, st = lg.labs_skew_search(cfg, pre)
+    res = lg.labs_chunked_search(cfg, pre, chunk=chunk)
+    torch.cuda.synchronize()
+    assert torch.equal(out, res["out"])
+    assert torch.equal(ws, res["walk_stats"])
+    assert lg.stats_numpy(st)["flips"] == lg.stats_numpy(res["stats"])["flips"] == n * budget
+
+
+@pytest.mark.parametrize("L,p,lam", [(101, 8, 3.0), (451, 24, 40.0), (100, 0, 5.0)])
+def test_learned_walks_replay_in_oracle(lg, L, p, lam):
+    """The GPU's logged logits replayed in the oracle give bit-identical moves, energies and statistics."""
+    n, budget, T_i, chunk = 12, 260, 100, 64
+    pre = inp.distinct_prefixes(64, p, seed=5) if p else np.zeros(1, dtype=np.uint64)
+    cfg = _walk_cfg(lg, L, p, n, budget, T_i, 77, 6)
+    pol = lg.Policy(L, seed=3)
+    res = lg.labs_chunked_search(cfg, pre, policy=pol, lam=lam, chunk=chunk, log_logits=True)
+    torch.cuda.synchronize()
+    logits = res["logits"].cpu().numpy().transpose(1, 0, 2).copy()  # [n, n_chunks, L]
+    assert np.isfinite(logits).all() and logits.std() > 0
+    cand = lg.candidates_numpy(res["out"], n, 6)
+    oc, ost = oracle.walk_search(L, L % 2 == 1, p, pre, n, budget, T_i, 77, R=6, n_threads=8, logits=logits,
+                                 chunk=chunk, lam=lam)
+    for f in ("E", "walk", "step", "fp", "seq"):
+        assert np.array_equal(cand[f], oc[f]), f
+    assert np.array_equal(res["walk_stats"].cpu().numpy()[:, :5], ost)
+    # the bias changed the walk: the plain walk differs
+    pc, _ = oracle.walk_search(L, L % 2 == 1, p, pre, n, budget, T_i, 77, R=6, n_threads=8)
+    assert not np.array_equal(pc["fp"], oc["fp"])
