@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
@@ -307,6 +307,29 @@ def run_pq(args, ws, rank, local):
     return 0
 
 
+def run_learned(args, ws, rank, local):
+    """Learned proposal at L=451: tuples from plain walks, training, lambda pre-registered on pilot seeds,
+    equal-budget gain over 30 fresh seeds (rank-sum) and time to a pre-registered E*, plain vs learned."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+    from paper_2409_07222_gb300 import learn
+
+    torch.cuda.set_device(local)
+    lg.load()
+    pre = inp.distinct_prefixes(W1["n_prefix"], W1["p"], seed=W1["prefix_seed"])
+    t0 = time.perf_counter()
+    res = learn.experiment(L=W1["L"], p=W1["p"], prefixes=pre, device=local, log=lambda m: print(m, file=sys.stderr))
+    tt = res["time_to_target"]
+    line = {"metric": "time-to-E* speedup (learned vs plain)", "value": tt["speedup_learned_vs_plain"],
+            "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": (time.perf_counter() - t0) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+bf16/fp32",
+            "data": "synthetic", "config": {"workload": "learned_proposal_L451", "L": W1["L"], "p": W1["p"]},
+            "learned": res}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -316,6 +339,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "learned":
+        return run_learned(args, ws, rank, local)
 
     import torch
 

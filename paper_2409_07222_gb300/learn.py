@@ -1,0 +1,154 @@
+"""Learned flip proposal: tuple collection from the search itself, training, and the equal-budget
+comparison with the plain walk.  Every number here comes from the library's kernels (chunked walks,
+network forward/backward/Adam); this module only schedules them and keeps the bookkeeping.
+
+Tuples (state, flip, Delta E, final walk F): the plain chunked walks log every walk's sequence at the
+start of each 64-flip chunk together with the chunk's first move; each walk's merit factor
+F = L^2 / (2 E_best) (Eq. 1) over its whole budget is its outcome.  A tuple's weight is the walk's
+clipped standardised advantage max(0, (F - mean F) / std F), so training imitates the moves of walks
+that ended well (advantage-weighted cross-entropy over the free positions).
+"""
+import numpy as np
+import torch
+
+from . import (INT32_MAX, Policy, candidates_numpy, labs_chunked_search, make_walk_cfg, stats_numpy,
+               words_per_seq)
+
+
+def free_range(L, p):
+    """0-based first and last free position of a walk of length L (skew for odd L)."""
+    last = (L + 1) // 2 if L % 2 else L
+    return p, last - 1
+
+
+def collect_tuples(L, p, prefixes, n_walks, flip_budget, seed, chunk=64, device=None):
+    """Runs plain chunked walks and returns (seqs int64 [K, W], target int32 [K], weight f32 [K], info)."""
+    cfg = make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n_walks, flip_budget=flip_budget, seed=seed, R=4,
+                        E_thr=INT32_MAX)
+    res = labs_chunked_search(cfg, prefixes, chunk=chunk, device=device, log_states=True, log_moves=True)
+    best = res["walk_stats"][:, 4].to(torch.float64)
+    F = (L * L) / (2.0 * best)
+    adv = torch.clamp((F - F.mean()) / F.std().clamp_min(1e-12), min=0.0)
+    moves = res["moves"]  # [nch, n, 2]
+    keep = (moves[..., 0] >= 1) & (adv[None, :] > 0)
+    idx = keep.nonzero(as_tuple=False)
+    seqs = res["states"][idx[:, 0], idx[:, 1]]
+    target = (moves[idx[:, 0], idx[:, 1], 0] - 1).to(torch.int32)
+    weight = adv[idx[:, 1]].to(torch.float32)
+    info = {"walks": n_walks, "chunks": int(moves.shape[0]), "tuples_logged": int((moves[..., 0] >= 1).sum()),
+            "tuples_kept": int(idx.shape[0]), "mean_F": float(F.mean()), "best_E": int(best.min())}
+    return seqs.contiguous(), target.contiguous(), weight.contiguous(), info
+
+
+def train(policy, seqs, target, weight, steps, batch, lr, free_lo, free_hi, seed=0):
+    """Adam steps on uniformly drawn minibatches; returns the loss after each step (host floats)."""
+    g = torch.Generator(device=seqs.device)
+    g.manual_seed(seed)
+    losses = []
+    for _ in range(steps):
+        pick = torch.randint(0, seqs.shape[0], (batch,), generator=g, device=seqs.device)
+        loss, _ = policy.train_step(seqs[pick], target[pick], weight[pick], free_lo, free_hi, lr)
+        losses.append(loss)
+    return [float(x) for x in torch.cat(losses).cpu()]
+
+
+def best_energies(L, p, prefixes, n_walks, flip_budget, seed, policy=None, lam=0.0, chunk=64, device=None,
+                  E_target=-(2**31)):
+    """Best energy over n_walks walks at an equal flip budget (plain or learned), plus per-walk stats."""
+    cfg = make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n_walks, flip_budget=flip_budget, seed=seed, R=4,
+                        E_thr=INT32_MAX, E_target=E_target)
+    res = labs_chunked_search(cfg, prefixes, policy=policy, lam=lam, chunk=chunk, device=device)
+    st = stats_numpy(res["stats"])
+    return int(st["best_E"]), res
+
+
+def rank_sum(a, b):
+    """Wilcoxon rank-sum test of a vs b (two-sided), as in the paper's step-2 ablation (Section 4)."""
+    from scipy.stats import ranksums
+
+    r = ranksums(a, b)
+    return float(r.statistic), float(r.pvalue)
+
+
+def _time_to_target(L, p, prefixes, n_walks, flip_budget, seed, E_star, policy, lam, chunk, cap_s, device=None):
+    """Seconds until some walk first reaches E <= E_star: the whole chunked run is timed with CUDA events and
+    the time to the chunk holding the earliest first hit (per-walk first-hit flip counts) is that share of
+    it (every chunk does the same work); None if no walk reaches E_star within the budget."""
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    res = labs_chunked_search(make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n_walks, flip_budget=flip_budget,
+                                            seed=seed, R=4, E_thr=INT32_MAX, E_target=E_star),
+                              prefixes, policy=policy, lam=lam, chunk=chunk, device=device)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t1.record()
+    torch.cuda.synchronize()
+    total_s = t0.elapsed_time(t1) * 1e-3
+    hit = res["walk_stats"][:, 5]
+    reached = hit[hit >= 0]
+    if reached.numel() == 0:
+        return None, total_s
+    # the first hit happens within the chunk containing the smallest first-hit flip count; time scales
+    # with the chunks run (each chunk costs the same), so interpolate on the chunk index
+    first_flip = int(reached.min())
+    n_chunks = (flip_budget + chunk - 1) // chunk
+    return total_s * ((first_flip + chunk - 1) // chunk) / n_chunks, total_s
+
+
+def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=8192, train_steps=3000, batch=512,
+               lr=1e-3, lambdas=(5.0, 20.0, 80.0), eval_walks=256, eval_flips=8192, n_seeds=30, ttt_walks=8192,
+               ttt_flips=16384, chunk=64, device=None, log=print):
+    """Collect tuples from plain walks, train the network, pick lambda on pilot seeds, then compare learned
+    vs plain at an equal flip budget on fresh seeds (rank-sum) and time both to a pre-registered E*."""
+    import time
+
+    out = {}
+    t = time.perf_counter()
+    seqs, tg, wt, info = collect_tuples(L, p, prefixes, collect_walks, collect_flips, seed=101, chunk=chunk,
+                                        device=device)
+    out["collect"] = dict(info, seconds=time.perf_counter() - t)
+    log("collected %s" % out["collect"])
+    pol = Policy(L, seed=7, device=device)
+    lo, hi = free_range(L, p)
+    t = time.perf_counter()
+    losses = train(pol, seqs, tg, wt, train_steps, batch, lr, lo, hi)
+    out["train"] = {"steps": train_steps, "batch": batch, "lr": lr, "loss_first": losses[0],
+                    "loss_last_100_mean": float(np.mean(losses[-100:])), "seconds": time.perf_counter() - t,
+                    "samples_seen": train_steps * batch}
+    log("trained %s" % out["train"])
+    # pre-registration on pilot seeds (not reused below): lambda and the target E*
+    pilot = [900 + i for i in range(4)]
+    plain_pilot = [best_energies(L, p, prefixes, eval_walks, eval_flips, s, device=device)[0] for s in pilot]
+    best_lam, best_gain = 0.0, 0.0
+    for lam in lambdas:
+        lrn = [best_energies(L, p, prefixes, eval_walks, eval_flips, s, policy=pol, lam=lam, chunk=chunk,
+                             device=device)[0] for s in pilot]
+        gain = float(np.mean(plain_pilot) - np.mean(lrn))
+        log("pilot lambda %g: plain %s learned %s" % (lam, plain_pilot, lrn))
+        if gain > best_gain:
+            best_lam, best_gain = lam, gain
+    lam = best_lam if best_lam > 0 else float(lambdas[0])
+    F_star = float(np.median([L * L / (2.0 * e) for e in plain_pilot]))
+    E_star = int(np.floor(L * L / (2.0 * F_star)))
+    out["preregistered"] = {"lambda": lam, "pilot_seeds": pilot, "F_star": F_star, "E_star": E_star}
+    # equal-budget comparison on fresh seeds
+    seeds = [1000 + i for i in range(n_seeds)]
+    plain = [best_energies(L, p, prefixes, eval_walks, eval_flips, s, device=device)[0] for s in seeds]
+    learned = [best_energies(L, p, prefixes, eval_walks, eval_flips, s, policy=pol, lam=lam, chunk=chunk,
+                             device=device)[0] for s in seeds]
+    stat, pval = rank_sum(learned, plain)
+    out["gain"] = {"seeds": n_seeds, "walks": eval_walks, "flips_per_walk": eval_flips,
+                   "plain_best_E_median": float(np.median(plain)), "learned_best_E_median": float(np.median(learned)),
+                   "median_gain_E": float(np.median(plain) - np.median(learned)), "ranksum_statistic": stat,
+                   "p_value": pval}
+    log("gain %s" % out["gain"])
+    # time to the pre-registered target: plain vs learned, same walks
+    ttt = {}
+    for name, pp, ll in (("plain", None, 0.0), ("learned", pol, lam)):
+        s_hit, s_total = _time_to_target(L, p, prefixes, ttt_walks, ttt_flips, 2000, E_star, pp, ll, chunk, 0,
+                                         device=device)
+        ttt[name] = {"seconds_to_E_star": s_hit, "seconds_total": s_total}
+    out["time_to_target"] = dict(ttt, walks=ttt_walks, flips_per_walk=ttt_flips, E_star=E_star)
+    p_s, l_s = ttt["plain"]["seconds_to_E_star"], ttt["learned"]["seconds_to_E_star"]
+    out["time_to_target"]["speedup_learned_vs_plain"] = (p_s / l_s) if (p_s and l_s) else None
+    log("time to target %s" % out["time_to_target"])
+    return out
