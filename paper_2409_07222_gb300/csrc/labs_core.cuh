@@ -163,8 +163,9 @@ __host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, 
   int cap = skew ? kClassBytes : kDirBytes;
   int need_f = qmax_end + 4 * ly.NGend + 8;
   int need_b = ly.Qr + 4 * ly.NGend + 8;
-  return (H == 1 || H == 2) && M % 4 == 0 && need_f < cap && need_b < cap && 4 * ly.NGend <= kCLen && L >= 2 &&
-         L <= kMaxL;
+  // the walk's P bookkeeping reads class index 2q - q_f <= 2 * qmax_end
+  return (H == 1 || H == 2) && M % 4 == 0 && need_f < cap && need_b < cap && 2 * qmax_end < cap &&
+         4 * ly.NGend <= kCLen && L >= 2 && L <= kMaxL;
 }
 
 // Tile tau -> (class, first class index).
@@ -405,52 +406,45 @@ __device__ __forceinline__ int finish_delta(const ScanSmem& sm, const Layout& ly
   return -2 * alpha * s_m * T + alpha * alpha * Q;
 }
 
-// P maintenance for one slot when the set F = {f0, f1} (f1 = 0 when single) flips; reads pre-flip s.
-// s0, s1 are the pre-flip values at f0, f1.  The pair (m - kappa, m + kappa) touches F only when
-// kappa = |m - f| is a multiple of lambda, and changes sign unless both ends are in F.
-__device__ __forceinline__ int p_update(const ScanSmem& sm, const Layout& ly, const SlotInfo& si, int P, int f0,
-                                        int s0, int f1, int s1) {
-  if (!si.active) return P;
-  const int gmax = min(si.nf, si.nb);
-  const int lmask = ly.lam - 1;
-#pragma unroll
-  for (int a = 0; a < 2; a++) {
-    const int f = a ? f1 : f0;
-    const int sf = a ? s1 : s0;
-    if (f == 0) continue;
-    const int d = si.m - f;
-    const int kap = d < 0 ? -d : d;
-    if (kap == 0 || (kap & lmask)) continue;
-    const int g = kap >> ly.lsh;
-    if (g > gmax || g == si.gd) continue;
-    const int other = si.m + d;
-    if (other == f0 || other == f1) continue;
-    P -= 2 * sf * s_at(sm, ly, other);
-  }
-  return P;
-}
-
-// Table update for flipping neighbour m* (pre-flip s): C_{lambda g} += -alpha s_m* y_g(m*), and the int8
-// copy alongside.  Returns the change of the table sum; *fast receives whether every |C| <= 127.
+// Table update for flipping neighbour m* (pre-flip s): C_{lambda g} += -alpha s_m* y_g(m*) for g = 1..G,
+// and the int8 copy alongside, four lags per lane and iteration: the windows s_{m* + lambda g} and
+// s_{m* - lambda g} of lags 4u+1..4u+4 are one realigned word per direction and y + 2 = fwd4 + bwd4
+// bytewise (as in the scan).  Lags beyond G have pads at both ends, so their y is 0 and C stays 0.
+// Returns the change of the table sum; *fast receives whether every |C| <= 127 (the int8 copy is only
+// read while that holds, and every step rewrites all of it).
 __device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bool* fast) {
   const int cls = pos_cls(ly, mstar), q = pos_q(ly, mstar);
   const int pair = (ly.skew && mstar != ly.c) ? 1 : 0;
-  const int alpha = pair ? 4 : 2;
   const int s_m = fwd_byte(sm, ly, cls, q) - 1;
+  const int as = -(pair ? 4 : 2) * s_m;  // C_g += as * y_g
   const int gd = pair ? (ly.L + 1 - 2 * mstar) >> 1 : 0;
   const int s_mp = pair ? (((ly.c - mstar) & 1) ? -s_m : s_m) : 0;
+  const uint32_t* Fw = sm.fwd + cls_words(cls);
+  const uint32_t* Bw = sm.bwd + cls_words(cls);
+  const int of = q + 1, ob = ly.Qr - q + 1;  // byte offsets of lag 1 in the two windows
+  const int wf = of >> 2, sf = 8 * (of & 3), wb = ob >> 2, sb = 8 * (ob & 3);
+  uint32_t* C16w = reinterpret_cast<uint32_t*>(sm.C16);
+  uint32_t* C8w = reinterpret_cast<uint32_t*>(sm.C8);
   int dsum = 0;
   bool ok = true;
-  for (int h = lane_id(); h < ly.G; h += 32) {
-    int g = h + 1;
-    int y = (fwd_byte(sm, ly, cls, q + g) - 1) + (bwd_byte(sm, ly, cls, ly.Qr - q + g) - 1);
-    if (g == gd) y -= s_mp;
-    int d = -alpha * s_m * y;
-    int v = sm.C16[h] + d;
-    sm.C16[h] = (int16_t)v;
-    sm.C8[h] = (int8_t)max(-127, min(127, v));
-    ok &= (v >= -127 && v <= 127);
-    dsum += d;
+  for (int u = lane_id(); u < ly.NG; u += 32) {
+    const uint32_t y4 = __funnelshift_r(Fw[wf + u], Fw[wf + u + 1], sf) + __funnelshift_r(Bw[wb + u], Bw[wb + u + 1], sb);
+    const uint32_t lo = C16w[2 * u], hi = C16w[2 * u + 1];
+    int c[4] = {(int)(int16_t)(lo & 0xffffu), (int)lo >> 16, (int)(int16_t)(hi & 0xffffu), (int)hi >> 16};
+    uint32_t c8 = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      int y = (int)((y4 >> (8 * e)) & 0xffu) - 2;
+      if (4 * u + e + 1 == gd) y -= s_mp;  // the pair's own product is not part of C
+      const int d = as * y;
+      c[e] += d;
+      dsum += d;
+      ok &= (c[e] >= -127 && c[e] <= 127);
+      c8 |= ((uint32_t)c[e] & 0xffu) << (8 * e);
+    }
+    C16w[2 * u] = ((uint32_t)c[0] & 0xffffu) | ((uint32_t)c[1] << 16);
+    C16w[2 * u + 1] = ((uint32_t)c[2] & 0xffffu) | ((uint32_t)c[3] << 16);
+    C8w[u] = c8;
   }
   __syncwarp();
   *fast = __all_sync(kFull, ok);

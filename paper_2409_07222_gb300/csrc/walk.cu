@@ -25,7 +25,8 @@ namespace {
 
 constexpr int kMaxLens = 96;    // lengths in one launch (kernel parameter table)
 constexpr int kMaxPasses = 3;   // lane passes over the tasks of one walk
-constexpr int kSlotBytes = 12;  // per slot and lane: Delta E, choice key (int32), P_m, s_m * m (int16)
+// per slot and lane: slot word and choice key (int32 each), plus Delta E when the choice is biased
+__host__ __device__ constexpr int slot_bytes(bool biased) { return biased ? 12 : 8; }
 
 struct WalkSmem {
   ScanSmem s;
@@ -109,45 +110,71 @@ __device__ __forceinline__ bool key_less(int Ea, uint64_t fa, int Eb, uint64_t f
   return Ea < Eb || (Ea == Eb && fa < fb);
 }
 
-struct SlotConst {
-  int alpha, gd, sigma, K0, gmax;
-};
+// Slot word of one neighbour: high half the signed position s_m * m (0: no neighbour in this slot), low
+// half alpha^2 Q_m, where Q_m = sum of y_kappa^2 over the valid lags = n_f + n_b - [pair] + 2 P_m.  It is
+// a sum of squares, so 0 <= alpha^2 Q_m <= 16 * 4 * 287 < 2^16 for every L <= 576.
+__device__ __forceinline__ int slot_pack(int sm_m, int Pt) { return (int)(((unsigned)sm_m << 16) | (unsigned)Pt); }
+__device__ __forceinline__ int slot_pos(int word) { return word >> 16; }  // s_m * m
+__device__ __forceinline__ int slot_Pt(int word) { return word & 0xffff; }
 
-// Closed forms: skew walks (L = 2c - 1, m <= c): n_f + n_b = G - 1 + (m & 1), n_b <= n_f, the excluded
-// lag of the pair (m, m') is g = c - m and s_{m'} = (-1)^{c-m} s_m (Eq. 2).  Unrestricted walks:
-// n_f + n_b = L - 1.
-__device__ __forceinline__ SlotConst slot_const(const Layout& ly, int m) {
-  SlotConst k;
-  if (ly.skew) {
-    const int pair = m != ly.c;
-    k.alpha = pair ? 4 : 2;
-    k.gd = ly.c - m;
-    k.sigma = (k.gd & 1) ? -1 : 1;
-    k.K0 = k.alpha * k.alpha * (ly.G - 1 + (m & 1) - pair);
-    k.gmax = (m - 1) >> 1;
-  } else {
-    k.alpha = 2;
-    k.gd = 0;
-    k.sigma = 1;
-    k.K0 = 4 * (ly.L - 1);
-    k.gmax = min(ly.L - m, m - 1);
+// Delta E of a neighbour from its accumulator a = sum_g C8/C16 (y + 2) and the table sum SC:
+//   Delta E = base - 2 alpha s_m (a - 2 SC),   base = alpha^2 Q_m + 2 alpha sigma C_{gd} [pair],
+// alpha = 4 for a skew pair (m, m'), 2 otherwise; the pair's own product at lag gd = c - m is removed
+// with s_{m'} = sigma s_m, sigma = (-1)^{c-m} (Eq. 2).  base depends only on the table and the slot
+// word, so it is formed before the scan.
+__device__ __forceinline__ int delta_base(const ScanSmem& sm, const Layout& ly, int word) {
+  const int ms = slot_pos(word);
+  const int m = ms < 0 ? -ms : ms;
+  int b = slot_Pt(word);
+  if (ly.skew && m != ly.c && m != 0) {
+    const int gd = ly.c - m;
+    const int cg = 8 * (int)sm.C16[gd - 1];
+    b += (gd & 1) ? -cg : cg;
   }
-  return k;
+  return b;
+}
+// 2 alpha s_m
+__device__ __forceinline__ int slot_sa(const Layout& ly, int ms) {
+  const int m = ms < 0 ? -ms : ms;
+  const int a2 = (ly.skew && m != ly.c) ? 8 : 4;
+  return ms < 0 ? -a2 : a2;
 }
 
-// P bookkeeping of one slot (class index q) when position f (class cf, class index qf, pre-flip value
-// sf) flips: the product s_{m - lambda g} s_{m + lambda g} with g = |q - qf| loses its sign unless g is
-// outside 1..gmax, is the excluded pair lag, or the product's other end flips too (the skew centre
-// when a pair flips).  The other end has class index 2q - qf.
-__device__ __forceinline__ int p_step(const ScanSmem& sm, int cls, int q, const SlotConst& k, int P, int cf, int qf,
-                                      int sf) {
-  const int d = q - qf;
-  const int g = d < 0 ? -d : d;
-  if (cls == cf && (unsigned)(g - 1) < (unsigned)k.gmax && g != k.gd) {
-    const uint8_t* F = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(cls));
-    P -= 2 * sf * ((int)F[q + d] - 1);
+// The last accepted move, not yet folded into the slot words: its flipped positions f0 (and the mirror
+// f1 of a skew pair), their class and class indices, and their values before the flip.  Flipping f
+// changes the product s_{2m-f} s_f of every neighbour m of f's class by -2 s_f s_{2m-f}; the byte at
+// class index 2q - q_f gives s_{2m-f}, and the pads (s = 0) drop products with an end outside 1..L.
+// That byte is never one of the flipped positions for the neighbours that change, so the update may be
+// applied after the flip, when the next step reads the slot anyway.  Excluded: the flipped neighbour
+// itself (its products do not contain s_m; its sign changes), the skew centre when a pair flips (both
+// ends of each of its products flip), and the pair product (m, m') of m, whose end m' is 2m - f0 when
+// 3 q - q_f0 = c + 6 - b (b = 1 for odd positions, 2 for even).
+struct PendingFlip {
+  bool on, pair;
+  int cls, q0f, q1f, s0, s1, qmir;
+};
+
+template <int MH>
+__device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, const PendingFlip& pf, int q_first,
+                                          int (&wv)[MH]) {
+  const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(pf.cls));
+  const int pmul = ly.skew ? -64 : -16;  // -4 alpha^2 for the neighbours that change
+  int v[MH];
+#pragma unroll
+  for (int k = 0; k < MH; k++) {
+    const int q = q_first + k;
+    v[k] = ((int)Fc[max(2 * q - pf.q0f, 0)] - 1) * pf.s0;
+    if (pf.pair) v[k] += ((int)Fc[max(2 * q - pf.q1f, 0)] - 1) * pf.s1;
   }
-  return P;
+#pragma unroll
+  for (int k = 0; k < MH; k++) {
+    const int q = q_first + k;
+    const int ms = slot_pos(wv[k]);
+    int vk = v[k];
+    if (ly.skew && 3 * q - pf.q0f == pf.qmir) vk -= ((int)Fc[2 * q - pf.q0f] - 1) * pf.s0;  // index >= 3 here
+    if (ms != 0 && q != pf.q0f && !(pf.pair && (ms == ly.c || ms == -ly.c))) wv[k] += pmul * vk;
+    if (ms != 0 && q == pf.q0f) wv[k] = slot_pack(-ms, slot_Pt(wv[k]));
+  }
 }
 
 // Task of `lane` in pass `ps`: tile (class, q0), lag range h, whether it exists.
@@ -163,13 +190,14 @@ __device__ __forceinline__ bool lane_task(const Layout& ly, int H, int ps, int l
 
 // One walk-step kernel for every length of the launch.  Template: tile size M and lag ranges per tile H
 // (the autotuned "words per thread"); the number of lane passes is per length (<= kMaxPasses).
-// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): Delta E and the choice
-// key (int32), P_m (int16, |P| <= L/2) and s_m * m (int16).  With `state` the walk runs in chunks of
+// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): the slot word, the
+// step's choice key and, for biased walks, its Delta E.  With `state` the walk runs in chunks of
 // accepted flips and is saved between launches (bits, table, Bloom filter, counters); the sieve slots
 // stay in the output records meanwhile.
 // ONE: a single-length launch -- the length's entry is read at a fixed parameter offset and its
-// Zobrist keys are tabulated once per block in shared memory.
-template <int M, int H, bool ONE>
+// Zobrist keys are tabulated once per block in shared memory.  BIASED: the choice key is the proposal
+// score of WalkParams::bias (single-length launches only).
+template <int M, int H, bool ONE, bool BIASED>
 __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ WalkParams P) {
   constexpr int MH = M / H;  // slots owned by a lane per pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -177,6 +205,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
   const int nwarps = blockDim.x >> 5;
   WalkSmem& ws = reinterpret_cast<WalkSmem*>(smem_raw)[wid];
   ScanSmem& sm = ws.s;
+  constexpr int kSlotBytes = slot_bytes(BIASED);
   uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * kSlotBytes) * nwarps);
   if (ONE) {
     const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)P.len[0].ly.L, 0);
@@ -184,10 +213,9 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     __syncthreads();
   }
   unsigned char* slot_base = smem_raw + sizeof(WalkSmem) * nwarps + (size_t)wid * P.slot_stride * 32 * kSlotBytes;
-  int* sl_d = reinterpret_cast<int*>(slot_base);
-  int* sl_k = sl_d + P.slot_stride * 32;
-  int16_t* sl_P = reinterpret_cast<int16_t*>(sl_k + P.slot_stride * 32);
-  int16_t* sl_ms = sl_P + P.slot_stride * 32;
+  int* sl_w = reinterpret_cast<int*>(slot_base);  // slot words
+  int* sl_k = sl_w + P.slot_stride * 32;            // choice keys of the step
+  int* sl_d = sl_k + P.slot_stride * 32;            // Delta E of the step (BIASED only; else = key)
   const int lane = lane_id();
   const uint32_t bmask = (1u << P.bloom_log2) - 1u;
   const int bwords = 1 << (P.bloom_log2 - 5);
@@ -215,7 +243,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     const int NP = (ly.n_tasks + 31) >> 5;
     const int S = NP * MH;
     labs_candidate* rec = P.out + (int64_t)item * R;
-    const float* bias = P.bias ? P.bias + (long long)item * ly.L : nullptr;
+    const float* bias = BIASED ? P.bias + (long long)item * ly.L : nullptr;
     WalkStateHdr* gh = P.state ? reinterpret_cast<WalkStateHdr*>(P.state + (size_t)item * P.state_stride) : nullptr;
     if (gh && gh->done) continue;
     const bool resumed = gh && gh->started;
@@ -227,7 +255,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
 #pragma unroll
       for (int k = 0; k < MH; k++) {
         const int m = q_pos(ly, cls, q0 + h * MH + k);
-        sl_ms[(ps * MH + k) * 32 + lane] = (int16_t)((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0);
+        sl_w[(ps * MH + k) * 32 + lane] = slot_pack((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0, 0);
       }
     }
     int cE = INT32_MAX;
@@ -243,6 +271,8 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     int mprev = 0;  // free position flipped by the previous move of this segment
     uint64_t fp = 0;
     bool fast = true, need_start = true;
+    PendingFlip pend;
+    pend.on = false;
 
     // rebuilds everything derived from the bits and the table: windows, int8 table, slot P and signs
     auto derive = [&]() {
@@ -250,16 +280,18 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       fast = pack_c8(sm);
       build_bytes(sm, ly);
       for (int t = 0; t < S; t++) {
-        int m = sl_ms[t * 32 + lane];
+        int m = slot_pos(sl_w[t * 32 + lane]);
         m = m < 0 ? -m : m;
-        int Pm = 0;
+        int word = 0;
         if (m) {
-          SlotInfo si = slot_info(ly, pos_cls(ly, m), pos_q(ly, m));
-          Pm = p_from_scratch(sm, ly, pos_cls(ly, m), pos_q(ly, m), si);
-          sl_ms[t * 32 + lane] = (int16_t)(s_at(sm, ly, m) * m);
+          const SlotInfo si = slot_info(ly, pos_cls(ly, m), pos_q(ly, m));
+          const int Pm = p_from_scratch(sm, ly, pos_cls(ly, m), pos_q(ly, m), si);
+          const int a2 = si.pair ? 16 : 4;
+          word = slot_pack(s_at(sm, ly, m) * m, a2 * (si.nf + si.nb - si.pair + 2 * Pm));
         }
-        sl_P[t * 32 + lane] = (int16_t)Pm;
+        sl_w[t * 32 + lane] = word;
       }
+      pend.on = false;
     };
     // INIT_PARTITIONED_SEQUENCE of a new segment (Algorithm 1)
     auto start_segment = [&]() {
@@ -342,6 +374,20 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       for (int ps = 0; ps < NP; ps++) {
         int cls, q0, h;
         const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+        {
+          // prep, while no accumulator is live: fold the last move into the slot words and park each
+          // neighbour's base in the key array
+          int wv[MH];
+#pragma unroll
+          for (int k = 0; k < MH; k++) wv[k] = sl_w[(ps * MH + k) * 32 + lane];
+          if (pend.on && has && cls == pend.cls) {
+            fold_flip<MH>(sm, ly, pend, q0 + h * MH, wv);
+#pragma unroll
+            for (int k = 0; k < MH; k++) sl_w[(ps * MH + k) * 32 + lane] = wv[k];
+          }
+#pragma unroll
+          for (int k = 0; k < MH; k++) sl_k[(ps * MH + k) * 32 + lane] = delta_base(sm, ly, wv[k]);
+        }
         int acc[M];
 #pragma unroll
         for (int j = 0; j < M; j++) acc[j] = 0;
@@ -357,35 +403,46 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
 #pragma unroll
           for (int j = 0; j < M; j++) acc[j] += __shfl_xor_sync(kFull, acc[j], 1);
         }
+        // finish: keys of this pass's neighbours, then their minimum by a tree of strict comparisons
+        // (the slots of a pass are in increasing m, so the left operand wins ties: smallest (key, m))
+        int kv[MH], mv[MH], dv[MH];
 #pragma unroll
         for (int k = 0; k < MH; k++) {
           const int t = ps * MH + k;
-          const int ms = sl_ms[t * 32 + lane];
+          const int ms = slot_pos(sl_w[t * 32 + lane]);
           const int m = ms < 0 ? -ms : ms;
           const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
-          int d = 0, key = INT32_MAX;
-          if (m) {
-            const SlotConst kc = slot_const(ly, m);
-            const int s_m = ms < 0 ? -1 : 1;
-            d = -2 * kc.alpha * s_m * (a - 2 * SC) + kc.K0 + 2 * kc.alpha * kc.alpha * (int)sl_P[t * 32 + lane];
-            if (kc.alpha == 4) d += 8 * kc.sigma * (int)sm.C16[kc.gd - 1];
-            key = d;
-            if (bias) {
-              float l = bias[m - 1];
-              if (!isfinite(l)) l = 0.f;  // a missing or broken proposal falls back to the plain choice
-              key = float_key(fmaf(-P.lambda, l, (float)d));
-            }
-            if (m == mprev) {
-              kprev = key;  // the state just left: certainly in the Bloom filter
-              key = INT32_MAX;
-            } else if (key < bk || (key == bk && m < bm)) {
-              bk = key;
-              bm = m;
-              bdE = d;
-            }
+          const int d = sl_k[t * 32 + lane] - slot_sa(ly, ms) * (a - 2 * SC);
+          int key = d;
+          if (BIASED && m) {
+            float l = bias[m - 1];
+            if (!isfinite(l)) l = 0.f;  // a missing or broken proposal falls back to the plain choice
+            key = float_key(fmaf(-P.lambda, l, (float)d));
           }
-          sl_d[t * 32 + lane] = d;
+          if (!m) key = INT32_MAX;
+          if (m && m == mprev) {
+            kprev = key;  // the state just left: certainly in the Bloom filter
+            key = INT32_MAX;
+          }
           sl_k[t * 32 + lane] = key;
+          if (BIASED) sl_d[t * 32 + lane] = d;
+          kv[k] = key;
+          mv[k] = m;
+          dv[k] = d;
+        }
+#pragma unroll
+        for (int st = 1; st < MH; st *= 2)
+#pragma unroll
+          for (int k = 0; k + st < MH; k += 2 * st)
+            if (kv[k + st] < kv[k]) {
+              kv[k] = kv[k + st];
+              mv[k] = mv[k + st];
+              dv[k] = dv[k + st];
+            }
+        if (kv[0] < bk || (kv[0] == bk && kv[0] != INT32_MAX && mv[0] < bm)) {
+          bk = kv[0];
+          bm = mv[0];
+          bdE = dv[0];
         }
       }
       // ---- select: smallest (key, m) whose neighbour is not in the Bloom filter
@@ -414,14 +471,14 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           int nbm = INT32_MAX, nbd = 0;
           for (int t = 0; t < S; t++) {
             const int key = sl_k[t * 32 + lane];
-            const int ms = sl_ms[t * 32 + lane];
+            const int ms = slot_pos(sl_w[t * 32 + lane]);
             const int m = ms < 0 ? -ms : ms;
             if (key == INT32_MAX) continue;
             if (key < kmin || (key == kmin && m <= mm)) continue;
             if (key < bk || (key == bk && m < nbm)) {
               bk = key;
               nbm = m;
-              nbd = sl_d[t * 32 + lane];
+              nbd = BIASED ? sl_d[t * 32 + lane] : key;
             }
           }
           bm = nbm;
@@ -437,28 +494,19 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         continue;
       }
       // ---- apply
-      const int f1 = (ly.skew && mstar != ly.c) ? ly.L + 1 - mstar : 0;
-      const int c0 = pos_cls(ly, mstar), q0f = pos_q(ly, mstar);
-      const int s0 = s_at(sm, ly, mstar);
-      const int q1f = f1 ? pos_q(ly, f1) : 0;  // the mirror has the class of m*
-      const int s1 = f1 ? s_at(sm, ly, f1) : 0;
-      for (int t = 0; t < S; t++) {
-        const int ms = sl_ms[t * 32 + lane];
-        const int m = ms < 0 ? -ms : ms;
-        if (m && !(f1 && m == ly.c)) {  // the centre's products (c - g, c + g) flip at both ends
-          const SlotConst kc = slot_const(ly, m);
-          const int cls = pos_cls(ly, m), q = pos_q(ly, m);
-          int Pm = sl_P[t * 32 + lane];
-          Pm = p_step(sm, cls, q, kc, Pm, c0, q0f, s0);
-          if (f1) Pm = p_step(sm, cls, q, kc, Pm, c0, q1f, s1);
-          sl_P[t * 32 + lane] = (int16_t)Pm;
-        }
-        if (m && m == mstar) sl_ms[t * 32 + lane] = (int16_t)(-ms);
-      }
+      // ---- apply; the slot words take the move at the next scan (fold_flip)
+      pend.on = true;
+      pend.pair = ly.skew && mstar != ly.c;
+      pend.cls = pos_cls(ly, mstar);
+      pend.q0f = pos_q(ly, mstar);
+      pend.s0 = s_at(sm, ly, mstar);
+      pend.q1f = pend.pair ? pos_q(ly, ly.L + 1 - mstar) : 0;  // the mirror has the class of m*
+      pend.s1 = pend.pair ? s_at(sm, ly, ly.L + 1 - mstar) : 0;
+      pend.qmir = ly.c + 6 - (pend.cls ? 1 : 2);
       mprev = mstar;
       SC += table_update(sm, ly, mstar, &fast);
       if (lane == 0) flip_position(sm, ly, mstar);
-      if (lane == 1 && f1) flip_position(sm, ly, f1);
+      if (lane == 1 && pend.pair) flip_position(sm, ly, ly.L + 1 - mstar);
       __syncwarp();
       E += dstar;
       fp = nfp;
@@ -678,10 +726,11 @@ static int passes_for(int L, int skew, int p, const Variant& v) {
 
 template <int M, int H>
 int walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st, bool configure, long long* blocks) {
-  const bool one = P.n_len == 1;
-  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * kSlotBytes) * (size_t)warps +
+  const bool one = P.n_len == 1, biased = P.bias != nullptr;
+  if (biased && !one) return LABS_ERR_INVALID_ARG;
+  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * slot_bytes(biased)) * (size_t)warps +
                       (one ? sizeof(uint64_t) * LABS_MAX_L : 0);
-  auto kern = one ? walk_kernel<M, H, true> : walk_kernel<M, H, false>;
+  auto kern = !one ? walk_kernel<M, H, false, false> : biased ? walk_kernel<M, H, true, true> : walk_kernel<M, H, true, false>;
   if (configure) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return LABS_ERR_CUDA;
@@ -891,8 +940,13 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
     P->len[0].E_thr_value = cfg->E_thr;
   }
   const int warps = cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8;
-  long long blocks = 0;
+  long long blocks = 0, blocks_biased = 0;
   if (s == LABS_OK) s = walk_variant(ctx, *P, v, warps, st, true, &blocks);
+  if (s == LABS_OK && policy) {  // the chunks run the biased instantiation: configure it as well
+    P->bias = logits;
+    s = walk_variant(ctx, *P, v, warps, st, true, &blocks_biased);
+    P->bias = nullptr;
+  }
   if (s == LABS_OK && cudaMemsetAsync(state, 0, (size_t)kStateBytes * (size_t)n, st) != cudaSuccess) s = LABS_ERR_CUDA;
   if (s == LABS_OK) {
     walk_init_kernel<<<1, 1, 0, st>>>(stats, P->E_thr_dev, P->len[0].E_thr_value, counter);
@@ -927,7 +981,7 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
       s = LABS_ERR_CUDA;
       break;
     }
-    s = walk_variant(ctx, *P, v, warps, st, false, &blocks);
+    s = walk_variant(ctx, *P, v, warps, st, false, policy ? &blocks_biased : &blocks);
   }
   delete P;
   return s;

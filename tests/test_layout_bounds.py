@@ -1,0 +1,119 @@
+"""Shared-memory index bounds of the walk kernel's layout, checked on the CPU for every length.
+
+A mirror of the layout rule (tiles of M neighbours at class indices q0 = 3 mod 4, the reversed arrays
+offset by Qr = 2 mod 4, lag groups padded to multiples of M/4 + 1) and of every index the scan, the
+Delta E finish, the P bookkeeping and the table update derive from it.  Any layout the rule accepts
+must keep every byte-window and table access inside its array; the kernel relies on this instead of
+run-time bounds checks.
+"""
+import pytest
+
+# CPU check of every shared-memory index the scan / table / P code touches, for all L, modes, p, M.
+kQOff, kDirBytes, kClassBytes, kCLen = 3, 1216, 608, 608
+
+def pos_q(skew, i):
+    return ((i - (1 if i & 1 else 2)) >> 1) + kQOff if skew else i - 1 + kQOff
+
+def q_pos(skew, cls, q):
+    return 2 * (q - kQOff) + (1 if cls else 2) if skew else q - kQOff + 1
+
+def layout(L, skew, p, M, H=1):
+    lam = 2 if skew else 1
+    G = (L - 1) // lam; NG = (G + 3) // 4; c = (L + 1) // 2; mlast = c if skew else L
+    tiles = []; qmax_end = 0
+    for cls in range(2 if skew else 1):
+        i_lo, i_hi = p + 1, mlast
+        if skew:
+            if (i_lo & 1) != cls: i_lo += 1
+            if (i_hi & 1) != cls: i_hi -= 1
+        if i_lo > i_hi: continue
+        q_lo, q_hi = pos_q(skew, i_lo), pos_q(skew, i_hi)
+        first = ((q_lo - 3) // 4) * 4 + 3
+        nt = (q_hi - first + 1 + M - 1) // M
+        tiles += [(cls, first + t * M) for t in range(nt)]
+        qmax_end = max(qmax_end, first + nt * M - 1)
+    Qr = qmax_end + ((2 - (qmax_end & 3)) & 3)
+    cap = kClassBytes if skew else kDirBytes
+    R = M // 4 + 1
+    if H == 1:
+        NGh = -(-NG // R) * R; NGend = NGh
+    else:
+        half = (NG + 1) // 2; NGh = -(-half // R) * R; rest = NG - NGh
+        NGend = NGh + (-(-rest // R) * R if rest > 0 else 0)
+    ok = (qmax_end + 4 * NGend + 8 < cap and Qr + 4 * NGend + 8 < cap and 2 * qmax_end < cap
+          and 4 * NGend <= kCLen)
+    return dict(lam=lam, G=G, NG=NG, c=c, mlast=mlast, tiles=tiles, Qr=Qr, cap=cap, ok=ok, NGh=NGh, NGend=NGend, R=R)
+
+
+
+VARIANTS = ((8, 1), (12, 1), (16, 1), (16, 2))
+
+
+def _cases():
+    for L in range(3, 577):
+        for skew in (0, 1):
+            if skew and L % 2 == 0:
+                continue
+            kk = (L - 1) // 2
+            for p in sorted(set([0, 1, 2, 3, 24, min(kk, 100), kk if skew else L - 1])):
+                if skew and p > kk:
+                    continue
+                if not skew and p >= L:
+                    continue
+                yield L, skew, p
+
+
+def _check(L, skew, p, M, H):
+    ly = layout(L, skew, p, M, H)
+    if not ly["ok"]:
+        return 0
+    words = ly["cap"] // 4
+    K = M // 4 + 1
+    covered = set()
+    c = ly["c"]
+    for cls, q0 in ly["tiles"]:
+        assert (q0 + 1) % 4 == 0 and (ly["Qr"] - q0 + 1) % 4 == 0
+        tf0 = (q0 + 1) >> 2
+        tb0 = ((ly["Qr"] - q0 + 1) >> 2) - M // 4
+        idx, idxb = [], []
+        for (ub, ue) in ([(0, ly["NGh"])] if H == 1 else [(0, ly["NGh"]), (ly["NGh"], ly["NGend"])]):
+            idx += [tf0 + ub + a for a in range(K)] + [tf0 + ub + u + K for u in range(ue - ub)]
+            idxb += [tb0 + ub + a for a in range(K)] + [tb0 + ub + u + K for u in range(ue - ub)]
+        assert min(idx) >= 0 and max(idx) < words and min(idxb) >= 0 and max(idxb) < words, (L, skew, p, M, q0)
+        for j in range(M):
+            q = q0 + j
+            m = q_pos(skew, cls, q)
+            if p + 1 <= m <= ly["mlast"]:
+                covered.add(m)
+            # finish / table update: windows s_{m +- lambda g} for g = 1..G and the neighbour itself
+            for g in (1, ly["G"]):
+                assert 0 <= q + g < ly["cap"] and 0 <= ly["Qr"] - q + g < ly["cap"], (L, skew, p, M, q, g)
+            assert 0 <= q < ly["cap"] and 0 <= ly["Qr"] - q < ly["cap"]
+            # table update: realigned words (q + 1) / 4 + u and (Qr - q + 1) / 4 + u, + 1, for u < NG
+            assert (q + 1) // 4 + ly["NG"] < words and (ly["Qr"] - q + 1) // 4 + ly["NG"] < words
+            # P bookkeeping: class index max(2q - q_f, 0) for every flipped position f of this class; the
+            # largest index comes from the smallest q_f (flipped positions lie in p+1..mlast)
+            f_lo = p + 1 + (1 if skew and ((p + 1) & 1) != cls else 0)
+            if f_lo <= ly["mlast"]:
+                assert max(2 * q - pos_q(skew, f_lo), 0) < ly["cap"], (L, skew, p, M, q)
+    if skew:
+        for f in range(p + 1, c):  # the mirror L + 1 - f of a pair flip: class index c + 6 - b - q_f
+            b = 1 if f & 1 else 2
+            assert pos_q(skew, L + 1 - f) == c + 6 - b - pos_q(skew, f)
+            # the pair term reads C16[c - m - 1]
+            if skew and p + 1 <= m < c:
+                assert 0 <= c - m - 1 < kCLen
+    assert covered == set(range(p + 1, ly["mlast"] + 1)), (L, skew, p, M)
+    return 1
+
+
+@pytest.mark.parametrize("M,H", VARIANTS)
+def test_layout_indices_stay_inside_their_arrays(M, H):
+    tested = sum(_check(L, skew, p, M, H) for L, skew, p in _cases())
+    assert tested > 1000
+
+
+def test_every_length_fits_some_variant():
+    for L in range(3, 577):
+        for skew in ((0, 1) if L % 2 else (0,)):
+            assert any(layout(L, skew, 0, M, H)["ok"] for M, H in VARIANTS), (L, skew)
