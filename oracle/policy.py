@@ -148,3 +148,18 @@ def loss_and_grads(p, x, free_mask, target, weight):
     logits, cache = forward(p, x)
     loss, dl = loss_and_dlogits(logits, free_mask, target, weight)
     return loss, backward(p, cache, dl), logits
+
+
+def adam_step(p, g, m1, m2, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in float32, elementwise:
+    m1 <- b1 m1 + (1 - b1) g,  m2 <- b2 m2 + (1 - b2) g^2,
+    p  <- p - lr (m1 / (1 - b1^t)) / (sqrt(m2 / (1 - b2^t)) + eps).
+    Returns (p, m1, m2) as new float32 arrays."""
+    f = np.float32
+    p, g, m1, m2 = (np.asarray(a, dtype=np.float32) for a in (p, g, m1, m2))
+    m1 = f(b1) * m1 + (f(1) - f(b1)) * g
+    m2 = f(b2) * m2 + (f(1) - f(b2)) * g * g
+    c1 = f(1) - f(b1) ** np.float32(t)
+    c2 = f(1) - f(b2) ** np.float32(t)
+    p = p - f(lr) * (m1 / c1) / (np.sqrt(m2 / c2) + f(eps))
+    return p.astype(np.float32), m1, m2

@@ -104,6 +104,29 @@ def test_adam_steps_reduce_the_loss(lg):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_adam_matches_restatement_and_refreshes_bf16(lg):
+    """Two optimizer steps equal the float32 Adam restatement applied to the GPU's own gradients, and the
+    BF16 weight copy the forward uses is refreshed: logits after the steps equal those of a network set
+    to the expected parameters."""
+    L, n, lr = 29, 16, 3e-3
+    w, _ = _batch(L, n, 21)
+    target = np.random.default_rng(6).integers(0, 14, size=n).astype(np.int32)
+    weight = np.random.default_rng(7).uniform(0.2, 2.0, size=n).astype(np.float32)
+    pol = lg.Policy(L, seed=12)
+    seqs = torch.from_numpy(w.view(np.int64)).cuda()
+    p = pol.get_params().cpu().numpy()
+    m1 = np.zeros_like(p)
+    m2 = np.zeros_like(p)
+    for t in (1, 2):
+        _, g = pol.train_step(seqs, target, weight, 0, 14, lr=lr, want_grads=True)
+        p, m1, m2 = opol.adam_step(p, g.cpu().numpy(), m1, m2, t, lr)
+    got = pol.get_params().cpu().numpy()
+    assert np.max(np.abs(got - p)) <= 1e-6, np.max(np.abs(got - p))
+    ref = lg.Policy(L, seed=0)
+    ref.set_params(got)
+    assert torch.equal(pol.forward(seqs), ref.forward(seqs))
+
+
 # ------------------------------------------------------------------------------------------------
 # Chunked and learned walks (labs_chunked_search)
 # ------------------------------------------------------------------------------------------------

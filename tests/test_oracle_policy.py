@@ -87,3 +87,18 @@ def test_loss_is_weighted_cross_entropy_over_free_positions():
     ce0 = np.log(np.exp(logits[0, [1, 4, 5]]).sum()) - logits[0, 4]
     ce1 = np.log(np.exp(logits[1, [0, 8]]).sum()) - logits[1, 8]
     assert np.isclose(loss, (3 * ce0 + ce1) / 4)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """Adam's bias correction makes the first step -lr * g / (|g| + eps): -lr sign(g) wherever |g| >> eps,
+    and nothing where g = 0; a second identical gradient moves by the same amount again."""
+    rng = np.random.default_rng(3)
+    p = rng.normal(size=200).astype(np.float32)
+    g = rng.normal(size=200).astype(np.float32)
+    g[::7] = 0.0
+    z = np.zeros_like(p)
+    p1, m1, m2 = policy.adam_step(p, g, z, z, 1, 1e-2)
+    step = np.where(g == 0, 0.0, -1e-2 * np.sign(g))
+    assert np.allclose(p1 - p, step, atol=1e-6)
+    p2, _, _ = policy.adam_step(p1, g, m1, m2, 2, 1e-2)
+    assert np.allclose(p2 - p1, step, atol=1e-6)
