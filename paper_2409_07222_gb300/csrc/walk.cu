@@ -121,24 +121,7 @@ __device__ __forceinline__ int slot_Pt(int word) { return word & 0xffff; }
 //   Delta E = base - 2 alpha s_m (a - 2 SC),   base = alpha^2 Q_m + 2 alpha sigma C_{gd} [pair],
 // alpha = 4 for a skew pair (m, m'), 2 otherwise; the pair's own product at lag gd = c - m is removed
 // with s_{m'} = sigma s_m, sigma = (-1)^{c-m} (Eq. 2).  base depends only on the table and the slot
-// word, so it is formed before the scan.
-__device__ __forceinline__ int delta_base(const ScanSmem& sm, const Layout& ly, int word) {
-  const int ms = slot_pos(word);
-  const int m = ms < 0 ? -ms : ms;
-  int b = slot_Pt(word);
-  if (ly.skew && m != ly.c && m != 0) {
-    const int gd = ly.c - m;
-    const int cg = 8 * (int)sm.C16[gd - 1];
-    b += (gd & 1) ? -cg : cg;
-  }
-  return b;
-}
-// 2 alpha s_m
-__device__ __forceinline__ int slot_sa(const Layout& ly, int ms) {
-  const int m = ms < 0 ? -ms : ms;
-  const int a2 = (ly.skew && m != ly.c) ? 8 : 4;
-  return ms < 0 ? -a2 : a2;
-}
+// word, so it is formed before the scan (prep_code).
 
 // The last accepted move, not yet folded into the slot words: its flipped positions f0 (and the mirror
 // f1 of a skew pair), their class and class indices, and their values before the flip.  Flipping f
@@ -154,27 +137,59 @@ struct PendingFlip {
   int cls, q0f, q1f, s0, s1, qmir;
 };
 
-template <int MH>
-__device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, const PendingFlip& pf, int q_first,
-                                          int (&wv)[MH]) {
+// Folds the pending move into the slot words of its class.  The class's (task, k) slots are spread over
+// all lanes, task fastest, so that neighbouring lanes touch different banks.
+template <int M, int H>
+__device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, const PendingFlip& pf, int* sl_w) {
+  constexpr int MH = M / H;
   const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(pf.cls));
   const int pmul = ly.skew ? -64 : -16;  // -4 alpha^2 for the neighbours that change
-  int v[MH];
-#pragma unroll
-  for (int k = 0; k < MH; k++) {
-    const int q = q_first + k;
-    v[k] = ((int)Fc[max(2 * q - pf.q0f, 0)] - 1) * pf.s0;
-    if (pf.pair) v[k] += ((int)Fc[max(2 * q - pf.q1f, 0)] - 1) * pf.s1;
+  const int qc = (pf.pair && pos_cls(ly, ly.c) == pf.cls) ? pos_q(ly, ly.c) : -1;  // the centre
+  const int m3 = ly.skew ? pf.qmir + pf.q0f : -1;                                  // 3 q of the pair-product
+  const int qm = (m3 >= 0 && m3 % 3 == 0) ? m3 / 3 : -1;                           // exclusion
+  const int q1f = pf.pair ? pf.q1f : (1 << 20);  // single flip: the f1 term reads a pad
+  const int nt = ly.ntiles[pf.cls] * H;          // tasks of the class
+  const int task0 = (pf.cls ? ly.ntiles[0] : 0) * H;
+  const int qt = ly.tile_first[pf.cls];
+  int tl = lane_id() % nt, k = lane_id() / nt;
+  const int step_t = 32 % nt, step_k = 32 / nt;
+  for (; k < MH;) {
+    const int task = task0 + tl;
+    const int q = qt + (tl / H) * M + (tl % H) * MH + k;
+    const int idx = ((task >> 5) * MH + k) * 32 + (task & 31);
+    int wv = sl_w[idx];
+    const int ms = slot_pos(wv);
+    int v = ((int)Fc[max(2 * q - pf.q0f, 0)] - 1) * pf.s0;
+    if (q == qm) v = 0;
+    v += ((int)Fc[max(2 * q - q1f, 0)] - 1) * pf.s1;
+    if (ms != 0 && q != pf.q0f && q != qc) wv += pmul * v;
+    if (ms != 0 && q == pf.q0f) wv = slot_pack(-ms, slot_Pt(wv));
+    sl_w[idx] = wv;
+    tl += step_t;
+    k += step_k;
+    if (tl >= nt) {
+      tl -= nt;
+      k++;
+    }
   }
-#pragma unroll
-  for (int k = 0; k < MH; k++) {
-    const int q = q_first + k;
-    const int ms = slot_pos(wv[k]);
-    int vk = v[k];
-    if (ly.skew && 3 * q - pf.q0f == pf.qmir) vk -= ((int)Fc[2 * q - pf.q0f] - 1) * pf.s0;  // index >= 3 here
-    if (ms != 0 && q != pf.q0f && !(pf.pair && (ms == ly.c || ms == -ly.c))) wv[k] += pmul * vk;
-    if (ms != 0 && q == pf.q0f) wv[k] = slot_pack(-ms, slot_Pt(wv[k]));
-  }
+  __syncwarp();
+}
+
+// Finish code of a slot, formed by prep: base * 32 + code, where base is the constant part of the
+// neighbour's Delta E and code = 2 alpha s_m + 8 (0, 4, 12 or 16), plus 1 for the neighbour
+// the last move flipped (the state just left), or 31 for no neighbour.  Branch-free: a slot without a
+// pair term reads the table's last entry, which is always zero (lags beyond G).
+constexpr int kNoSlot = 31;
+__device__ __forceinline__ int prep_code(const ScanSmem& sm, const Layout& ly, int word, bool back) {
+  const int ms = slot_pos(word);
+  const int m = ms < 0 ? -ms : ms;
+  const bool pair = ly.skew && m != ly.c && m != 0;
+  const int gd = pair ? ly.c - m : kCLen;
+  const int cg = 8 * (int)sm.C16[gd - 1];
+  const int base = slot_Pt(word) + ((gd & 1) ? -cg : cg);
+  const int a2 = pair ? 8 : 4;
+  const int code = (ms < 0 ? 8 - a2 : 8 + a2) + (back ? 1 : 0);
+  return ms == 0 ? kNoSlot : base * 32 + code;
 }
 
 // Task of `lane` in pass `ps`: tile (class, q0), lag range h, whether it exists.
@@ -367,6 +382,10 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     while (flips < budget && taken < chunk) {
       if (need_start) start_segment();
       it++;
+      if (pend.on) {  // the last move's P bookkeeping
+        fold_flip<M, H>(sm, ly, pend, sl_w);
+        pend.on = false;
+      }
       // ---- scan; each lane keeps its best (key, m) where key orders the choice: Delta E, or the
       //      biased score Delta E - lambda * logit[m] mapped to an order-preserving integer
       int bk = INT32_MAX, bm = INT32_MAX, bdE = 0;
@@ -374,19 +393,18 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       for (int ps = 0; ps < NP; ps++) {
         int cls, q0, h;
         const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+        const int q_first = q0 + h * MH;
         {
-          // prep, while no accumulator is live: fold the last move into the slot words and park each
-          // neighbour's base in the key array
+          // prep, while no accumulator is live: park each neighbour's Delta E base with its finish code
+          // in the key array
           int wv[MH];
 #pragma unroll
           for (int k = 0; k < MH; k++) wv[k] = sl_w[(ps * MH + k) * 32 + lane];
-          if (pend.on && has && cls == pend.cls) {
-            fold_flip<MH>(sm, ly, pend, q0 + h * MH, wv);
+          // the move back: the neighbour flipped by the previous move of this segment
+          const int kback = (mprev && pos_cls(ly, mprev) == cls) ? pos_q(ly, mprev) - q_first : -1;
 #pragma unroll
-            for (int k = 0; k < MH; k++) sl_w[(ps * MH + k) * 32 + lane] = wv[k];
-          }
-#pragma unroll
-          for (int k = 0; k < MH; k++) sl_k[(ps * MH + k) * 32 + lane] = delta_base(sm, ly, wv[k]);
+          for (int k = 0; k < MH; k++)
+            sl_k[(ps * MH + k) * 32 + lane] = prep_code(sm, ly, wv[k], k == kback);
         }
         int acc[M];
 #pragma unroll
@@ -405,22 +423,25 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         }
         // finish: keys of this pass's neighbours, then their minimum by a tree of strict comparisons
         // (the slots of a pass are in increasing m, so the left operand wins ties: smallest (key, m))
+        const int m_first = q_pos(ly, cls, q_first);
         int kv[MH], mv[MH], dv[MH];
 #pragma unroll
         for (int k = 0; k < MH; k++) {
           const int t = ps * MH + k;
-          const int ms = slot_pos(sl_w[t * 32 + lane]);
-          const int m = ms < 0 ? -ms : ms;
+          const int pk = sl_k[t * 32 + lane];
+          const int code = pk & 31;
+          const int m = m_first + ly.lam * k;
           const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
-          const int d = sl_k[t * 32 + lane] - slot_sa(ly, ms) * (a - 2 * SC);
+          const int d = (pk >> 5) - ((code & 30) - 8) * (a - 2 * SC);
           int key = d;
-          if (BIASED && m) {
-            float l = bias[m - 1];
+          if (BIASED) {
+            float l = bias[min(max(m, 1), ly.L) - 1];
             if (!isfinite(l)) l = 0.f;  // a missing or broken proposal falls back to the plain choice
             key = float_key(fmaf(-P.lambda, l, (float)d));
           }
-          if (!m) key = INT32_MAX;
-          if (m && m == mprev) {
+          if (code == kNoSlot) {
+            key = INT32_MAX;
+          } else if (code & 1) {
             kprev = key;  // the state just left: certainly in the Bloom filter
             key = INT32_MAX;
           }
@@ -437,21 +458,38 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
             if (kv[k + st] < kv[k]) {
               kv[k] = kv[k + st];
               mv[k] = mv[k + st];
-              dv[k] = dv[k + st];
+              if (BIASED) dv[k] = dv[k + st];
             }
         if (kv[0] < bk || (kv[0] == bk && kv[0] != INT32_MAX && mv[0] < bm)) {
           bk = kv[0];
           bm = mv[0];
-          bdE = dv[0];
+          bdE = BIASED ? dv[0] : kv[0];
         }
       }
       // ---- select: smallest (key, m) whose neighbour is not in the Bloom filter
       int mstar = -1, kstar = 0, dstar = 0;
       uint64_t nfp = 0;
       for (int guard = 0; guard <= S * 32; guard++) {
-        const int kmin = warp_min_i32(bk);
-        if (kmin == INT32_MAX) break;
-        const int mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+        int kmin, mm;
+        if (!BIASED) {
+          // one reduction on (key, m) while the minimum key is inside the 22-bit window: a key clamped to
+          // the window's edge can only tie with the minimum when the minimum is at that edge itself
+          constexpr int kHalf = 1 << 21;
+          const unsigned comp = bk == INT32_MAX ? 0xffffffffu
+                                                : ((unsigned)(min(max(bk, -kHalf), kHalf - 1) + kHalf) << 10) | (unsigned)bm;
+          const unsigned cmin = warp_min_u32(comp);
+          if (cmin == 0xffffffffu) break;
+          kmin = (int)(cmin >> 10) - kHalf;
+          mm = (int)(cmin & 1023u);
+          if (kmin == -kHalf || kmin == kHalf - 1) {
+            kmin = warp_min_i32(bk);
+            mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+          }
+        } else {
+          kmin = warp_min_i32(bk);
+          if (kmin == INT32_MAX) break;
+          mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+        }
         const unsigned owner = __ballot_sync(kFull, bk == kmin && bm == mm);
         const int dmm = __shfl_sync(kFull, bdE, __ffs(owner) - 1);
         uint64_t cand = fp ^ (ONE ? ztab[mm - 1] : zobrist(zkey, mm));
