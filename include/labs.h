@@ -282,8 +282,18 @@ void labs_policy_destroy(labs_policy* policy);
 int labs_policy_set_params(labs_policy* policy, const float* params, void* stream);
 /* Copies the FP32 master parameters to device memory [n]. */
 int labs_policy_get_params(labs_policy* policy, float* params, void* stream);
-/* logits [n][L] FP32 (device) of n packed sequences (device). */
+/*
+ * logits [n][L] FP32 (device) of n packed sequences (device).  Runs on the tensor cores (tcgen05): the
+ * convolution outputs are stored as BF16 between layers (training keeps them in FP32), every sum
+ * accumulates in FP32.  Workspace: about 173 B x L per sample for up to 16,384 samples at a time.
+ * A tensor-core wait that expires is reported by labs_policy_sync_status.
+ */
 int labs_policy_forward(labs_policy* policy, const uint64_t* seqs, int64_t n, float* logits, void* stream);
+/*
+ * Synchronises `stream` and returns LABS_ERR_TIMEOUT if a tensor-core wait of an earlier
+ * labs_policy_forward expired (its logits are then invalid), else LABS_OK; clears the flag.
+ */
+int labs_policy_sync_status(labs_policy* policy, void* stream);
 /*
  * One training step on n samples: forward, weighted cross-entropy over the free positions
  * [free_lo, free_hi] (0-based, the same for every sample) toward target[q] (0-based position), backward,
@@ -306,7 +316,8 @@ int labs_policy_train_step(labs_policy* policy, const uint64_t* seqs, const int3
  *   logits_log [n_chunks][n_walks][L] FP32: the logits each chunk used;
  *   state_log  [n_chunks][n_walks][W] uint64: every walk's sequence when its chunk began;
  *   move_log   [n_chunks][n_walks][2] int32: the chunk's first move (position, Delta E), (-1, 0) if none.
- *   Workspace: about 5.5 KB per walk.
+ *   Workspace: about 5.5 KB per walk.  With a policy the call synchronises `stream` at its end and returns
+ *   LABS_ERR_TIMEOUT if a tensor-core wait of the network expired.
  */
 int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* policy, float lambda, int chunk,
                         const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,

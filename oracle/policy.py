@@ -90,14 +90,25 @@ def conv_backward(h, w, dy):
     return dh, dw, db
 
 
-def forward(p, x):
-    """Returns (logits [N, L], cache)."""
+def bf16_round(a):
+    """Rounds to bfloat16 the way the device stores an FP32 value as BF16: first to float32, then to the
+    nearest bfloat16 (ties to even) by rounding away the low 16 bits of the float32 encoding."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(f.shape)
+
+
+def forward(p, x, act_bf16=False):
+    """Returns (logits [N, L], cache).  act_bf16: the three convolution outputs (after ReLU) are stored
+    as bfloat16 before the next layer reads them, as the device's inference path does."""
+    r = bf16_round if act_bf16 else (lambda v: v)
     c1 = conv_forward(x, p["w1"], p["b1"])
-    h1 = np.maximum(c1, 0)
+    h1 = r(np.maximum(c1, 0))
     c2 = conv_forward(h1, p["w2"], p["b2"])
-    h2 = np.maximum(c2, 0)
+    h2 = r(np.maximum(c2, 0))
     c3 = conv_forward(h2, p["w3"], p["b3"])
-    h3 = np.maximum(c3, 0)
+    h3 = r(np.maximum(c3, 0))
     N, C, L = h3.shape
     f = h3.reshape(N, C * L)
     z = f @ p["W4"].T + p["b4"]

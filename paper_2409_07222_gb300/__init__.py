@@ -254,6 +254,7 @@ class Policy:
         out = torch.empty((s.shape[0], self.L), dtype=torch.float32, device=self.dev)
         _lib.check(load().labs_policy_forward(self.h, _ptr(s), s.shape[0], _ptr(out), _stream(self.dev)),
                    "labs_policy_forward")
+        _lib.check(load().labs_policy_sync_status(self.h, _stream(self.dev)), "labs_policy_forward")
         return out
 
     def train_step(self, seqs, target, weight, free_lo, free_hi, lr, want_grads=False):

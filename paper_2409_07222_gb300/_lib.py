@@ -43,6 +43,7 @@ SIGNATURES = {
     "labs_policy_set_params": (_ci, [_P, _P, _P]),
     "labs_policy_get_params": (_ci, [_P, _P, _P]),
     "labs_policy_forward": (_ci, [_P, _P, _i64, _P, _P]),
+    "labs_policy_sync_status": (_ci, [_P, _P]),
     "labs_policy_train_step": (_ci, [_P, _P, _P, _P, _i64, _ci, _ci, ctypes.c_float, _P, _P, _P]),
 }
 

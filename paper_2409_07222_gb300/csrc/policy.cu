@@ -8,11 +8,14 @@
 // FP32.  Training minimises the weighted cross-entropy over each sample's free positions toward the
 // flip it took, with Adam.
 //
-// Kernels (CUDA cores, FP32 FMA): direct convolution tiles (64 output channels x 128 positions per
-// block, 8x4 outputs per thread, input and weight chunks staged in shared memory) for the forward pass
-// and the data gradient (the same kernel on flipped, transposed weights); an outer-product kernel for
-// the weight gradient; a 64x64-tile GEMM with strided operands for the two dense layers and their
-// gradients.
+// Inference (labs_policy_forward, the learned walks) runs on the tensor cores (policy_tc.cu): BF16
+// channels-last activations, tcgen05 implicit-GEMM convolutions and a tcgen05 GEMM for the 64 L -> 256
+// layer; the first convolution and the 256 -> L layer stay on CUDA cores.
+// Training (labs_policy_train_step) runs on CUDA cores with FP32 activations: direct convolution tiles
+// (64 output channels x 128 positions per block, 8x4 outputs per thread, input and weight chunks staged
+// in shared memory) for the forward pass and the data gradient (the same kernel on flipped, transposed
+// weights); an outer-product kernel for the weight gradient; a 64x64-tile GEMM with strided operands for
+// the two dense layers and their gradients.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -21,6 +24,7 @@
 
 #include "labs_core.cuh"
 #include "labs_internal.h"
+#include "policy_tc.h"
 
 struct labs_policy {
   labs_ctx* ctx;
@@ -35,9 +39,16 @@ struct labs_policy {
   float* m1;
   float* m2;
   long long step;
-  // activations for up to cap_n samples
+  // training activations for up to cap_n samples
   long long cap_n;
   float *x, *h1, *h2, *h3, *a, *logits, *d_logits, *da, *dh_a, *dh_b, *wsum, *loss;
+  // tensor-core inference: weight images (rebuilt when tc_stale) and activations for up to cap_i samples
+  __nv_bfloat16 *img2, *img3, *W4p;
+  bool tc_stale;
+  int* tc_err;
+  long long cap_i;
+  float *xi, *ai;
+  __nv_bfloat16 *h1b, *h2b, *h3b;
 };
 
 namespace labsg {
@@ -416,6 +427,46 @@ void forward(labs_policy* P, long long n, float* logits, cudaStream_t st) {
        m + P->off[9], 0, (const float*)nullptr, 0);
 }
 
+int ensure_inference(labs_policy* P, long long n) {
+  if (n <= P->cap_i) return LABS_OK;
+  void* bufs[] = {P->xi, P->ai, P->h1b, P->h2b, P->h3b};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  P->xi = P->ai = nullptr;
+  P->h1b = P->h2b = P->h3b = nullptr;
+  P->cap_i = 0;
+  const size_t L = (size_t)P->L, act = (size_t)n * L * kC * 2;
+  if (cudaMalloc(&P->xi, 4 * (size_t)n * 2 * L) != cudaSuccess || cudaMalloc(&P->ai, 4 * (size_t)n * kHid) != cudaSuccess ||
+      cudaMalloc(&P->h1b, act) != cudaSuccess || cudaMalloc(&P->h2b, act) != cudaSuccess ||
+      cudaMalloc(&P->h3b, act) != cudaSuccess)
+    return LABS_ERR_NOMEM;
+  P->cap_i = n;
+  return LABS_OK;
+}
+
+// Inference for n packed sequences: features, conv1 (CUDA cores, BF16 channels-last out), conv2 and
+// conv3 (tcgen05), the 64 L -> 256 layer (tcgen05), the 256 -> L layer (CUDA cores).
+int forward_tc(labs_policy* P, const uint64_t* seqs, long long n, float* logits, cudaStream_t st) {
+  const int L = P->L;
+  const float* m = P->master;
+  const int sms = P->ctx->num_sms;
+  int s = LABS_OK;
+  if (P->tc_stale) {
+    s = tc::tc_prepare_weights(m + P->off[2], m + P->off[4], m + P->off[6], L, P->img2, P->img3, P->W4p, st);
+    if (s != LABS_OK) return s;
+    P->tc_stale = false;
+  }
+  features_kernel<<<(unsigned)std::min<long long>((n + 3) / 4, 4096), 128, 0, st>>>(seqs, L, n, P->xi);
+  s = tc::tc_conv1(P->xi, P->wbf + P->off[0], m + P->off[1], P->h1b, L, n, sms, st);
+  if (s == LABS_OK) s = tc::tc_conv64(P->h1b, P->img2, m + P->off[3], P->h2b, L, n, sms, P->tc_err, st);
+  if (s == LABS_OK) s = tc::tc_conv64(P->h2b, P->img3, m + P->off[5], P->h3b, L, n, sms, P->tc_err, st);
+  if (s == LABS_OK) s = tc::tc_dense(P->h3b, P->W4p, m + P->off[7], P->ai, n, kC * L, P->tc_err, st);
+  if (s != LABS_OK) return s;
+  gemm(st, (int)n, L, (long long)kHid, P->ai, (long long)kHid, 1ll, P->wbf + P->off[8], 1ll, (long long)kHid, logits, L,
+       m + P->off[9], 0, (const float*)nullptr, 0);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
 
 int policy_length(const labs_policy* P) { return P->L; }
@@ -455,11 +506,15 @@ int labs_policy_create(labs_ctx* ctx, int L, uint64_t seed, labs_policy** out) {
       cudaMalloc(&P->grad, 4 * n) != cudaSuccess || cudaMalloc(&P->m1, 4 * n) != cudaSuccess ||
       cudaMalloc(&P->m2, 4 * n) != cudaSuccess || cudaMalloc(&P->wT2, 2 * sizes[2]) != cudaSuccess ||
       cudaMalloc(&P->wT3, 2 * sizes[4]) != cudaSuccess || cudaMalloc(&P->wsum, 8) != cudaSuccess ||
-      cudaMalloc(&P->loss, 8) != cudaSuccess) {
+      cudaMalloc(&P->loss, 8) != cudaSuccess || cudaMalloc(&P->img2, 2 * sizes[2]) != cudaSuccess ||
+      cudaMalloc(&P->img3, 2 * sizes[4]) != cudaSuccess || cudaMalloc(&P->W4p, 2 * sizes[6]) != cudaSuccess ||
+      cudaMalloc(&P->tc_err, sizeof(int)) != cudaSuccess) {
     labs_policy_destroy(P);
     return LABS_ERR_NOMEM;
   }
   cudaMemset(P->master, 0, 4 * n);
+  cudaMemset(P->tc_err, 0, sizeof(int));
+  P->tc_stale = true;
   cudaMemset(P->m1, 0, 4 * n);
   cudaMemset(P->m2, 0, 4 * n);
   // He-uniform weights, zero biases
@@ -482,7 +537,8 @@ void labs_policy_destroy(labs_policy* P) {
   cudaSetDevice(P->ctx->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {P->master, P->wbf, P->grad, P->m1, P->m2, P->wT2, P->wT3, P->wsum, P->loss, P->x, P->h1,
-                  P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b};
+                  P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b, P->img2, P->img3,
+                  P->W4p, P->tc_err, P->xi, P->ai, P->h1b, P->h2b, P->h3b};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete P;
@@ -497,6 +553,7 @@ int labs_policy_set_params(labs_policy* P, const float* params, void* stream) {
   cudaMemsetAsync(P->m1, 0, 4 * (size_t)P->n_params, st);
   cudaMemsetAsync(P->m2, 0, 4 * (size_t)P->n_params, st);
   P->step = 0;
+  P->tc_stale = true;
   return cuda_status(cudaGetLastError());
 }
 
@@ -510,16 +567,13 @@ int labs_policy_forward(labs_policy* P, const uint64_t* seqs, int64_t n, float* 
   if (!P || n < 0 || (n > 0 && (!seqs || !logits))) return LABS_ERR_INVALID_ARG;
   if (n == 0) return LABS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const long long chunk = 8192;
-  int s = ensure_acts(P, std::min<long long>(n, chunk));
+  const long long chunk = 16384;
+  int s = ensure_inference(P, std::min<long long>(n, chunk));
   if (s != LABS_OK) return s;
   const int W = (P->L + 63) / 64;
-  for (long long b = 0; b < n; b += chunk) {
-    const long long m = std::min<long long>(chunk, n - b);
-    features_kernel<<<(unsigned)std::min<long long>((m + 3) / 4, 4096), 128, 0, st>>>(seqs + b * W, P->L, m, P->x);
-    forward(P, m, logits + b * P->L, st);
-  }
-  return cuda_status(cudaGetLastError());
+  for (long long b = 0; b < n && s == LABS_OK; b += chunk)
+    s = forward_tc(P, seqs + b * W, std::min<long long>(chunk, n - b), logits + b * P->L, st);
+  return s;
 }
 
 int labs_policy_train_step(labs_policy* P, const uint64_t* seqs, const int32_t* target, const float* weight, int64_t n,
@@ -577,8 +631,18 @@ int labs_policy_train_step(labs_policy* P, const uint64_t* seqs, const int32_t* 
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)P->step), c2 = 1.f - powf(b2, (float)P->step);
     adam_kernel<<<1024, 256, 0, st>>>(P->master, g, P->m1, P->m2, P->wbf, P->n_params, lr, b1, b2, 1e-8f, c1, c2);
+    P->tc_stale = true;
   }
   return cuda_status(cudaGetLastError());
+}
+
+int labs_policy_sync_status(labs_policy* P, void* stream) {
+  if (!P) return LABS_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return LABS_ERR_CUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, P->tc_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return LABS_ERR_CUDA;
+  if (e && cudaMemset(P->tc_err, 0, sizeof(int)) != cudaSuccess) return LABS_ERR_CUDA;
+  return e ? LABS_ERR_TIMEOUT : LABS_OK;
 }
 
 }  // extern "C"

@@ -1022,6 +1022,10 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
     s = walk_variant(ctx, *P, v, warps, st, false, policy ? &blocks_biased : &blocks);
   }
   delete P;
+  if (policy) {  // the network's tensor-core waits: a failure makes the logits of that chunk invalid
+    const int ps = labs_policy_sync_status(policy, st);
+    if (s == LABS_OK) s = ps;
+  }
   return s;
 }
 

@@ -102,3 +102,13 @@ def test_adam_first_step_is_lr_times_sign():
     assert np.allclose(p1 - p, step, atol=1e-6)
     p2, _, _ = policy.adam_step(p1, g, m1, m2, 2, 1e-2)
     assert np.allclose(p2 - p1, step, atol=1e-6)
+
+
+def test_bf16_round_matches_torch():
+    """bf16_round against torch's float32 -> bfloat16 conversion (round to nearest even), including ties
+    and values that are exact in bfloat16."""
+    rng = np.random.default_rng(8)
+    v = np.concatenate([rng.normal(size=2000) * 10.0 ** rng.integers(-5, 5, size=2000),
+                        [0.0, 1.0, -2.5, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 255.0, 257.0]]).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(policy.bf16_round(v), ref)
