@@ -285,7 +285,8 @@ int labs_policy_get_params(labs_policy* policy, float* params, void* stream);
 /*
  * logits [n][L] FP32 (device) of n packed sequences (device).  Runs on the tensor cores (tcgen05): the
  * convolution outputs are stored as BF16 between layers (training keeps them in FP32), every sum
- * accumulates in FP32.  Workspace: about 173 B x L per sample for up to 16,384 samples at a time.
+ * accumulates in FP32.  Workspace: about 0.2 KB x L per sample for up to 8,192 samples at a time.
+ * A sample's logits do not depend on the batch it is evaluated in (fixed summation order).
  * A tensor-core wait that expires is reported by labs_policy_sync_status.
  */
 int labs_policy_forward(labs_policy* policy, const uint64_t* seqs, int64_t n, float* logits, void* stream);

@@ -47,7 +47,7 @@ struct labs_policy {
   bool tc_stale;
   int* tc_err;
   long long cap_i;
-  float *xi, *ai;
+  float *xi, *ai, *part;
   __nv_bfloat16 *h1b, *h2b, *h3b;
 };
 
@@ -429,14 +429,16 @@ void forward(labs_policy* P, long long n, float* logits, cudaStream_t st) {
 
 int ensure_inference(labs_policy* P, long long n) {
   if (n <= P->cap_i) return LABS_OK;
-  void* bufs[] = {P->xi, P->ai, P->h1b, P->h2b, P->h3b};
+  void* bufs[] = {P->xi, P->ai, P->part, P->h1b, P->h2b, P->h3b};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  P->xi = P->ai = nullptr;
+  P->xi = P->ai = P->part = nullptr;
   P->h1b = P->h2b = P->h3b = nullptr;
   P->cap_i = 0;
   const size_t L = (size_t)P->L, act = (size_t)n * L * kC * 2;
+  const size_t part_rows = (size_t)tc::tc_dense_splits(kC * P->L) * (size_t)n;  // split-K partial sums
   if (cudaMalloc(&P->xi, 4 * (size_t)n * 2 * L) != cudaSuccess || cudaMalloc(&P->ai, 4 * (size_t)n * kHid) != cudaSuccess ||
+      cudaMalloc(&P->part, 4 * part_rows * kHid) != cudaSuccess ||
       cudaMalloc(&P->h1b, act) != cudaSuccess || cudaMalloc(&P->h2b, act) != cudaSuccess ||
       cudaMalloc(&P->h3b, act) != cudaSuccess)
     return LABS_ERR_NOMEM;
@@ -460,7 +462,7 @@ int forward_tc(labs_policy* P, const uint64_t* seqs, long long n, float* logits,
   s = tc::tc_conv1(P->xi, P->wbf + P->off[0], m + P->off[1], P->h1b, L, n, sms, st);
   if (s == LABS_OK) s = tc::tc_conv64(P->h1b, P->img2, m + P->off[3], P->h2b, L, n, sms, P->tc_err, st);
   if (s == LABS_OK) s = tc::tc_conv64(P->h2b, P->img3, m + P->off[5], P->h3b, L, n, sms, P->tc_err, st);
-  if (s == LABS_OK) s = tc::tc_dense(P->h3b, P->W4p, m + P->off[7], P->ai, n, kC * L, P->tc_err, st);
+  if (s == LABS_OK) s = tc::tc_dense(P->h3b, P->W4p, m + P->off[7], P->part, P->ai, n, kC * L, sms, P->tc_err, st);
   if (s != LABS_OK) return s;
   gemm(st, (int)n, L, (long long)kHid, P->ai, (long long)kHid, 1ll, P->wbf + P->off[8], 1ll, (long long)kHid, logits, L,
        m + P->off[9], 0, (const float*)nullptr, 0);
@@ -538,7 +540,7 @@ void labs_policy_destroy(labs_policy* P) {
   cudaDeviceSynchronize();
   void* ptrs[] = {P->master, P->wbf, P->grad, P->m1, P->m2, P->wT2, P->wT3, P->wsum, P->loss, P->x, P->h1,
                   P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b, P->img2, P->img3,
-                  P->W4p, P->tc_err, P->xi, P->ai, P->h1b, P->h2b, P->h3b};
+                  P->W4p, P->tc_err, P->xi, P->ai, P->part, P->h1b, P->h2b, P->h3b};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete P;
@@ -567,7 +569,7 @@ int labs_policy_forward(labs_policy* P, const uint64_t* seqs, int64_t n, float* 
   if (!P || n < 0 || (n > 0 && (!seqs || !logits))) return LABS_ERR_INVALID_ARG;
   if (n == 0) return LABS_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const long long chunk = 16384;
+  const long long chunk = 8192;
   int s = ensure_inference(P, std::min<long long>(n, chunk));
   if (s != LABS_OK) return s;
   const int W = (P->L + 63) / 64;

@@ -91,9 +91,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// 64 consecutive FP32 columns of this thread's TMEM lane, one load and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,"
+      "%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,"
+      "%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int j = 0; j < 64; j++) v[j] = __uint_as_float(r[j]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// 16-byte asynchronous global -> shared copy; valid = false writes zeros (nothing is read).
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -105,233 +136,306 @@ constexpr int kATile = 8 * kALbo;            // 17,536 B
 constexpr int kWLbo = 64 * 16;               // K-chunk stride of one tap's weights (1024 B)
 constexpr int kWTap = 8 * kWLbo;             // 8,192 B
 constexpr int kWImg = 9 * kWTap;             // 73,728 B
-constexpr int kConvSmem = kWImg + kATile + 1024;
+constexpr int kConvSmem = kWImg + 2 * kATile + 1024;
 
-__global__ void __launch_bounds__(128, 2) conv64_tc_kernel(const __nv_bfloat16* __restrict__ in,
-                                                           const __nv_bfloat16* __restrict__ wimg,
-                                                           const float* __restrict__ bias,
-                                                           __nv_bfloat16* __restrict__ out, int L, long long n,
-                                                           int tiles_per_sample, int* err) {
+// Warp-specialised: warps 0-3 fetch input tiles (cp.async) and drain accumulators, warp 4 issues the
+// MMAs.  Two input buffers and two TMEM accumulators; per buffer b four mbarriers:
+//   full[b]  -- the tile in buffer b has landed (128 arrivals)      -> the MMA warp may start,
+//   mma[b]   -- the MMAs reading buffer b are done (commit)         -> buffer b may be refilled and
+//                                                                      accumulator b read out,
+//   drain[b] -- accumulator b has been read out (128 arrivals)      -> the MMA warp may overwrite it.
+// Tile j of the CTA uses buffer and accumulator j & 1; every barrier completes once per use of b, so
+// the parity of use u = j >> 1 is u & 1.
+constexpr int kConvThreads = 160;
+
+__device__ __forceinline__ void mbar_init_n(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)));
+}
+// cp.async completion of this thread's copies counted as one arrival on bar (non-blocking).
+__device__ __forceinline__ void cp_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+__global__ void __launch_bounds__(kConvThreads, 2) conv64_tc_kernel(const __nv_bfloat16* __restrict__ in,
+                                                                    const __nv_bfloat16* __restrict__ wimg,
+                                                                    const float* __restrict__ bias,
+                                                                    __nv_bfloat16* __restrict__ out, int L, long long n,
+                                                                    int tiles_per_sample, int* err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
   unsigned char* Ws = base;
-  unsigned char* As = base + kWImg;
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t full[2], mmad[2], drain[2], wbar;
   __shared__ float bias_s[64];
+  __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < kWImg / 16; e += 128)
-    reinterpret_cast<uint4*>(Ws)[e] = reinterpret_cast<const uint4*>(wimg)[e];
-  if (tid < 64) bias_s[tid] = bias[tid];
-  if (warp == 0) tmem_alloc(&tmem_base, 64);
-  if (tid == 0) mbar_init(&bar);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16(128, 64);
-  const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
-  uint32_t phase = 0;
   const long long n_tiles = n * tiles_per_sample;
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long long s = tile / tiles_per_sample;
-    const int i0 = (int)(tile % tiles_per_sample) * 128;
-    const __nv_bfloat16* src = in + s * (long long)L * 64;
-    for (int e = tid; e < kRows * 8; e += 128) {
-      const int r = e >> 3, c8 = e & 7, pos = i0 - 4 + r;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (pos >= 0 && pos < L) v = *reinterpret_cast<const uint4*>(src + (long long)pos * 64 + c8 * 8);
-      *reinterpret_cast<uint4*>(As + c8 * kALbo + r * 16) = v;
+  const long long my_tiles = (long long)blockIdx.x < n_tiles ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto tile_id = [&](long long j) { return (long long)blockIdx.x + j * gridDim.x; };
+  if (tid < 64) bias_s[tid] = bias[tid];
+  if (warp == 0) tmem_alloc(&tmem_base, 128);
+  if (tid == 0) {
+    for (int b = 0; b < 2; b++) {
+      mbar_init_n(&full[b], 128);
+      mbar_init_n(&mmad[b], 1);
+      mbar_init_n(&drain[b], 128);
     }
-    fence_smem_to_async();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (tid == 0) {
-#pragma unroll 1
-      for (int t = 0; t < 9; t++)
-#pragma unroll
-        for (int c = 0; c < 4; c++)
-          mma_bf16(tmem, sdesc(a0 + 16 * t + 2 * c * kALbo, kALbo, 128), sdesc(w0 + t * kWTap + 2 * c * kWLbo, kWLbo, 128),
-                   idesc, (t | c) ? 1u : 0u);
-      mma_commit(&bar);
-    }
-    const bool ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicExch(err, 1);
-      break;
-    }
-    fence_after();
-    const int i = i0 + warp * 32 + lane;
-    __nv_bfloat16* dst = out + (s * (long long)L + i) * 64;
-#pragma unroll
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      uint32_t w[8];
-#pragma unroll
-      for (int j = 0; j < 8; j++)
-        w[j] = pack_bf16(fmaxf(v[2 * j] + bias_s[c0 + 2 * j], 0.f), fmaxf(v[2 * j + 1] + bias_s[c0 + 2 * j + 1], 0.f));
-      if (i < L) {
-        reinterpret_cast<uint4*>(dst + c0)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<uint4*>(dst + c0)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      }
-    }
-    fence_before();
-    __syncthreads();  // the next tile overwrites the input tile and the accumulator
-    fence_after();
+    mbar_init_n(&wbar, 128);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 64);
+  if (warp < 4) {
+    // ---- loader / drain warps
+    for (int e = tid; e < kWImg / 16; e += 128) cp16(Ws + 16 * e, reinterpret_cast<const uint4*>(wimg) + e, true);
+    cp_arrive(&wbar);
+    for (long long j = 0; j <= my_tiles; j++) {
+      // fetch tile j into buffer j & 1 once the MMAs of tile j - 2 have released it
+      if (j < my_tiles) {
+        const int b = (int)(j & 1);
+        if (j >= 2 && !mbar_wait(&mmad[b], (uint32_t)(((j >> 1) - 1) & 1))) atomicExch(&fail, 1);
+        unsigned char* As = base + kWImg + b * kATile;
+        const long long tile = tile_id(j);
+        const long long s = tile / tiles_per_sample;
+        const int i0 = (int)(tile % tiles_per_sample) * 128;
+        const __nv_bfloat16* src = in + s * (long long)L * 64;
+        for (int e = tid; e < kRows * 8; e += 128) {
+          const int r = e >> 3, c8 = e & 7, pos = i0 - 4 + r;
+          const bool ok = pos >= 0 && pos < L;
+          cp16(As + c8 * kALbo + r * 16, ok ? src + (long long)pos * 64 + c8 * 8 : src, ok);
+        }
+        cp_arrive(&full[b]);
+      }
+      // drain tile j - 1
+      if (j >= 1) {
+        const long long jj = j - 1;
+        const int b = (int)(jj & 1);
+        if (!mbar_wait(&mmad[b], (uint32_t)((jj >> 1) & 1))) atomicExch(&fail, 1);
+        fence_after();
+        const long long tile = tile_id(jj);
+        const long long s = tile / tiles_per_sample;
+        const int i = (int)(tile % tiles_per_sample) * 128 + warp * 32 + lane;
+        float v[64];
+        tmem_ld64(tmem_base + (uint32_t)(b * 64) + ((uint32_t)(warp * 32) << 16), v);
+        fence_before();
+        mbar_arrive(&drain[b]);
+        uint32_t w[32];
+#pragma unroll
+        for (int k = 0; k < 32; k++)
+          w[k] = pack_bf16(fmaxf(v[2 * k] + bias_s[2 * k], 0.f), fmaxf(v[2 * k + 1] + bias_s[2 * k + 1], 0.f));
+        if (i < L) {
+          uint4* dst = reinterpret_cast<uint4*>(out + (s * (long long)L + i) * 64);
+#pragma unroll
+          for (int k = 0; k < 8; k++) dst[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+        }
+      }
+      if (*reinterpret_cast<volatile int*>(&fail)) break;
+    }
+  } else if (lane == 0) {
+    // ---- MMA warp (one lane)
+    const uint32_t idesc = idesc_bf16(128, 64);
+    const uint64_t adesc0 = sdesc(smem_u32(base + kWImg), kALbo, 128);
+    const uint64_t wdesc0 = sdesc(smem_u32(Ws), kWLbo, 128);
+    bool ok = mbar_wait(&wbar, 0);
+    for (long long j = 0; j < my_tiles && ok; j++) {
+      const int b = (int)(j & 1);
+      const uint32_t u = (uint32_t)((j >> 1) & 1);
+      ok = mbar_wait(&full[b], u);                                 // the input tile has landed
+      if (ok && j >= 2) ok = mbar_wait(&drain[b], u ^ 1u);          // accumulator b was read out
+      if (!ok) break;
+      asm volatile("fence.proxy.async.shared::cta;");
+      fence_after();
+      const uint64_t ab = adesc0 + (uint64_t)((b * kATile) >> 4);
+      const uint32_t d = tmem_base + (uint32_t)(b * 64);
+#pragma unroll
+      for (int t = 0; t < 9; t++)
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+          mma_bf16(d, ab + (uint64_t)((16 * t + 2 * c * kALbo) >> 4), wdesc0 + (uint64_t)((t * kWTap + 2 * c * kWLbo) >> 4),
+                   idesc, (t | c) ? 1u : 0u);
+      mma_commit(&mmad[b]);
+    }
+    if (!ok) atomicExch(&fail, 1);
+  }
+  cp_wait<0>();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (fail && tid == 0) atomicExch(err, 1);
+  if (warp == 0) tmem_dealloc(tmem_base, 128);
 }
 
 // ------------------------------------------------------------------------------------------------
-// Linear(K -> 256) + bias + ReLU, FP32 output: out[q][j] = relu(bias[j] + sum_k A[q][k] B[j][k])
+// Linear(K -> 256): partial sums part[split][q][j] = sum over the split's K range of A[q][k] B[j][k].
+// K in stages of 64 (4 MMAs of M 128, N 256, K 16), three shared-memory stages filled by cp.async two
+// stages ahead.  The splits of K spread the 64 L-long rows over the SMs; dense_reduce_kernel adds the
+// partial sums in split order (deterministic), the bias and the ReLU.
 // ------------------------------------------------------------------------------------------------
 constexpr int kDLboA = 128 * 16 + 16;  // 2,064 B
 constexpr int kDLboB = 256 * 16 + 16;  // 4,112 B
 constexpr int kDStageA = 8 * kDLboA;   // 16,512 B
 constexpr int kDStageB = 8 * kDLboB;   // 32,896 B
 constexpr int kDStage = kDStageA + kDStageB;
-constexpr int kDenseSmem = 2 * kDStage + 1024;
+constexpr int kDStages = 3;
+constexpr int kDenseSmem = kDStages * kDStage + 1024;
 
 __global__ void __launch_bounds__(128, 1) dense_tc_kernel(const __nv_bfloat16* __restrict__ A,
-                                                          const __nv_bfloat16* __restrict__ B,
-                                                          const float* __restrict__ bias, float* __restrict__ out,
-                                                          long long n, int K, int* err) {
+                                                          const __nv_bfloat16* __restrict__ B, float* __restrict__ part,
+                                                          long long n, int K, int kb_per_split, int* err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* base = dsm + ((1024 - (smem_u32(dsm) & 1023)) & 1023);
   __shared__ uint32_t tmem_base;
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[kDStages];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long m0 = (long long)blockIdx.x * 128;
-  if (warp == 0) tmem_alloc(&tmem_base, 256);
-  if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16(128, 256);
-  uint32_t phase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  bool failed = false;
   const int nk = K / 64;
-  for (int kb = 0; kb < nk && !failed; kb++) {
-    const int st = kb & 1;
-    unsigned char* As = base + st * kDStage;
+  const int kb0 = blockIdx.y * kb_per_split;
+  const int nkb = max(0, min(nk, kb0 + kb_per_split) - kb0);
+  auto load = [&](int i) {
+    unsigned char* As = base + (i % kDStages) * kDStage;
     unsigned char* Bs = As + kDStageA;
-    if (pending[st]) {  // the MMAs of stage kb - 2 still read this buffer
-      const bool ok = mbar_wait(&bar[st], phase[st]);
-      phase[st] ^= 1u;
-      pending[st] = false;
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-    }
-    const long long k0 = (long long)kb * 64;
+    const long long k0 = (long long)(kb0 + i) * 64;
     for (int e = tid; e < 128 * 8; e += 128) {
       const int r = e >> 3, c8 = e & 7;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (m0 + r < n) v = *reinterpret_cast<const uint4*>(A + (m0 + r) * (long long)K + k0 + c8 * 8);
-      *reinterpret_cast<uint4*>(As + c8 * kDLboA + r * 16) = v;
+      const bool ok = m0 + r < n;
+      cp16(As + c8 * kDLboA + r * 16, ok ? A + (m0 + r) * (long long)K + k0 + c8 * 8 : A, ok);
     }
     for (int e = tid; e < 256 * 8; e += 128) {
       const int r = e >> 3, c8 = e & 7;
-      *reinterpret_cast<uint4*>(Bs + c8 * kDLboB + r * 16) =
-          *reinterpret_cast<const uint4*>(B + (long long)r * K + k0 + c8 * 8);
+      cp16(Bs + c8 * kDLboB + r * 16, B + (long long)r * K + k0 + c8 * 8, true);
     }
+  };
+  if (nkb > 0) load(0);
+  cp_commit();
+  if (nkb > 1) load(1);
+  cp_commit();
+  if (warp == 0) tmem_alloc(&tmem_base, 256);
+  if (tid == 0)
+    for (int b = 0; b < kDStages; b++) mbar_init(&bar[b]);
+  const uint32_t idesc = idesc_bf16(128, 256);
+  uint32_t phase[kDStages] = {0u, 0u, 0u};
+  bool failed = false;
+  for (int i = 0; i < nkb; i++) {
+    const int st = i % kDStages;
+    cp_wait<1>();  // stage i has landed (only the most recent group may still be in flight)
     fence_smem_to_async();
     fence_before();
     __syncthreads();
     fence_after();
     if (tid == 0) {
-      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      const uint32_t a0 = smem_u32(base + st * kDStage), b0 = a0 + kDStageA;
 #pragma unroll
       for (int c = 0; c < 4; c++)
-        mma_bf16(tmem, sdesc(a0 + 2 * c * kDLboA, kDLboA, 128), sdesc(b0 + 2 * c * kDLboB, kDLboB, 128), idesc,
-                 (kb | c) ? 1u : 0u);
+        mma_bf16(tmem_base, sdesc(a0 + 2 * c * kDLboA, kDLboA, 128), sdesc(b0 + 2 * c * kDLboB, kDLboB, 128), idesc,
+                 (i | c) ? 1u : 0u);
       mma_commit(&bar[st]);
     }
-    pending[st] = true;
-  }
-  for (int st = 0; st < 2; st++)
-    if (pending[st]) {
-      const bool ok = mbar_wait(&bar[st], phase[st]);
-      phase[st] ^= 1u;
-      if (!ok) failed = true;
+    if (i >= 1) {  // the MMAs of stage i-1 are done: its buffer takes stage i+2
+      const int sp = (i - 1) % kDStages;
+      const bool ok = mbar_wait(&bar[sp], phase[sp]);
+      phase[sp] ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
     }
-  if (__syncthreads_or(failed)) {
+    if (i + 2 < nkb) load(i + 2);
+    cp_commit();
+  }
+  if (!failed && nkb > 0) {
+    const int sl = (nkb - 1) % kDStages;
+    const bool ok = mbar_wait(&bar[sl], phase[sl]);
+    if (__syncthreads_or(!ok)) failed = true;
+  }
+  cp_wait<0>();
+  if (failed) {
     if (tid == 0) atomicExch(err, 1);
   } else {
     fence_after();
     const long long q = m0 + warp * 32 + lane;
+    float* dst = part + ((long long)blockIdx.y * n + q) * 256;
 #pragma unroll 1
-    for (int c0 = 0; c0 < 256; c0 += 16) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (q < n) {
-        float4* dst = reinterpret_cast<float4*>(out + q * 256 + c0);
+    for (int c0 = 0; c0 < 256; c0 += 64) {
+      float v[64];
+      if (nkb > 0) {
+        tmem_ld64(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      } else {
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-          dst[j] = make_float4(fmaxf(v[4 * j] + bias[c0 + 4 * j], 0.f), fmaxf(v[4 * j + 1] + bias[c0 + 4 * j + 1], 0.f),
-                               fmaxf(v[4 * j + 2] + bias[c0 + 4 * j + 2], 0.f),
-                               fmaxf(v[4 * j + 3] + bias[c0 + 4 * j + 3], 0.f));
+        for (int j = 0; j < 64; j++) v[j] = 0.f;
+      }
+      if (q < n) {
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+          reinterpret_cast<float4*>(dst + c0)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
       }
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 256);
+  if (warp == 0) tmem_dealloc(tmem_base, 256);
+}
+
+// out[q][j] = relu(bias[j] + sum over splits of part[s][q][j]), splits added in order.
+__global__ void dense_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bias,
+                                    float* __restrict__ out, long long n, int splits) {
+  const long long total = n * 256;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    float v = part[e];
+    for (int s = 1; s < splits; s++) v += part[(long long)s * total + e];
+    out[e] = fmaxf(v + bias[e & 255], 0.f);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
 // CUDA-core pieces of the inference path: the first convolution (2 input channels) into BF16
 // channels-last, and the weight images.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) conv1_cl_kernel(const float* __restrict__ x, const __nv_bfloat16* __restrict__ w,
+// One block per (sample, 128 positions), 256 threads: thread (cp, g) keeps the 36 weights of output
+// channels 2cp, 2cp+1 in registers and slides over positions i0 + 16g .. i0 + 16g + 15 of the two input
+// channels staged in shared memory; a warp's 32 channel pairs write one 128-byte position row.
+__global__ void __launch_bounds__(256) conv1_cl_kernel(const float* __restrict__ x, const __nv_bfloat16* __restrict__ w,
                                                        const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
                                                        int L, long long n) {
-  __shared__ float ws[64 * 18];
-  __shared__ float bs[64];
-  for (int e = threadIdx.x; e < 64 * 18; e += blockDim.x) ws[e] = __bfloat162float(w[e]);
-  if (threadIdx.x < 64) bs[threadIdx.x] = bias[threadIdx.x];
-  __syncthreads();
-  const long long total = n * L;
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
-    const long long s = g / L;
-    const int i = (int)(g % L);
-    float xin[2][9];
+  __shared__ float xs[2][136];
+  const int cp = threadIdx.x & 31, g = threadIdx.x >> 5;
+  float wr[2][2][9];
+#pragma unroll
+  for (int o = 0; o < 2; o++)
 #pragma unroll
     for (int ci = 0; ci < 2; ci++)
 #pragma unroll
-      for (int t = 0; t < 9; t++) {
-        const int pos = i + t - 4;
-        xin[ci][t] = (pos >= 0 && pos < L) ? x[(s * 2 + ci) * L + pos] : 0.f;
-      }
-    uint32_t pk[32];
-#pragma unroll
-    for (int co = 0; co < 64; co += 2) {
-      float acc0 = bs[co], acc1 = bs[co + 1];
+      for (int t = 0; t < 9; t++) wr[o][ci][t] = __bfloat162float(w[((2 * cp + o) * 2 + ci) * 9 + t]);
+  const float b0 = bias[2 * cp], b1 = bias[2 * cp + 1];
+  const int tps = (L + 127) / 128;
+  for (long long tile = blockIdx.x; tile < n * tps; tile += gridDim.x) {
+    const long long s = tile / tps;
+    const int i0 = (int)(tile % tps) * 128;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * 136; e += blockDim.x) {
+      const int ci = e / 136, r = e % 136, pos = i0 - 4 + r;
+      xs[ci][r] = (pos >= 0 && pos < L) ? x[(s * 2 + ci) * L + pos] : 0.f;
+    }
+    __syncthreads();
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (s * L + i0 + 16 * g) * 64) + cp;
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+      float a0 = b0, a1 = b1;
 #pragma unroll
       for (int ci = 0; ci < 2; ci++)
 #pragma unroll
         for (int t = 0; t < 9; t++) {
-          acc0 = fmaf(ws[(co * 2 + ci) * 9 + t], xin[ci][t], acc0);
-          acc1 = fmaf(ws[((co + 1) * 2 + ci) * 9 + t], xin[ci][t], acc1);
+          const float xv = xs[ci][16 * g + k + t];
+          a0 = fmaf(wr[0][ci][t], xv, a0);
+          a1 = fmaf(wr[1][ci][t], xv, a1);
         }
-      pk[co >> 1] = pack_bf16(fmaxf(acc0, 0.f), fmaxf(acc1, 0.f));
+      if (i0 + 16 * g + k < L) dst[k * 32] = pack_bf16(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
     }
-    uint4* dst = reinterpret_cast<uint4*>(out + g * 64);
-#pragma unroll
-    for (int j = 0; j < 8; j++) dst[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
   }
 }
 
@@ -370,9 +474,9 @@ int tc_prepare_weights(const float* w2, const float* w3, const float* W4, int L,
 
 int tc_conv1(const float* x, const __nv_bfloat16* w1, const float* b1, __nv_bfloat16* h1, int L, long long n,
              int num_sms, cudaStream_t st) {
-  const long long total = n * L;
-  const long long blocks = std::min<long long>((total + 127) / 128, (long long)num_sms * 16);
-  conv1_cl_kernel<<<(unsigned)blocks, 128, 0, st>>>(x, w1, b1, h1, L, n);
+  const long long tiles = n * ((L + 127) / 128);
+  const long long blocks = std::min<long long>(tiles, (long long)num_sms * 8);
+  if (blocks > 0) conv1_cl_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, w1, b1, h1, L, n);
   return cuda_status(cudaGetLastError());
 }
 
@@ -389,12 +493,16 @@ int tc_conv64(const __nv_bfloat16* in, const __nv_bfloat16* img, const float* bi
   const int tps = (L + 127) / 128;
   const long long tiles = n * tps;
   const long long blocks = std::min<long long>(tiles, 2ll * num_sms);
-  conv64_tc_kernel<<<(unsigned)blocks, 128, kConvSmem, st>>>(in, img, bias, out, L, n, tps, err);
+  if (blocks > 0) conv64_tc_kernel<<<(unsigned)blocks, kConvThreads, kConvSmem, st>>>(in, img, bias, out, L, n, tps, err);
   return cuda_status(cudaGetLastError());
 }
 
-int tc_dense(const __nv_bfloat16* A, const __nv_bfloat16* Bp, const float* bias, float* out, long long n, int K,
-             int* err, cudaStream_t st) {
+// Splits of K: a function of K alone (about 64 stages each, at most 8), so a sample's logits do not
+// depend on the batch it is evaluated in.
+int tc_dense_splits(int K) { return std::max(1, std::min(8, (K / 64) / 64)); }
+
+int tc_dense(const __nv_bfloat16* A, const __nv_bfloat16* Bp, const float* bias, float* part, float* out, long long n,
+             int K, int num_sms, int* err, cudaStream_t st) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -403,8 +511,12 @@ int tc_dense(const __nv_bfloat16* A, const __nv_bfloat16* Bp, const float* bias,
       return LABS_ERR_CUDA;
     configured[dev] = true;
   }
-  if (K % 64) return LABS_ERR_INVALID_ARG;
-  dense_tc_kernel<<<(unsigned)((n + 127) / 128), 128, kDenseSmem, st>>>(A, Bp, bias, out, n, K, err);
+  if (K % 64 || n <= 0) return n == 0 ? LABS_OK : LABS_ERR_INVALID_ARG;
+  const int splits = tc_dense_splits(K);
+  const int nk = K / 64, per = (nk + splits - 1) / splits;
+  dense_tc_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)splits), 128, kDenseSmem, st>>>(A, Bp, part, n, K, per, err);
+  dense_reduce_kernel<<<(unsigned)std::min<long long>((n * 256 + 255) / 256, (long long)num_sms * 16), 256, 0, st>>>(
+      part, bias, out, n, splits);
   return cuda_status(cudaGetLastError());
 }
 

@@ -20,8 +20,10 @@ int tc_conv1(const float* x, const __nv_bfloat16* w1, const float* b1, __nv_bflo
 int tc_conv64(const __nv_bfloat16* in, const __nv_bfloat16* img, const float* bias, __nv_bfloat16* out, int L,
               long long n, int num_sms, int* err, cudaStream_t st);
 // out[n][256] = relu(bias + A[n][K] . Bp[256][K]^T) in FP32; K a multiple of 64; *err = 1 if a wait expired.
-int tc_dense(const __nv_bfloat16* A, const __nv_bfloat16* Bp, const float* bias, float* out, long long n, int K,
-             int* err, cudaStream_t st);
+// part: FP32 scratch of tc_dense_splits(K) * n * 256 floats (partial sums of the K splits).
+int tc_dense(const __nv_bfloat16* A, const __nv_bfloat16* Bp, const float* bias, float* part, float* out, long long n,
+             int K, int num_sms, int* err, cudaStream_t st);
+int tc_dense_splits(int K);
 
 int tc_conv_smem_bytes();
 int tc_dense_smem_bytes();
