@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
-                         "pq: step-2 refinement from step-1 candidates")
+                         "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
+                         "network: the proposal network's inference alone")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -307,6 +308,72 @@ def run_pq(args, ws, rank, local):
     return 0
 
 
+def peaks():
+    """Measured peaks of this GPU pool (HBM copy GB/s, dense BF16 TFLOP/s burst and sustained) if the file
+    is present, else {} (the caller then uses the fallback figure and says so)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def network_roofline(lg, L, n, local):
+    """The network's inference (labs_policy_forward) on n walks' sequences: its FLOPs per call over the
+    CUDA-event time of 10 calls on the launching stream, against the measured dense BF16 peak (burst:
+    the forward is timed on its own)."""
+    import ctypes
+
+    import torch
+
+    pol = lg.Policy(L, seed=1, device=local)
+    w = torch.from_numpy(inp.random_words(n, L, seed=3).view(np.int64)).to(torch.device("cuda", local))
+    out = torch.empty((n, L), dtype=torch.float32, device=w.device)
+    lib = lg.load()
+    st = torch.cuda.current_stream(w.device)
+    args = (pol.h, ctypes.c_void_p(w.data_ptr()), n, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream))
+    for _ in range(3):
+        lib.labs_policy_forward(*args)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(10):
+        lib.labs_policy_forward(*args)
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    status = lib.labs_policy_sync_status(pol.h, ctypes.c_void_p(st.cuda_stream))
+    flop = n * (2 * 64 * 2 * 9 * L + 2 * 2 * 64 * 64 * 9 * L + 2 * 256 * 64 * L + 2 * 256 * L)
+    pk = peaks()
+    peak = pk.get("bf16_tflops", 1900.0)
+    src = "bf16_tflops burst, of measured" if "bf16_tflops" in pk else "1.9 PFLOP/s, of fallback"
+    ach = flop / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "kernel": "labs_policy_forward (features, conv1, 2 x tcgen05 conv, tcgen05 dense, 256->L)",
+            "work": "2*64*(2+2*64)*9*L + 2*256*65*L FLOP per sequence", "n": n, "ms_per_forward": ms,
+            "status": status, "peak_source": src}
+
+
+def run_network(args, ws, rank, local):
+    """The proposal network's inference at L=451 on 8,192 sequences (one chunk's worth of walks), as
+    sequences scored per second, with the tensor-core roofline of the forward."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    lg.load()
+    roof = network_roofline(lg, W1["L"], 8192, local)
+    ms = roof["ms_per_forward"]
+    line = {"metric": "sequences/s", "value": 8192 / (ms * 1e-3), "unit": "sequences/s", "n_gpus": 1, "steps": 10,
+            "warmup": 3, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "proposal_network_forward_L451_8192seq", "L": W1["L"], "n": 8192},
+            "roofline": roof}
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args, ws, rank, local):
     """Learned proposal at L=451: tuples from plain walks, training, lambda pre-registered on pilot seeds,
     equal-budget gain over 30 fresh seeds (rank-sum) and time to a pre-registered E*, plain vs learned."""
@@ -321,11 +388,12 @@ def run_learned(args, ws, rank, local):
     t0 = time.perf_counter()
     res = learn.experiment(L=W1["L"], p=W1["p"], prefixes=pre, device=local, log=lambda m: print(m, file=sys.stderr))
     tt = res["time_to_target"]
+    roof = network_roofline(lg, W1["L"], 8192, local)
     line = {"metric": "time-to-E* speedup (learned vs plain)", "value": tt["speedup_learned_vs_plain"],
             "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": (time.perf_counter() - t0) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32+bf16/fp32",
             "data": "synthetic", "config": {"workload": "learned_proposal_L451", "L": W1["L"], "p": W1["p"]},
-            "learned": res}
+            "roofline": roof, "learned": res}
     print(json.dumps(line))
     return 0
 
@@ -339,6 +407,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "network":
+        return run_network(args, ws, rank, local)
     if args.workload == "learned":
         return run_learned(args, ws, rank, local)
 

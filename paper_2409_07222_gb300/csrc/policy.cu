@@ -41,7 +41,7 @@ struct labs_policy {
   long long step;
   // training activations for up to cap_n samples
   long long cap_n;
-  float *x, *h1, *h2, *h3, *a, *logits, *d_logits, *da, *dh_a, *dh_b, *wsum, *loss;
+  float *x, *h1, *h2, *h3, *a, *logits, *d_logits, *da, *dh_a, *dh_b, *wsum, *loss, *lossv, *wpart;
   // tensor-core inference: weight images (rebuilt when tc_stale) and activations for up to cap_i samples
   __nv_bfloat16 *img2, *img3, *W4p;
   bool tc_stale;
@@ -153,12 +153,12 @@ __global__ void __launch_bounds__(256) conv_kernel(const float* __restrict__ in,
   }
 }
 
-// Weight gradient of a convolution: dw[co][ci][t] += sum_{n,i} dout[n][co][i] in[n][ci][i+t-4] and
-// db[co] += sum_{n,i} dout[n][co][i], for a chunk of samples per block (atomics into the FP32 grads).
+// Weight gradient of a convolution for a chunk of samples per block: part[block][(co * CIN + ci) * 9 + t] =
+// sum_{n in chunk, i} dout[n][co][i] in[n][ci][i+t-4] and part[block][64 * CIN * 9 + co] = sum dout[n][co][i];
+// wgrad_reduce_kernel adds the blocks in order (deterministic).
 template <int CIN>
 __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict__ in, const float* __restrict__ dout,
-                                                         float* __restrict__ dw, float* __restrict__ db, int L,
-                                                         long long n, int per_block) {
+                                                         float* __restrict__ part, int L, long long n, int per_block) {
   constexpr int CH = CIN < kCT ? CIN : kCT;
   __shared__ float do_s[kC][129];
   __shared__ float in_s[CH][128 + 8];
@@ -205,14 +205,29 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict
       __syncthreads();
     }
   }
+  float* pb = part + (long long)blockIdx.x * (kC * CIN * kKW + kC);
   if (cig < CH) {
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       const int co = 4 * cg + a;
 #pragma unroll
-      for (int t = 0; t < kKW; t++) atomicAdd(&dw[((long long)co * CIN + c0 + cig) * kKW + t], acc[a][t]);
-      if (cig == 0 && blockIdx.y == 0) atomicAdd(&db[co], dbs[a]);
+      for (int t = 0; t < kKW; t++) pb[(co * CIN + c0 + cig) * kKW + t] = acc[a][t];
+      if (cig == 0 && blockIdx.y == 0) pb[kC * CIN * kKW + co] = dbs[a];
     }
+  }
+}
+
+// dw[e] += sum over blocks of part[b][e] (e < 64 CIN 9), db likewise, blocks in order.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int blocks, int nw, float* __restrict__ dw,
+                                    float* __restrict__ db) {
+  const int stride = nw + kC;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < stride; e += gridDim.x * blockDim.x) {
+    float v = 0.f;
+    for (int b = 0; b < blocks; b++) v += part[(long long)b * stride + e];
+    if (e < nw)
+      dw[e] += v;
+    else
+      db[e - nw] += v;
   }
 }
 
@@ -351,7 +366,7 @@ __global__ void __launch_bounds__(128) loss_kernel(const float* __restrict__ log
       if (i == t) d -= 1.f;
       dlogits[q * L + i] = d * w;
     }
-    if (lane == 0) atomicAdd(loss, w * (mx + logf(z) - lg[t]));
+    if (lane == 0) loss[q] = w * (mx + logf(z) - lg[t]);  // summed in order by wsum_kernel
   }
 }
 
@@ -388,17 +403,20 @@ __global__ void init_params_kernel(float* __restrict__ p, long long lo, long lon
   }
 }
 
+constexpr int kWgradSamples = 4;  // samples per block of the weight-gradient kernels
+
 int ensure_acts(labs_policy* P, long long n) {
   if (n <= P->cap_n) return LABS_OK;
-  float* bufs[] = {P->x, P->h1, P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b};
+  float* bufs[] = {P->x, P->h1, P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b, P->lossv, P->wpart};
   for (float* b : bufs)
     if (b) cudaFree(b);
   const long long L = P->L;
   const size_t sz[] = {(size_t)n * 2 * L, (size_t)n * kC * L, (size_t)n * kC * L, (size_t)n * kC * L,
                        (size_t)n * kHid, (size_t)n * L, (size_t)n * L, (size_t)n * kHid, (size_t)n * kC * L,
-                       (size_t)n * kC * L};
-  float** dst[] = {&P->x, &P->h1, &P->h2, &P->h3, &P->a, &P->logits, &P->d_logits, &P->da, &P->dh_a, &P->dh_b};
-  for (int i = 0; i < 10; i++) {
+                       (size_t)n * kC * L, (size_t)n, (size_t)((n + kWgradSamples - 1) / kWgradSamples) * (kC * kC * kKW + kC)};
+  float** dst[] = {&P->x, &P->h1, &P->h2, &P->h3, &P->a, &P->logits, &P->d_logits, &P->da, &P->dh_a, &P->dh_b,
+                   &P->lossv, &P->wpart};
+  for (int i = 0; i < 12; i++) {
     *dst[i] = nullptr;
     if (cudaMalloc(dst[i], sizeof(float) * sz[i]) != cudaSuccess) {
       P->cap_n = 0;
@@ -539,7 +557,7 @@ void labs_policy_destroy(labs_policy* P) {
   cudaSetDevice(P->ctx->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {P->master, P->wbf, P->grad, P->m1, P->m2, P->wT2, P->wT3, P->wsum, P->loss, P->x, P->h1,
-                  P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b, P->img2, P->img3,
+                  P->h2, P->h3, P->a, P->logits, P->d_logits, P->da, P->dh_a, P->dh_b, P->lossv, P->wpart, P->img2, P->img3,
                   P->W4p, P->tc_err, P->xi, P->ai, P->part, P->h1b, P->h2b, P->h3b};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -590,11 +608,11 @@ int labs_policy_train_step(labs_policy* P, const uint64_t* seqs, const int32_t* 
   features_kernel<<<(unsigned)std::min<long long>((n + 3) / 4, 4096), 128, 0, st>>>(seqs, L, n, P->x);
   forward(P, n, P->logits, st);
   cudaMemsetAsync(P->grad, 0, 4 * (size_t)P->n_params, st);
-  cudaMemsetAsync(P->loss, 0, 4, st);
   wsum_kernel<<<1, 1024, 0, st>>>(weight, n, P->wsum);
   loss_kernel<<<(unsigned)std::min<long long>((n + 3) / 4, 4096), 128, 0, st>>>(P->logits, L, n, free_lo, free_hi,
                                                                                   target, weight, P->wsum,
-                                                                                  P->d_logits, P->loss);
+                                                                                  P->d_logits, P->lossv);
+  wsum_kernel<<<1, 1024, 0, st>>>(P->lossv, n, P->loss);
   float* g = P->grad;
   const __nv_bfloat16* w = P->wbf;
   // fc2: dW5[i][j] = sum_n dl[n][i] a[n][j]; db5; da[n][j] = sum_i dl[n][i] W5[i][j], masked by a > 0
@@ -610,20 +628,22 @@ int labs_policy_train_step(labs_policy* P, const uint64_t* seqs, const int32_t* 
   gemm(st, (int)n, (int)K4, (long long)kHid, P->da, (long long)kHid, 1ll, w + P->off[6], K4, 1ll, P->dh_a, K4,
        (const float*)nullptr, 0, P->h3, 0);
   // conv3: weight gradient from (h2, dc3); data gradient into h2's grid, masked by h2 > 0
-  const int per_block = 4;
+  const int per_block = kWgradSamples;
   const unsigned nbk = (unsigned)((n + per_block - 1) / per_block);
-  conv_wgrad_kernel<64><<<dim3(nbk, kC / kCT), 256, 0, st>>>(P->h2, P->dh_a, g + P->off[4], g + P->off[5], L, n,
-                                                              per_block);
+  const int nw64 = kC * kC * kKW, nw2 = kC * 2 * kKW;
+  conv_wgrad_kernel<64><<<dim3(nbk, kC / kCT), 256, 0, st>>>(P->h2, P->dh_a, P->wpart, L, n, per_block);
+  wgrad_reduce_kernel<<<(nw64 + kC + 255) / 256, 256, 0, st>>>(P->wpart, (int)nbk, nw64, g + P->off[4], g + P->off[5]);
   flip_transpose_kernel<<<(kC * kC * kKW + 255) / 256, 256, 0, st>>>(P->master + P->off[4], P->wT3, kC, kC);
   const dim3 gc((L + 127) / 128, (unsigned)n);
   conv_kernel<64><<<gc, 256, 0, st>>>(P->dh_a, P->wT3, nullptr, P->h2, P->dh_b, L, 0);
   // conv2
-  conv_wgrad_kernel<64><<<dim3(nbk, kC / kCT), 256, 0, st>>>(P->h1, P->dh_b, g + P->off[2], g + P->off[3], L, n,
-                                                              per_block);
+  conv_wgrad_kernel<64><<<dim3(nbk, kC / kCT), 256, 0, st>>>(P->h1, P->dh_b, P->wpart, L, n, per_block);
+  wgrad_reduce_kernel<<<(nw64 + kC + 255) / 256, 256, 0, st>>>(P->wpart, (int)nbk, nw64, g + P->off[2], g + P->off[3]);
   flip_transpose_kernel<<<(kC * kC * kKW + 255) / 256, 256, 0, st>>>(P->master + P->off[2], P->wT2, kC, kC);
   conv_kernel<64><<<gc, 256, 0, st>>>(P->dh_b, P->wT2, nullptr, P->h1, P->dh_a, L, 0);
   // conv1 (input features need no gradient)
-  conv_wgrad_kernel<2><<<dim3(nbk, 1), 256, 0, st>>>(P->x, P->dh_a, g + P->off[0], g + P->off[1], L, n, per_block);
+  conv_wgrad_kernel<2><<<dim3(nbk, 1), 256, 0, st>>>(P->x, P->dh_a, P->wpart, L, n, per_block);
+  wgrad_reduce_kernel<<<(nw2 + kC + 255) / 256, 256, 0, st>>>(P->wpart, (int)nbk, nw2, g + P->off[0], g + P->off[1]);
   if (grads_out && cudaMemcpyAsync(grads_out, g, 4 * (size_t)P->n_params, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return LABS_ERR_CUDA;
   if (loss_out && cudaMemcpyAsync(loss_out, P->loss, 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)

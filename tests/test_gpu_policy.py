@@ -184,3 +184,20 @@ def test_learned_walks_replay_in_oracle(lg, L, p, lam):
     # the bias changed the walk: the plain walk differs
     pc, _ = oracle.walk_search(L, L % 2 == 1, p, pre, n, budget, T_i, 77, R=6, n_threads=8)
     assert not np.array_equal(pc["fp"], oc["fp"])
+
+
+def test_training_is_deterministic(lg):
+    """Training sums in a fixed order (no floating-point atomics): two networks trained on the same
+    batches from the same initial weights agree bit for bit, losses included."""
+    L, n = 41, 40
+    w, _ = _batch(L, n, 17)
+    target = np.random.default_rng(2).integers(5, 20, size=n).astype(np.int32)
+    weight = np.random.default_rng(3).uniform(0.1, 1.0, size=n).astype(np.float32)
+    seqs = torch.from_numpy(w.view(np.int64)).cuda()
+    runs = []
+    for _ in range(2):
+        pol = lg.Policy(L, seed=4)
+        losses = [pol.train_step(seqs, target, weight, 5, 20, lr=2e-3)[0] for _ in range(3)]
+        runs.append((torch.cat(losses).cpu(), pol.get_params().cpu()))
+    assert torch.equal(runs[0][0], runs[1][0])
+    assert torch.equal(runs[0][1], runs[1][1])
