@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
+    ap.add_argument("--pq-tr", type=int, default=0, help="pq workload: MAKE_ROTATIONS per side (0: off)")
     return ap.parse_args()
 
 
@@ -284,7 +285,7 @@ def run_pq(args, ws, rank, local):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best, bE, st = lg.labs_pq_refine(L, seeds, B=S2["B"], cap=S2["cap"], H_log2=args.pq_hlog2,
-                                         max_expansions=args.pq_expansions, T_u=S2["T_u"])
+                                         max_expansions=args.pq_expansions, T_u=S2["T_u"], T_r=args.pq_tr)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times[-args.steps:])
@@ -295,7 +296,8 @@ def run_pq(args, ws, rank, local):
     line = {"metric": "expansions/s", "value": exps / t, "unit": "expansions/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(1, args.warmup), "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "step2_pq_L%d_4096seeds_cap2^22_B4096" % L, "L": L, "seeds": int(len(pick)),
+            "config": {"workload": "step2_pq_L%d_4096seeds_cap2^22_B4096" % L + ("_Tr%d" % args.pq_tr if args.pq_tr else ""),
+                       "L": L, "seeds": int(len(pick)), "T_r": args.pq_tr,
                        "max_expansions": args.pq_expansions, "H_slots_log2": args.pq_hlog2,
                        "seed_best_E": seed_best, "best_E": int(bE.cpu()[0]), "stats": {k: int(s2[k]) for k in
                        ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements",

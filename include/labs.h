@@ -224,7 +224,11 @@ int labs_sample_threshold_noalloc(int L, int skew, int p, const uint64_t* prefix
  *  - the open set becomes the cap smallest keys of (rest of open set) u survivors; H receives exactly the
  *    admitted survivors;
  *  - the best improves on a strict E' < E_best (to the smallest survivor key); u counts pops since the
- *    last improvement; rotations (MAKE_ROTATIONS, T_r) are not applied.
+ *    last improvement;
+ *  - MAKE_ROTATIONS: with T_r > 0 each popped pivot also offers its rotations by 1..T_r elements to the
+ *    left (first elements moved to the end) and to the right (last elements moved to the start), energy
+ *    and fingerprint computed from scratch, ordered after the pivot's L flips; they are survivors like
+ *    the flips (visited-set test, admission, best).
  * With B = 1 and a cap never reached this is Algorithm 2 step by step.
  */
 typedef struct {
@@ -232,7 +236,7 @@ typedef struct {
   int32_t B;              /* pops per round, 1..8192 */
   int64_t cap;            /* open-set capacity, 1..2^24 */
   int32_t H_log2;         /* visited set: 2^H_log2 slots of 8 bytes, 10..31; it must stay <= 3/4 full */
-  int32_t T_r;            /* rotations: must be 0 */
+  int32_t T_r;            /* rotations per side: 0..64, 2 T_r < L */
   int64_t max_expansions; /* pops in total */
   int64_t T_u;            /* stop after T_u pops without improvement; <= 0: no limit */
 } labs_pq_cfg;
@@ -257,7 +261,7 @@ typedef struct {
  *   seeds [n_seeds][W] uint64 DEVICE; best_seq [W] uint64 DEVICE; best_E int32 DEVICE; stats DEVICE.
  *   Workspace: two open-set buffers (cap * (12 + 8W) bytes each), the visited set (8 * 2^H_log2 bytes),
  *   survivor and sort buffers (about 60 * B * L bytes).
- * Errors: LABS_ERR_INVALID_ARG on a bad configuration (T_r != 0 included), LABS_ERR_NOMEM if the
+ * Errors: LABS_ERR_INVALID_ARG on a bad configuration, LABS_ERR_NOMEM if the
  * workspace cannot be allocated.
  */
 int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,

@@ -57,7 +57,7 @@ def lib():
                                                ctypes.c_float, P, P, ci]),
             "oracle_threshold": (ci, [ci, ci, ci, P, ci, ci, u64, i64, i64, P, P]),
             "oracle_skew_exhaustive": (ci, [ci, ci, P, P, P, P, P]),
-            "oracle_pq_refine": (ci, [ci, P, ci, i64, ci, i64, i64, P, P, P, P]),
+            "oracle_pq_refine": (ci, [ci, P, ci, i64, ci, i64, i64, ci, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -248,14 +248,15 @@ def skew_exhaustive(L, p=0, prefix=0):
     return int(minE[0]), int(cnt[0]), int(arg[0]), words
 
 
-def pq_refine(L, seeds, cap, B, max_expansions, T_u=0):
-    """Returns (best_words [W], best_E, best_fp, stats dict)."""
+def pq_refine(L, seeds, cap, B, max_expansions, T_u=0, T_r=0):
+    """Returns (best_words [W], best_E, best_fp, stats dict).  T_r > 0: every popped pivot also offers its
+    2 T_r rotations (1..T_r elements to the left, then to the right) as candidates."""
     w = _words(seeds, L)
     best = np.zeros(words_per_seq(L), dtype=np.uint64)
     bE = np.zeros(1, dtype=np.int32)
     bfp = np.zeros(1, dtype=np.uint64)
     st = np.zeros(8, dtype=np.int64)
-    _check(lib().oracle_pq_refine(L, _p(w), w.shape[0], cap, B, max_expansions, T_u, _p(best), _p(bE), _p(bfp),
+    _check(lib().oracle_pq_refine(L, _p(w), w.shape[0], cap, B, max_expansions, T_u, T_r, _p(best), _p(bE), _p(bfp),
                                   _p(st)), "pq_refine")
     names = ["expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements", "stop_reason"]
     return best, int(bE[0]), int(bfp[0]), dict(zip(names, (int(x) for x in st)))

@@ -745,10 +745,30 @@ static int fpset_insert(fpset_t* h, uint64_t fp) {
   }
 }
 
+/* MAKE_ROTATIONS (Section 3, Algorithm 2): rotation code c = 0 .. 2 T_r - 1 of a sequence; c < T_r moves
+   the first c + 1 elements to the end (left rotation), c >= T_r moves the last c - T_r + 1 elements to the
+   start (right rotation).  out[i] = s[(i + r) mod L] for the left shift r. */
+static void rotate_seq(const int8_t* s, int L, int T_r, int c, int8_t* out) {
+  int r = c < T_r ? c + 1 : L - ((c - T_r + 1) % L);
+  r %= L;
+  for (int i = 0; i < L; i++) out[i] = s[(i + r) % L];
+}
+
+/* child of pivot s: position pos (1..L) flipped, or rotation pos - L - 1 */
+static void child_seq(const int8_t* s, int L, int T_r, int pos, int8_t* out) {
+  if (pos <= L) {
+    memcpy(out, s, (size_t)L);
+    out[pos - 1] = (int8_t)-out[pos - 1];
+  } else {
+    rotate_seq(s, L, T_r, pos - L - 1, out);
+  }
+}
+
 int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int B, int64_t max_expansions,
-                     int64_t T_u, uint64_t* best_words, int32_t* best_E_out, uint64_t* best_fp_out,
+                     int64_t T_u, int T_r, uint64_t* best_words, int32_t* best_E_out, uint64_t* best_fp_out,
                      int64_t* stats) {
-  if (L < 2 || L > ORACLE_MAX_L || n_seeds < 1 || cap < 1 || B < 1 || max_expansions < 0) return ORC_ERR_ARG;
+  if (L < 2 || L > ORACLE_MAX_L || n_seeds < 1 || cap < 1 || B < 1 || max_expansions < 0 || T_r < 0 || 2 * T_r >= L)
+    return ORC_ERR_ARG;
   int W = (L + 63) / 64;
   uint64_t Z[ORACLE_MAX_L + 1];
   zobrist_table(L, Z);
@@ -793,7 +813,7 @@ int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int
     if (b > nP) b = nP;
     if (b > max_expansions - expansions) b = max_expansions - expansions;
     /* expand the b popped nodes */
-    int64_t nS = 0, capS = b * L;
+    int64_t nS = 0, capS = b * (L + 2 * T_r);
     pq_entry* S = (pq_entry*)malloc(sizeof(pq_entry) * (size_t)(capS > 0 ? capS : 1));
     if (!S) { status = ORC_ERR_NOMEM; break; }
     for (int64_t q = 0; q < b; q++) {
@@ -809,6 +829,19 @@ int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int
         S[nS].s = NULL;
         nS++;
       }
+      /* MAKE_ROTATIONS of the pivot: energy and fingerprint from scratch, skipped when visited */
+      for (int c = 0; c < 2 * T_r; c++) {
+        int8_t rs[ORACLE_MAX_L];
+        rotate_seq(P[q].s, L, T_r, c, rs);
+        uint64_t rfp = fingerprint(rs, L, Z);
+        if (fpset_contains(&H, rfp)) continue;
+        S[nS].E = (int32_t)energy(rs, L);
+        S[nS].fp = rfp;
+        S[nS].parent = q;
+        S[nS].pos = L + 1 + c;
+        S[nS].s = NULL;
+        nS++;
+      }
     }
     qsort(S, (size_t)nS, sizeof(pq_entry), cmp_pq);
     int64_t nU = 0;
@@ -821,8 +854,7 @@ int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int
     if (nU > 0 && S[0].E < best_E) {
       best_E = S[0].E;
       best_fp = S[0].fp;
-      memcpy(best_s, P[S[0].parent].s, (size_t)L);
-      best_s[S[0].pos - 1] = (int8_t)-best_s[S[0].pos - 1];
+      child_seq(P[S[0].parent].s, L, T_r, S[0].pos, best_s);
       stats[6]++;
       u = 0;
     } else {
@@ -845,8 +877,7 @@ int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int
       } else {
         pq_entry e = S[ib++];
         int8_t* ns = (int8_t*)malloc((size_t)L);
-        memcpy(ns, P[e.parent].s, (size_t)L);
-        ns[e.pos - 1] = (int8_t)-ns[e.pos - 1];
+        child_seq(P[e.parent].s, L, T_r, e.pos, ns);
         e.s = ns;
         e.parent = -1;
         e.pos = 0;

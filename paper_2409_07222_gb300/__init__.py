@@ -198,7 +198,7 @@ def labs_batched_search(cfg, lengths, walks, prefixes, device=None, out=None, wa
     return out
 
 
-def labs_pq_refine(L, seeds, B=4096, cap=1 << 22, H_log2=24, max_expansions=10**7, T_u=0, device=None):
+def labs_pq_refine(L, seeds, B=4096, cap=1 << 22, H_log2=24, max_expansions=10**7, T_u=0, T_r=0, device=None):
     """Algorithm 2 on the device from packed seed sequences (device int64 [n, W]).
 
     Returns (best words int64 [W], best E int32 [1], stats uint8 [72]); ``pq_stats_numpy`` decodes stats.
@@ -206,7 +206,7 @@ def labs_pq_refine(L, seeds, B=4096, cap=1 << 22, H_log2=24, max_expansions=10**
     s = _dev_words(seeds, L)
     dev = s.device
     cfg = _lib.PqCfg()
-    cfg.L, cfg.B, cfg.cap, cfg.H_log2, cfg.T_r = L, B, cap, H_log2, 0
+    cfg.L, cfg.B, cfg.cap, cfg.H_log2, cfg.T_r = L, B, cap, H_log2, T_r
     cfg.max_expansions, cfg.T_u = max_expansions, T_u
     best = torch.empty(words_per_seq(L), dtype=torch.int64, device=dev)
     bE = torch.empty(1, dtype=torch.int32, device=dev)

@@ -213,7 +213,7 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
 int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                    int32_t* best_E, labs_pq_stats* stats, void* stream) {
   if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->B < 1 || cfg->B > 8192 || cfg->cap < 1 ||
-      cfg->cap > (1ll << 24) || cfg->H_log2 < 10 || cfg->H_log2 > 31 || cfg->T_r != 0 || cfg->max_expansions < 0 ||
+      cfg->cap > (1ll << 24) || cfg->H_log2 < 10 || cfg->H_log2 > 31 || cfg->T_r < 0 || cfg->T_r > 64 || 2 * cfg->T_r >= cfg->L || cfg->max_expansions < 0 ||
       n_seeds < 1)
     return LABS_ERR_INVALID_ARG;
   if (!seeds || !aligned8(seeds) || !best_seq || !aligned8(best_seq) || !best_E || !aligned4(best_E) || !stats ||

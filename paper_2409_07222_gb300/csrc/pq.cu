@@ -12,6 +12,8 @@
 //   merge    -- merge path of (open set minus the pops) with the survivors into the other buffer, cut at
 //               cap; admitted survivors enter the visited set (open addressing, atomicCAS);
 // keeps every result identical to the sequential definition whatever order threads run in.
+// With T_r > 0 every popped pivot also offers its 2 T_r rotations (MAKE_ROTATIONS) as survivor columns
+// L .. L + 2 T_r - 1, after its L flips.
 #include <algorithm>
 #include <new>
 
@@ -36,6 +38,7 @@ struct PqState {
 
 struct PqBufs {
   int L, W, B, H_log2;
+  int Tr, width;  // rotations per side (MAKE_ROTATIONS) and survivor columns per pop: L flips + 2 Tr rotations
   long long cap, max_exp, T_u;
   int32_t* PE[2];
   uint64_t* Pfp[2];
@@ -56,6 +59,31 @@ struct PqBufs {
   uint64_t* best_seq;
   const uint64_t* seeds;
 };
+
+// Left shift of rotation code c (MAKE_ROTATIONS): c < Tr moves the first c + 1 elements to the end,
+// c >= Tr moves the last c - Tr + 1 elements to the start (a left shift by L - (c - Tr + 1)).
+__host__ __device__ __forceinline__ int rot_shift(int L, int Tr, int c) {
+  const int r = c < Tr ? c + 1 : L - ((c - Tr + 1) % L);
+  return r % L;
+}
+
+// Survivor column col of a pivot (src, W words): col < L flips position col + 1, else rotation col - L.
+// One thread; dst may be global memory.
+__device__ __forceinline__ void pq_child(const uint64_t* src, const PqBufs& b, int col, uint64_t* dst) {
+  uint64_t out[LABS_MAX_W];
+  if (col < b.L) {
+    for (int t = 0; t < b.W; t++) out[t] = src[t] ^ (t == (col >> 6) ? 1ull << (col & 63) : 0ull);
+  } else {
+    const int r = rot_shift(b.L, b.Tr, col - b.L);
+    for (int t = 0; t < b.W; t++) out[t] = 0;
+    for (int i = 0; i < b.L; i++) {
+      int j = i + r;
+      if (j >= b.L) j -= b.L;
+      if ((src[j >> 6] >> (j & 63)) & 1ull) out[i >> 6] |= 1ull << (i & 63);
+    }
+  }
+  for (int t = 0; t < b.W; t++) dst[t] = out[t];
+}
 
 __device__ __forceinline__ uint64_t h_slot(uint64_t fp, int log2) { return (fp * kGamma) >> (64 - log2); }
 
@@ -198,13 +226,15 @@ __global__ void pq_round_begin_kernel(PqBufs b) {
   long long bb = min((long long)b.B, st->nP);
   bb = min(bb, b.max_exp - st->expansions);
   st->b = (int)bb;
-  st->n_dense = bb * b.L;
+  st->n_dense = bb * b.width;
 }
 
 // One warp per popped node: Delta E of all L single flips, visited-set test, dense survivor output.
 __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layout ly) {
   __shared__ ScanSmem slabs[kPqWarps];
+  __shared__ uint32_t rbits_all[kPqWarps][kBitWords];
   ScanSmem& sm = slabs[threadIdx.x >> 5];
+  uint32_t* rbits = rbits_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const PqState* st = b.st;
   const int nb = st->b;
@@ -237,11 +267,43 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
           const int P = p_from_scratch(sm, ly, cls, q0 + j, si);
           const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
           const uint64_t nfp = fp ^ b.ztab[si.m - 1];
-          const size_t di = (size_t)q * b.L + (si.m - 1);
+          const size_t di = (size_t)q * b.width + (si.m - 1);
           b.dE[di] = h_contains(b, nfp) ? INT32_MAX : E + d;
           b.dfp[di] = nfp;
         }
       }
+    }
+    // MAKE_ROTATIONS of the pivot: each rotation's energy and fingerprint from scratch
+    for (int c = 0; c < 2 * b.Tr; c++) {
+      const int r = rot_shift(b.L, b.Tr, c);
+      for (int w = 0; w < kBitWords; w++) {
+        const int i = 32 * w + lane;  // 0-based position of the rotated sequence
+        int bit = 0;
+        if (i < b.L) {
+          int j = i + r;
+          if (j >= b.L) j -= b.L;
+          bit = seq_bit(sm, j + 1);
+        }
+        const unsigned word = __ballot_sync(kFull, bit);
+        if (lane == 0) rbits[w] = word;
+      }
+      __syncwarp();
+      int e = 0;
+      for (int k = lane + 1; k < b.L; k += 32) {
+        const int cv = corr_lag(rbits, b.L, k);
+        e += cv * cv;
+      }
+      e = warp_sum_i32(e);
+      uint64_t h = 0;
+      for (int i = lane; i < b.L; i += 32)
+        if (!((rbits[i >> 5] >> (i & 31)) & 1u)) h ^= b.ztab[i];
+      h = warp_xor_u64(h);
+      if (lane == 0) {
+        const size_t di = (size_t)q * b.width + b.L + c;
+        b.dE[di] = h_contains(b, h) ? INT32_MAX : e;
+        b.dfp[di] = h;
+      }
+      __syncwarp();
     }
     __syncwarp();
   }
@@ -509,13 +571,8 @@ __global__ void pq_best_kernel(PqBufs b) {
   if (st->nU > 0 && b.uE[0] < st->best_E) {
     st->best_E = b.uE[0];
     st->best_fp = b.ufp[0];
-    const int q = b.uidx[0] / b.L, pos = b.uidx[0] % b.L;
-    const uint64_t* src = b.Pseq[st->cur] + (size_t)q * b.W;
-    for (int t = 0; t < b.W; t++) {
-      uint64_t v = src[t];
-      if (t == (pos >> 6)) v ^= 1ull << (pos & 63);
-      b.best_seq[t] = v;
-    }
+    const int q = b.uidx[0] / b.width, col = b.uidx[0] % b.width;
+    pq_child(b.Pseq[st->cur] + (size_t)q * b.W, b, col, b.best_seq);
     st->improvements++;
     st->u = 0;
   } else {
@@ -556,15 +613,10 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
       b.Pfp[nxt][o] = Rfp[a];
       for (int t = 0; t < b.W; t++) b.Pseq[nxt][o * b.W + t] = Rseq[a * b.W + t];
     } else {
-      const int q = b.uidx[ui] / b.L, pos = b.uidx[ui] % b.L;
+      const int q = b.uidx[ui] / b.width, col = b.uidx[ui] % b.width;
       b.PE[nxt][o] = b.uE[ui];
       b.Pfp[nxt][o] = b.ufp[ui];
-      const uint64_t* src = b.Pseq[cur] + (size_t)q * b.W;
-      for (int t = 0; t < b.W; t++) {
-        uint64_t v = src[t];
-        if (t == (pos >> 6)) v ^= 1ull << (pos & 63);
-        b.Pseq[nxt][o * b.W + t] = v;
-      }
+      pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
       h_insert(b, b.ufp[ui]);
     }
   }
@@ -618,7 +670,8 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   const int L = cfg->L, W = (L + 63) / 64;
   Layout ly;
   if (!make_layout(ly, L, 0, 0, kPqM)) return LABS_ERR_INVALID_ARG;
-  const long long nmax = std::max<long long>((long long)cfg->B * L, n_seeds);
+  const int width = L + 2 * cfg->T_r;
+  const long long nmax = std::max<long long>((long long)cfg->B * width, n_seeds);
   const long long nblk = (nmax + kTile - 1) / kTile;
   // workspace layout (one region, 256-byte aligned pieces)
   size_t off = 0;
@@ -643,6 +696,8 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   b.L = L;
   b.W = W;
   b.B = cfg->B;
+  b.Tr = cfg->T_r;
+  b.width = width;
   b.H_log2 = cfg->H_log2;
   b.cap = cfg->cap;
   b.max_exp = cfg->max_expansions;
@@ -708,7 +763,7 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   for (long long r = 0; r < max_rounds; r++) {
     pq_round_begin_kernel<<<1, 1, 0, st>>>(b);
     pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, st>>>(b, ly);
-    sort_and_dedup((long long)cfg->B * L);
+    sort_and_dedup((long long)cfg->B * width);
     pq_best_kernel<<<1, 1, 0, st>>>(b);
     pq_merge_kernel<<<merge_blocks, 256, 0, st>>>(b);
     pq_round_end_kernel<<<1, 1, 0, st>>>(b);

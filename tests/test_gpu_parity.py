@@ -267,11 +267,11 @@ def test_batched_target_hits(lg):
 # ------------------------------------------------------------------------------------------------
 # labs_pq_refine (Algorithm 2, batch-synchronous)
 # ------------------------------------------------------------------------------------------------
-def _pq_compare(lg, L, seeds, cap, B, max_exp, T_u=0, H_log2=20):
+def _pq_compare(lg, L, seeds, cap, B, max_exp, T_u=0, H_log2=20, T_r=0):
     best, bE, st = lg.labs_pq_refine(L, dev_words(seeds), B=B, cap=cap, H_log2=H_log2, max_expansions=max_exp,
-                                     T_u=T_u)
+                                     T_u=T_u, T_r=T_r)
     torch.cuda.synchronize()
-    ob, oE, ofp, ost = oracle.pq_refine(L, seeds, cap, B, max_exp, T_u)
+    ob, oE, ofp, ost = oracle.pq_refine(L, seeds, cap, B, max_exp, T_u, T_r)
     gs = lg.pq_stats_numpy(st)
     assert int(bE.cpu()[0]) == oE
     assert int(gs["best_fp"]) == ofp
@@ -293,6 +293,23 @@ def test_pq_duplicate_seeds_and_tu_stop(lg):
     s = inp.random_words(6, L, seed=9)
     seeds = np.concatenate([s, s[:3]])  # repeated seeds are admitted once
     _pq_compare(lg, L, seeds, 1 << 12, 4, 10**6, T_u=40)
+
+
+@pytest.mark.parametrize("L,n_seeds,cap,B,max_exp,T_r", [(13, 2, 1 << 14, 1, 150, 2), (31, 6, 200, 8, 400, 5),
+                                                         (64, 4, 5000, 16, 500, 1), (101, 8, 3000, 32, 600, 8),
+                                                         (451, 24, 1 << 16, 64, 640, 4)])
+def test_pq_rotations(lg, L, n_seeds, cap, B, max_exp, T_r):
+    """MAKE_ROTATIONS (T_r > 0): best, energy and every statistic equal the oracle's, with and without
+    eviction, at B = 1 (Algorithm 2 step by step) and in batches."""
+    seeds = inp.random_words(n_seeds, L, seed=3 * L + T_r)
+    _pq_compare(lg, L, seeds, cap, B, max_exp, T_r=T_r)
+
+
+def test_pq_rejects_bad_rotation_count(lg):
+    seeds = dev_words(inp.random_words(2, 13, seed=1))
+    for T_r in (-1, 7, 65):
+        with pytest.raises(lg.LabsError):
+            lg.labs_pq_refine(13, seeds, B=4, cap=64, H_log2=12, max_expansions=10, T_r=T_r)
 
 
 @pytest.mark.parametrize("L", [451, 527])

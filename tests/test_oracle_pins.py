@@ -379,8 +379,10 @@ def test_threshold_is_nearest_rank_of_samples():
 # --------------------------------------------------------------------------------------------
 # Algorithm 2 (priority queue)
 # --------------------------------------------------------------------------------------------
-def _textbook_pq(L, seeds_pm1, max_expansions):
-    """Algorithm 2 with B = 1: a heapq best-first search with an exact hash set of visited states."""
+def _textbook_pq(L, seeds_pm1, max_expansions, T_r=0):
+    """Algorithm 2 with B = 1: a heapq best-first search with an exact hash set of visited states; with
+    T_r > 0 every pivot also offers its rotations by 1..T_r elements left (s[r:] + s[:r]) and right
+    (s[-r:] + s[:-r])."""
     Z = [int(z) for z in oracle.zobrist(L)]
 
     def fp_of(s):
@@ -413,6 +415,11 @@ def _textbook_pq(L, seeds_pm1, max_expansions):
             t = list(s)
             t[i] = -t[i]
             kids.append(((np_energy(t), nfp), tuple(t)))
+        rots = [s[r:] + s[:r] for r in range(1, T_r + 1)] + [s[-r:] + s[:-r] for r in range(1, T_r + 1)]
+        for t in rots:
+            rfp = fp_of(t)
+            if rfp not in H:
+                kids.append(((np_energy(t), rfp), tuple(t)))
         kids.sort()
         for key, t in kids:
             if key[1] in H:
@@ -432,6 +439,21 @@ def test_pq_b1_equals_textbook_best_first(L):
     assert (best_E, best_fp) == exp_best
     assert st["expansions"] == exp_n
     assert int(oracle.energy_batch(best_w[None], L)[0]) == best_E
+
+
+@pytest.mark.parametrize("L,T_r", [(9, 1), (12, 3), (15, 7)])
+def test_pq_rotations_b1_equal_textbook(L, T_r):
+    """MAKE_ROTATIONS: with B = 1 the oracle's search with rotations equals the textbook best-first search
+    that also pushes each pivot's 2 T_r rotations."""
+    seeds = inp.random_words(2, L, seed=70 + L)
+    best_w, best_E, best_fp, st = oracle.pq_refine(L, seeds, cap=1 << 20, B=1, max_expansions=50, T_r=T_r)
+    exp_best, exp_n = _textbook_pq(L, oracle.words_to_pm1(seeds, L), 50, T_r=T_r)
+    assert (best_E, best_fp) == exp_best
+    assert st["expansions"] == exp_n
+    assert int(oracle.energy_batch(best_w[None], L)[0]) == best_E
+    # rotations add visited states beyond the flips
+    _, _, _, st0 = oracle.pq_refine(L, seeds, cap=1 << 20, B=1, max_expansions=50)
+    assert st["h_size"] > st0["h_size"]
 
 
 def test_pq_reaches_global_optimum_l13():
