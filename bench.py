@@ -48,10 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network", "operators"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
-                         "network: the proposal network's inference alone")
+                         "network: the proposal network's inference alone; operators: the end-element operators")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -356,6 +356,48 @@ def network_roofline(lg, L, n, local):
             "status": status, "peak_source": src}
 
 
+def run_operators(args, ws, rank, local):
+    """The end-element operators at L=451 on 2^20 sequences (the four L+1 and two L-1 results with their
+    exact energies), as results per second.  The work is the six energies: one popcount per 32 products,
+    sum over k of ceil((L'-k)/32) per result; POPC issues at 16 lanes per clock per SM on this part."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    lg.load()
+    L, n = W1["L"], 1 << 20
+    w = torch.from_numpy(inp.random_words(n, L, seed=11).view(np.int64)).to(torch.device("cuda", local))
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        lg.labs_sequence_operators(L, w)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(st)
+    for _ in range(reps):
+        lg.labs_sequence_operators(L, w)
+    e1.record(st)
+    st.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    def popc_per_energy(Lv):  # one popcount per 32 products of each lag
+        return sum(-(-(Lv - k) // 32) for k in range(1, Lv))
+
+    popc = 4 * popc_per_energy(L + 1) + 2 * popc_per_energy(L - 1)
+    ach = popc * n / (ms * 1e-3) / 1e9
+    peak = SMS * 16 * SM_MAX_MHZ * 1e6 / 1e9
+    line = {"metric": "operator results/s", "value": 6 * n / (ms * 1e-3), "unit": "results/s", "n_gpus": 1,
+            "steps": reps, "warmup": 3, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "sequence_operators_L451_2^20seq", "L": L, "n": n},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpopc/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "operators_kernel",
+                         "work": "6 energies per sequence: sum_k ceil((L'-k)/32) popcounts each; "
+                                 "peak = 152 SMs x 16 POPC/clk x 2070 MHz"}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_network(args, ws, rank, local):
     """The proposal network's inference at L=451 on 8,192 sequences (one chunk's worth of walks), as
     sequences scored per second, with the tensor-core roofline of the forward."""
@@ -409,6 +451,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "operators":
+        return run_operators(args, ws, rank, local)
     if args.workload == "network":
         return run_network(args, ws, rank, local)
     if args.workload == "learned":

@@ -330,6 +330,20 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
                         void* stream);
 
 /*
+ * labs_sequence_operators -- the end-element operators of Section 3 (Fig. 4): appending or removing one
+ * element at either end moves a candidate of length L to L+1 or L-1 with a comparable merit factor, and
+ * the results re-enter step 2 (labs_pq_refine at the new length).  For each input sequence S (length L):
+ *   grow[q][v], length L+1:   v = 0: S then +1,  1: S then -1,  2: +1 then S,  3: -1 then S;
+ *   shrink[q][v], length L-1: v = 0: S without its last element,  1: S without its first element;
+ * with the exact energies of the six results.
+ *   seqs [n][W(L)] uint64; grow [n][4][W(L+1)] uint64; E_grow [n][4] int32; shrink [n][2][W(L-1)]
+ *   uint64; E_shrink [n][2] int32 -- all device; any output may be NULL (not computed / not written).
+ * Errors: LABS_ERR_INVALID_ARG for L outside [3, 575], n < 0, a NULL or misaligned pointer.
+ */
+int labs_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
+                            uint64_t* shrink, int32_t* E_shrink, void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

@@ -58,6 +58,7 @@ def lib():
             "oracle_threshold": (ci, [ci, ci, ci, P, ci, ci, u64, i64, i64, P, P]),
             "oracle_skew_exhaustive": (ci, [ci, ci, P, P, P, P, P]),
             "oracle_pq_refine": (ci, [ci, P, ci, i64, ci, i64, i64, ci, P, P, P, P]),
+            "oracle_sequence_operators": (ci, [P, ci, i64, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -260,3 +261,15 @@ def pq_refine(L, seeds, cap, B, max_expansions, T_u=0, T_r=0):
                                   _p(st)), "pq_refine")
     names = ["expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements", "stop_reason"]
     return best, int(bE[0]), int(bfp[0]), dict(zip(names, (int(x) for x in st)))
+
+
+def sequence_operators(seqs, L):
+    """End-element operators: (grow [n, 4, W(L+1)], E_grow [n, 4], shrink [n, 2, W(L-1)], E_shrink [n, 2])."""
+    w = _words(seqs, L)
+    n = w.shape[0]
+    grow = np.zeros((n, 4, words_per_seq(L + 1)), dtype=np.uint64)
+    Eg = np.zeros((n, 4), dtype=np.int32)
+    shrink = np.zeros((n, 2, words_per_seq(L - 1)), dtype=np.uint64)
+    Es = np.zeros((n, 2), dtype=np.int32)
+    _check(lib().oracle_sequence_operators(_p(w), L, n, _p(grow), _p(Eg), _p(shrink), _p(Es)), "sequence_operators")
+    return grow, Eg, shrink, Es

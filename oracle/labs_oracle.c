@@ -908,3 +908,37 @@ int oracle_pq_refine(int L, const uint64_t* seeds, int n_seeds, int64_t cap, int
   *best_fp_out = best_fp;
   return status;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * End-element sequence operators (Section 3, the loop of Fig. 4 back into step 2): for every input
+ * sequence S of length L the four sequences of length L+1 (S then +1, S then -1, +1 then S, -1 then S)
+ * and the two of length L-1 (S without its last element, S without its first), with their energies by
+ * the Section 1 definition.  Parity pinned by restating the operators with list slicing in the tests.
+ * --------------------------------------------------------------------------------------------- */
+int oracle_sequence_operators(const uint64_t* words, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
+                              uint64_t* shrink, int32_t* E_shrink) {
+  if (L < 3 || L + 1 > ORACLE_MAX_L || n < 0) return ORC_ERR_ARG;
+  const int W = (L + 63) / 64, Wg = (L + 64) / 64, Ws = (L + 62) / 64;
+  int8_t s[ORACLE_MAX_L], t[ORACLE_MAX_L + 1];
+  for (int64_t q = 0; q < n; q++) {
+    unpack(words + q * W, L, s);
+    for (int v = 0; v < 4; v++) {
+      const int8_t x = (v & 1) ? -1 : 1;
+      if (v < 2) {
+        memcpy(t, s, (size_t)L);
+        t[L] = x;
+      } else {
+        t[0] = x;
+        memcpy(t + 1, s, (size_t)L);
+      }
+      pack(t, L + 1, grow + (q * 4 + v) * Wg);
+      E_grow[q * 4 + v] = (int32_t)energy(t, L + 1);
+    }
+    for (int v = 0; v < 2; v++) {
+      const int8_t* src = v == 0 ? s : s + 1;
+      pack(src, L - 1, shrink + (q * 2 + v) * Ws);
+      E_shrink[q * 2 + v] = (int32_t)energy(src, L - 1);
+    }
+  }
+  return ORC_OK;
+}

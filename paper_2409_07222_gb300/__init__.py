@@ -216,6 +216,21 @@ def labs_pq_refine(L, seeds, B=4096, cap=1 << 22, H_log2=24, max_expansions=10**
     return best, bE, st
 
 
+def labs_sequence_operators(L, seqs, device=None):
+    """The end-element operators: returns (grow int64 [n, 4, W(L+1)], E_grow int32 [n, 4],
+    shrink int64 [n, 2, W(L-1)], E_shrink int32 [n, 2]) for packed sequences of length L (device int64)."""
+    s = _dev_words(seqs, L)
+    dev = s.device
+    n = s.shape[0]
+    grow = torch.empty((n, 4, words_per_seq(L + 1)), dtype=torch.int64, device=dev)
+    Eg = torch.empty((n, 4), dtype=torch.int32, device=dev)
+    shrink = torch.empty((n, 2, words_per_seq(L - 1)), dtype=torch.int64, device=dev)
+    Es = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    _lib.check(load().labs_sequence_operators(context(dev.index), _ptr(s), L, n, _ptr(grow), _ptr(Eg), _ptr(shrink),
+                                              _ptr(Es), _stream(dev)), "labs_sequence_operators")
+    return grow, Eg, shrink, Es
+
+
 def pq_stats_numpy(st):
     return st.cpu().numpy().view(PQ_STATS_DTYPE)[0]
 

@@ -224,6 +224,17 @@ int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds,
   return labsg::launch_pq_refine(ctx, cfg, seeds, n_seeds, best_seq, best_E, stats, (cudaStream_t)stream);
 }
 
+int labs_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
+                            uint64_t* shrink, int32_t* E_shrink, void* stream) {
+  if (!ctx || L < 3 || L > LABS_MAX_L - 1 || n < 0) return LABS_ERR_INVALID_ARG;
+  if (n > 0 && (!seqs || !aligned8(seqs) || (grow && !aligned8(grow)) || (shrink && !aligned8(shrink)) ||
+                (E_grow && !aligned4(E_grow)) || (E_shrink && !aligned4(E_shrink))))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_sequence_operators(ctx, seqs, L, n, grow, E_grow, shrink, E_shrink, (cudaStream_t)stream);
+}
+
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
   if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;

@@ -61,6 +61,8 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
                           const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
                           labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
                           cudaStream_t st);
+int launch_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
+                              uint64_t* shrink, int32_t* E_shrink, cudaStream_t st);
 int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                      int32_t* best_E, labs_pq_stats* stats, cudaStream_t st);
 int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,

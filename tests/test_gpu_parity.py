@@ -316,3 +316,44 @@ def test_pq_rejects_bad_rotation_count(lg):
 def test_pq_paper_lengths(lg, L):
     seeds = oracle.skew_fill(inp.random_words(24, L, seed=L), L) if L % 2 else inp.random_words(24, L, seed=L)
     _pq_compare(lg, L, seeds, 4096, 64, 256)
+
+
+# ------------------------------------------------------------------------------------------------
+# End-element sequence operators and the loop back into step 2 (Fig. 4)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [3, 4, 31, 32, 33, 63, 64, 65, 127, 128, 129, 451, 574, 575])
+def test_sequence_operators(lg, L):
+    seqs = np.concatenate([inp.random_words(37, L, seed=L), inp.edge_words(L)])
+    g, Eg, s, Es = lg.labs_sequence_operators(L, dev_words(seqs))
+    torch.cuda.synchronize()
+    og, oEg, os_, oEs = oracle.sequence_operators(seqs, L)
+    assert np.array_equal(host_words(g.cpu()).reshape(og.shape), og)
+    assert np.array_equal(Eg.cpu().numpy(), oEg)
+    assert np.array_equal(host_words(s.cpu()).reshape(os_.shape), os_)
+    assert np.array_equal(Es.cpu().numpy(), oEs)
+
+
+def test_sequence_operators_empty_and_bad_length(lg):
+    g, Eg, s, Es = lg.labs_sequence_operators(13, dev_words(inp.random_words(0, 13, seed=1)))
+    assert g.shape[0] == 0
+    for L in (2, 576):
+        with pytest.raises(lg.LabsError):
+            lg.labs_sequence_operators(L, dev_words(inp.random_words(2, L, seed=1)))
+
+
+def test_operators_feed_step2(lg):
+    """Step 2 at L, the operators on its best sequence, then step 2 again at L+1 and L-1 from the grown
+    and shrunk sequences: every stage equals the oracle's."""
+    L = 21
+    seeds = inp.random_words(6, L, seed=5)
+    best, bE, _ = lg.labs_pq_refine(L, dev_words(seeds), B=8, cap=4096, H_log2=16, max_expansions=300)
+    ob, oE, _, _ = oracle.pq_refine(L, seeds, 4096, 8, 300)
+    assert int(bE.cpu()[0]) == oE and np.array_equal(host_words(best.cpu()), ob)
+    g, Eg, s, Es = lg.labs_sequence_operators(L, best.reshape(1, -1))
+    og, oEg, os_, oEs = oracle.sequence_operators(ob[None], L)
+    assert np.array_equal(Eg.cpu().numpy(), oEg) and np.array_equal(Es.cpu().numpy(), oEs)
+    for Ln, dev_seeds, host_seeds in ((L + 1, g.reshape(4, -1), og.reshape(4, -1)),
+                                      (L - 1, s.reshape(2, -1), os_.reshape(2, -1))):
+        best2, bE2, _ = lg.labs_pq_refine(Ln, dev_seeds, B=4, cap=2048, H_log2=16, max_expansions=200)
+        ob2, oE2, _, _ = oracle.pq_refine(Ln, host_seeds, 2048, 4, 200)
+        assert int(bE2.cpu()[0]) == oE2 and np.array_equal(host_words(best2.cpu()), ob2)

@@ -473,3 +473,24 @@ def test_pq_batch_invariants():
     assert st_small["expansions"] == 400 and st_big["expansions"] == 400
     assert st_small["evicted"] > 0
     assert st_big["admitted"] + 8 == st_big["h_size"]
+
+
+# --------------------------------------------------------------------------------------------
+# End-element sequence operators (Fig. 4 loop back into step 2)
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [3, 13, 64, 65, 127, 128, 451, 575])
+def test_sequence_operators_by_slicing(L):
+    """The six results equal the operators written with list slicing, and their energies equal the
+    energy of those lists computed with numpy."""
+    seqs = inp.random_words(5, L, seed=L + 7)
+    grow, Eg, shrink, Es = oracle.sequence_operators(seqs, L)
+    for q, s in enumerate(oracle.words_to_pm1(seqs, L)):
+        s = list(int(v) for v in s)
+        want_g = [s + [1], s + [-1], [1] + s, [-1] + s]
+        want_s = [s[:-1], s[1:]]
+        for v, t in enumerate(want_g):
+            assert list(oracle.words_to_pm1(grow[q, v][None], L + 1)[0]) == t
+            assert Eg[q, v] == np_energy(t)
+        for v, t in enumerate(want_s):
+            assert list(oracle.words_to_pm1(shrink[q, v][None], L - 1)[0]) == t
+            assert Es[q, v] == np_energy(t)
