@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network", "operators"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network", "operators", "legendre"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
-                         "network: the proposal network's inference alone; operators: the end-element operators")
+                         "network: the proposal network's inference alone; operators: the end-element operators; "
+                         "legendre: Legendre seeds for step 2 (Table 2 lengths)")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -398,6 +399,65 @@ def run_operators(args, ws, rank, local):
     return 0
 
 
+def run_legendre(args, ws, rank, local):
+    """Legendre seeds: the construction's throughput (every rotation of every prime with up to 30%
+    appended, L = 450..527, exact energies on the device) with its POPC roofline; then, at the lengths of
+    Table 2, the (0.20, 0.24, 0.1) family and step 2 (Algorithm 2, B = 4,096, open set 2^22) from all of
+    its seeds, with the best constructed and refined merit factors per length (Table 2 prints 6.1976 /
+    6.3088, 6.2332 / 6.2998, 6.4292 / 6.4292, 6.3240 / 6.3240: context from the paper's own search)."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lg.load()
+    S2 = inp.STEP2
+    # construction throughput: every rotation of every prime with up to 30% appended, L = 450..527
+    fams = [(L, torch.from_numpy(lg.labs_legendre_family(L, 0.0, 1.0, 0.3)).to(dev)) for L in range(450, 528)]
+    for L, fam in fams[:2]:
+        lg.labs_legendre_construct(L, fam)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for L, fam in fams:
+        lg.labs_legendre_construct(L, fam)
+    e1.record()
+    torch.cuda.synchronize()
+    t_con = e0.elapsed_time(e1) * 1e-3
+    n_tot = sum(int(f.shape[0]) for _, f in fams)
+    popc_tot = sum(int(f.shape[0]) * sum(-(-(L - k) // 32) for k in range(1, L)) for L, f in fams)
+    # Table 2 lengths: the (0.20, 0.24, 0.1) family, then step 2 from all of its seeds
+    per_L = []
+    for L in (450, 471, 491, 526):
+        fam = torch.from_numpy(lg.labs_legendre_family(L)).to(dev)
+        seqs, E = lg.labs_legendre_construct(L, fam)
+        torch.cuda.synchronize()
+        n = fam.shape[0]
+        t0 = time.perf_counter()
+        best, bE, st = lg.labs_pq_refine(L, seqs, B=S2["B"], cap=S2["cap"], H_log2=args.pq_hlog2,
+                                         max_expansions=args.pq_expansions, T_u=S2["T_u"])
+        torch.cuda.synchronize()
+        t_pq = time.perf_counter() - t0
+        s2 = lg.pq_stats_numpy(st)
+        per_L.append({"L": L, "seeds": int(n), "F_construct": round(L * L / (2.0 * int(E.min())), 4),
+                      "F_refined": round(L * L / (2.0 * int(bE.cpu()[0])), 4), "expansions": int(s2["expansions"]),
+                      "refine_s": t_pq})
+    peak = SMS * 16 * SM_MAX_MHZ * 1e6 / 1e9
+    ach = popc_tot / t_con / 1e9
+    line = {"metric": "seeds/s", "value": n_tot / t_con, "unit": "seeds/s", "n_gpus": 1, "steps": 1, "warmup": 2,
+            "ms_per_step": t_con * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "legendre_seeds_L450-527_all_rotations", "seeds": n_tot,
+                       "table2_family": "r 0.20..0.24 of L, t <= 0.1 p", "max_expansions": args.pq_expansions},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpopc/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "legendre_kernel",
+                         "work": "sum_k ceil((L-k)/32) popcounts per seed; peak = 152 SMs x 16 POPC/clk x 2070 MHz"},
+            "per_length": per_L}
+    print(json.dumps(line))
+    return 0
+
+
 def run_network(args, ws, rank, local):
     """The proposal network's inference at L=451 on 8,192 sequences (one chunk's worth of walks), as
     sequences scored per second, with the tensor-core roofline of the forward."""
@@ -451,6 +511,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "legendre":
+        return run_legendre(args, ws, rank, local)
     if args.workload == "operators":
         return run_operators(args, ws, rank, local)
     if args.workload == "network":

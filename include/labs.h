@@ -344,6 +344,29 @@ int labs_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t 
                             uint64_t* shrink, int32_t* E_shrink, void* stream);
 
 /*
+ * Legendre-sequence seeds for step 2 (Section 4, Table 2).  A seed is the periodic extension of a
+ * rotated Legendre sequence of prime length p <= L:
+ *     s_i = chi((i + off) mod p),  i = 0 .. L-1   (the rotation by `off`, then its first L - p elements
+ *                                                  appended),
+ * chi(j) = +1 for a non-zero quadratic residue j mod p, -1 otherwise (j = 0 included).
+ *
+ * labs_legendre_family (host only, no device work) -- the parameter family of length L: every prime
+ *   p <= L with L - p <= t_max * p and every rotation off < p with r_lo <= off / L <= r_hi, written as
+ *   (p, off) int32 pairs to params [max_n][2] (host; NULL to count only), in increasing (p, off);
+ *   *n_out receives the family size.  LABS_ERR_CAPACITY if it exceeds max_n (the first max_n are written).
+ *   The family (0.20, 0.24, 0.1) reproduces the construction column of Table 2.
+ * labs_legendre_construct -- the n seeds of params [n][2] (DEVICE int32 pairs, p prime, 0 <= off < p,
+ *   p <= L) as packed sequences seqs [n][W] and exact energies E_out [n] (device; either may be NULL).
+ *   A pair that is not a seed of length L (p not a prime in [2, L], off outside [0, p)) gets a zero
+ *   sequence and E = INT32_MAX.
+ * Errors: LABS_ERR_INVALID_ARG for L outside [3, 576], bad ranges or pointers.
+ */
+int labs_legendre_family(int L, double r_lo, double r_hi, double t_max, int32_t* params, int64_t max_n,
+                         int64_t* n_out);
+int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t n, uint64_t* seqs, int32_t* E_out,
+                            void* stream);
+
+/*
  * labs_skew_exhaustive -- every skew-symmetric sequence (Eq. 2) of odd length L <= 127 behind the
  * prefix (Eq. 3, p <= k), 2^(k-p+1) of them, with k-p+1 <= 40.  Free bit j of an assignment is 1 iff
  * s_{p+1+j} = -1.

@@ -59,6 +59,7 @@ def lib():
             "oracle_skew_exhaustive": (ci, [ci, ci, P, P, P, P, P]),
             "oracle_pq_refine": (ci, [ci, P, ci, i64, ci, i64, i64, ci, P, P, P, P]),
             "oracle_sequence_operators": (ci, [P, ci, i64, P, P, P, P]),
+            "oracle_legendre_construct": (ci, [ci, P, i64, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -273,3 +274,13 @@ def sequence_operators(seqs, L):
     Es = np.zeros((n, 2), dtype=np.int32)
     _check(lib().oracle_sequence_operators(_p(w), L, n, _p(grow), _p(Eg), _p(shrink), _p(Es)), "sequence_operators")
     return grow, Eg, shrink, Es
+
+
+def legendre_construct(L, params):
+    """Legendre seeds for (p, off) pairs: (packed words [n, W], energies [n])."""
+    pr = np.ascontiguousarray(np.asarray(params, dtype=np.int32).reshape(-1, 2))
+    n = pr.shape[0]
+    w = np.zeros((n, words_per_seq(L)), dtype=np.uint64)
+    E = np.zeros(n, dtype=np.int32)
+    _check(lib().oracle_legendre_construct(L, _p(pr), n, _p(w), _p(E)), "legendre_construct")
+    return w, E

@@ -942,3 +942,29 @@ int oracle_sequence_operators(const uint64_t* words, int L, int64_t n, uint64_t*
   }
   return ORC_OK;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Legendre-sequence seeds (Section 4, Table 2): s_i = chi((i + off) mod p) for i = 0..L-1, the rotation of
+ * the Legendre sequence of prime length p by off with its first L - p elements appended; chi(j) = +1 for a
+ * non-zero square mod p, -1 otherwise (chi(0) = -1).  Squares found by listing k^2 mod p.  Pinned by the
+ * construction column of Table 2 and by the two-valued periodic autocorrelation of Legendre sequences.
+ * --------------------------------------------------------------------------------------------- */
+int oracle_legendre_construct(int L, const int32_t* params, int64_t n, uint64_t* words, int32_t* E_out) {
+  if (L < 3 || L > ORACLE_MAX_L || n < 0) return ORC_ERR_ARG;
+  const int W = (L + 63) / 64;
+  int8_t s[ORACLE_MAX_L];
+  uint8_t square[ORACLE_MAX_L];
+  for (int64_t q = 0; q < n; q++) {
+    const int p = params[2 * q], off = params[2 * q + 1];
+    if (p < 2 || p > L || off < 0 || off >= p) return ORC_ERR_ARG;
+    memset(square, 0, (size_t)p);
+    for (int k = 1; k < p; k++) square[(k * k) % p] = 1;
+    for (int i = 0; i < L; i++) {
+      const int j = (i + off) % p;
+      s[i] = (j != 0 && square[j]) ? 1 : -1;
+    }
+    pack(s, L, words + q * W);
+    E_out[q] = (int32_t)energy(s, L);
+  }
+  return ORC_OK;
+}

@@ -231,6 +231,30 @@ def labs_sequence_operators(L, seqs, device=None):
     return grow, Eg, shrink, Es
 
 
+def labs_legendre_family(L, r_lo=0.20, r_hi=0.24, t_max=0.1):
+    """Host enumeration of the Legendre seed family: int32 numpy [n, 2] of (prime p, rotation off)."""
+    n = ctypes.c_int64()
+    _lib.check(load().labs_legendre_family(L, r_lo, r_hi, t_max, None, 0, ctypes.byref(n)), "labs_legendre_family")
+    out = np.zeros((n.value, 2), dtype=np.int32)
+    if n.value:
+        _lib.check(load().labs_legendre_family(L, r_lo, r_hi, t_max, out.ctypes.data_as(ctypes.c_void_p), n.value,
+                                               ctypes.byref(n)), "labs_legendre_family")
+    return out
+
+
+def labs_legendre_construct(L, params, device=None):
+    """Seeds for (p, off) pairs (int32 [n, 2], host or device): (packed int64 [n, W], energies int32 [n])."""
+    dev = _device(device)
+    pr = torch.as_tensor(np.ascontiguousarray(params, dtype=np.int32) if not torch.is_tensor(params) else params,
+                         dtype=torch.int32).to(dev).contiguous().reshape(-1, 2)
+    n = pr.shape[0]
+    seqs = torch.empty((n, words_per_seq(L)), dtype=torch.int64, device=dev)
+    E = torch.empty(n, dtype=torch.int32, device=dev)
+    _lib.check(load().labs_legendre_construct(context(dev.index), L, _ptr(pr), n, _ptr(seqs), _ptr(E), _stream(dev)),
+               "labs_legendre_construct")
+    return seqs, E
+
+
 def pq_stats_numpy(st):
     return st.cpu().numpy().view(PQ_STATS_DTYPE)[0]
 

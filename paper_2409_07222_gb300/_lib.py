@@ -36,6 +36,8 @@ SIGNATURES = {
     "labs_sample_threshold_noalloc": (_ci, [_ci, _ci, _ci, _P, _ci, _u64, _i64, _i64, _P, _P]),
     "labs_batched_search": (_ci, [_P, _P, _P, _P, _P, _ci, _P, _P, _P, _P, _P]),
     "labs_sequence_operators": (_ci, [_P, _P, _ci, _i64, _P, _P, _P, _P, _P]),
+    "labs_legendre_family": (_ci, [_ci, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _i64, _P]),
+    "labs_legendre_construct": (_ci, [_P, _ci, _P, _i64, _P, _P, _P]),
     "labs_pq_refine": (_ci, [_P, _P, _P, _ci, _P, _P, _P, _P]),
     "labs_chunked_search": (_ci, [_P, _P, _P, ctypes.c_float, _ci, _P, _ci, _P, _P, _P, _P, _P, _P, _P]),
     "labs_policy_param_count": (_ci, [_ci, _P]),

@@ -235,6 +235,23 @@ int labs_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t 
   return labsg::launch_sequence_operators(ctx, seqs, L, n, grow, E_grow, shrink, E_shrink, (cudaStream_t)stream);
 }
 
+int labs_legendre_family(int L, double r_lo, double r_hi, double t_max, int32_t* params, int64_t max_n,
+                         int64_t* n_out) {
+  if (L < 3 || L > LABS_MAX_L || !(r_lo >= 0.0) || !(r_hi >= r_lo) || !(t_max >= 0.0) || !n_out || max_n < 0)
+    return LABS_ERR_INVALID_ARG;
+  return labsg::legendre_family(L, r_lo, r_hi, t_max, params, max_n, n_out);
+}
+
+int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t n, uint64_t* seqs, int32_t* E_out,
+                            void* stream) {
+  if (!ctx || L < 3 || L > LABS_MAX_L || n < 0) return LABS_ERR_INVALID_ARG;
+  if (n > 0 && (!params || !aligned4(params) || (seqs && !aligned8(seqs)) || (E_out && !aligned4(E_out))))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_legendre(ctx, L, params, n, seqs, E_out, (cudaStream_t)stream);
+}
+
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
   if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;

@@ -62,3 +62,30 @@ def test_null_context_is_rejected_without_gpu(lib):
     # argument validation happens before any CUDA call
     assert lib.labs_energy_batch(None, None, 13, 0, None, None, None) == 1
     assert lib.labs_flip_deltas(None, None, None, 13, 0, 0, 0, None, None) == 1
+
+
+def test_legendre_family_host_enumeration(lib):
+    """labs_legendre_family (host code, no device) lists exactly the (prime, rotation) pairs of its
+    definition, in increasing order, and reports a short buffer as a capacity error."""
+    import ctypes
+
+    import numpy as np
+
+    def family(L, r_lo, r_hi, t_max):
+        primes = [p for p in range(2, L + 1) if all(p % d for d in range(2, int(p ** 0.5) + 1))]
+        return [(p, o) for p in primes if L - p <= t_max * p for o in range(p) if r_lo <= o / L <= r_hi]
+
+    f = lib.labs_legendre_family
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                  ctypes.c_void_p]
+    for L, r_lo, r_hi, t_max in ((450, 0.20, 0.24, 0.1), (37, 0.0, 1.0, 0.5), (101, 0.2, 0.25, 0.05)):
+        want = family(L, r_lo, r_hi, t_max)
+        n = ctypes.c_int64()
+        assert f(L, r_lo, r_hi, t_max, None, 0, ctypes.byref(n)) == 0 and n.value == len(want)
+        out = np.zeros((len(want), 2), dtype=np.int32)
+        assert f(L, r_lo, r_hi, t_max, out.ctypes.data, len(want), ctypes.byref(n)) == 0
+        assert [tuple(r) for r in out.tolist()] == want
+        if len(want) > 1:
+            short = np.zeros((1, 2), dtype=np.int32)
+            assert f(L, r_lo, r_hi, t_max, short.ctypes.data, 1, ctypes.byref(n)) == 2  # LABS_ERR_CAPACITY

@@ -357,3 +357,37 @@ def test_operators_feed_step2(lg):
         best2, bE2, _ = lg.labs_pq_refine(Ln, dev_seeds, B=4, cap=2048, H_log2=16, max_expansions=200)
         ob2, oE2, _, _ = oracle.pq_refine(Ln, host_seeds, 2048, 4, 200)
         assert int(bE2.cpu()[0]) == oE2 and np.array_equal(host_words(best2.cpu()), ob2)
+
+
+# ------------------------------------------------------------------------------------------------
+# Legendre seeds (Section 4, Table 2)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [3, 64, 65, 450, 471, 491, 526, 576])
+def test_legendre_construct(lg, L):
+    fam = lg.labs_legendre_family(L, 0.0, 1.0, 0.3)
+    rng = np.random.default_rng(L)
+    pick = fam[rng.choice(len(fam), size=min(len(fam), 300), replace=False)] if len(fam) else fam
+    w, E = lg.labs_legendre_construct(L, pick)
+    ow, oE = oracle.legendre_construct(L, pick)
+    assert np.array_equal(host_words(w.cpu()), ow) and np.array_equal(E.cpu().numpy(), oE)
+
+
+def test_legendre_table2_on_device(lg):
+    """The device's best seed of the (0.20, 0.24, 0.1) family at each tabulated length has the merit
+    factor printed in the construction column of Table 2."""
+    import os
+
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "legendre_table2.txt"))
+            if l.strip() and not l.startswith("#")]
+    for L_s, F_s in rows:
+        L = int(L_s)
+        _, E = lg.labs_legendre_construct(L, lg.labs_legendre_family(L))
+        assert round(L * L / (2 * int(E.min())), 4) == float(F_s)
+
+
+def test_legendre_bad_parameters_give_no_seed(lg):
+    w, E = lg.labs_legendre_construct(13, np.array([[4, 1], [13, 13], [0, 0], [11, 3]], dtype=np.int32))
+    E = E.cpu().numpy()
+    assert list(E[:3]) == [2**31 - 1] * 3
+    _, oE = oracle.legendre_construct(13, [(11, 3)])
+    assert E[3] == oE[0]

@@ -494,3 +494,36 @@ def test_sequence_operators_by_slicing(L):
         for v, t in enumerate(want_s):
             assert list(oracle.words_to_pm1(shrink[q, v][None], L - 1)[0]) == t
             assert Es[q, v] == np_energy(t)
+
+
+# --------------------------------------------------------------------------------------------
+# Legendre seeds (Section 4, Table 2)
+# --------------------------------------------------------------------------------------------
+def _primes(n):
+    return [p for p in range(2, n + 1) if all(p % d for d in range(2, int(p ** 0.5) + 1))]
+
+
+def _legendre_family(L, r_lo=0.20, r_hi=0.24, t_max=0.1):
+    """Every prime p <= L with L - p <= t_max p, every rotation off < p with r_lo <= off / L <= r_hi."""
+    return [(p, off) for p in _primes(L) if L - p <= t_max * p for off in range(p) if r_lo <= off / L <= r_hi]
+
+
+@pytest.mark.parametrize("p", [7, 11, 19, 23, 43, 431, 443, 467, 491])
+def test_legendre_periodic_autocorrelation(p):
+    """For a prime p = 3 (mod 4) every non-trivial periodic autocorrelation of the Legendre sequence is -1;
+    for p = 1 (mod 4) they lie in {1, -3} (classical two-valued property of quadratic-residue sequences)."""
+    w, _ = oracle.legendre_construct(p, [(p, 0)])
+    s = oracle.words_to_pm1(w, p)[0].astype(np.int64)
+    R = [int(np.dot(s, np.roll(s, -k))) for k in range(1, p)]
+    assert set(R) == ({-1} if p % 4 == 3 else {1, -3})
+
+
+def test_legendre_table2_construction_column():
+    """The best seed of the family at each tabulated length has exactly the printed merit factor."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "legendre_table2.txt")) if l.strip() and not l.startswith("#")]
+    for L_s, F_s in rows:
+        L = int(L_s)
+        fam = _legendre_family(L)
+        _, E = oracle.legendre_construct(L, fam)
+        best = int(E.min())
+        assert round(L * L / (2 * best), 4) == float(F_s), (L, best)
