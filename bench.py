@@ -48,15 +48,16 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "learned", "network", "operators", "legendre"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
                          "network: the proposal network's inference alone; operators: the end-element operators; "
-                         "legendre: Legendre seeds for step 2 (Table 2 lengths)")
+                         "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
     ap.add_argument("--pq-tr", type=int, default=0, help="pq workload: MAKE_ROTATIONS per side (0: off)")
+    ap.add_argument("--pq-indep-pops", type=int, default=500, help="pq_indep workload: pops per candidate")
     return ap.parse_args()
 
 
@@ -399,6 +400,59 @@ def run_operators(args, ws, rank, local):
     return 0
 
 
+def run_pq_indep(args, ws, rank, local):
+    """Step 2 with one queue per candidate: the 4,096 best distinct states of a step-1 search at L (as in
+    the pq workload) each refined alone, B = 1, unbounded queue, --pq-indep-pops pops each."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lg.load()
+    L = args.L
+    skew = L % 2 == 1
+    p = W1["p"] if skew else 0
+    pre_h = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"]) if p else np.zeros(1, np.uint64)
+    n_w, R = 16384, 4
+    cfg = lg.make_walk_cfg(L, skew=skew, p=p, n_walks=n_w, flip_budget=5000, seed=W1["seed"], R=R, E_thr=lg.INT32_MAX)
+    out, _, _ = lg.labs_skew_search(cfg, pre_h, with_walk_stats=False)
+    cand = lg.candidates_numpy(out, n_w, R).reshape(-1)
+    cand = cand[cand["E"] != lg.INT32_MAX]
+    order = np.lexsort((cand["fp"], cand["E"]))
+    _, first = np.unique(cand["fp"][order], return_index=True)
+    pick = order[np.sort(first)][: inp.STEP2["n_seeds"]]
+    W = (L + 63) // 64
+    seeds = torch.from_numpy(np.ascontiguousarray(cand["seq"][pick][:, :W]).view(np.int64)).to(dev)
+    pops = args.pq_indep_pops
+    times = []
+    for it in range(max(1, args.warmup) + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, bE, st = lg.labs_pq_independent(L, seeds, max_expansions=pops, H_log2=20)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.mean(times[-args.steps:])
+    stn = st.cpu().numpy().view(lg.PQ_STATS_DTYPE).reshape(-1)
+    exps = int(stn["expansions"].sum())
+    terms = exps * L * (L - 1)
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    line = {"metric": "expansions/s", "value": exps / t, "unit": "expansions/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "step2_independent_L%d_4096candidates_%dpops" % (L, pops), "L": L,
+                       "candidates": int(len(pick)), "pops_each": pops, "H_slots_log2": 20,
+                       "seed_best_E": int(cand["E"][pick].min()), "best_E": int(bE.min().cpu()),
+                       "improved_candidates": int((stn["improvements"] > 0).sum()),
+                       "status_nonzero": int((stn["status"] != 0).sum())},
+            "neighbour_evaluations_per_s": exps * L / t,
+            "roofline": {"bound": "alu", "achieved": terms / t / 1e9, "peak": peak, "unit": "Gop/s",
+                         "frac": terms / t / 1e9 / peak, "traffic": None,
+                         "work": "per expansion L(L-1) neighbour-lag multiply-adds (whole refinement timed)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_legendre(args, ws, rank, local):
     """Legendre seeds: the construction's throughput (every rotation of every prime with up to 30%
     appended, L = 450..527, exact energies on the device) with its POPC roofline; then, at the lengths of
@@ -511,6 +565,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "pq_indep":
+        return run_pq_indep(args, ws, rank, local)
     if args.workload == "legendre":
         return run_legendre(args, ws, rank, local)
     if args.workload == "operators":

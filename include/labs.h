@@ -268,6 +268,32 @@ int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds,
                    int32_t* best_E, labs_pq_stats* stats, void* stream);
 
 /*
+ * labs_pq_independent -- Algorithm 2 run separately for every candidate (the paper's parallelisation of
+ * step 2): candidate q starts its own queue and visited set from seeds[q] and is refined with one pop per
+ * step, the queue unbounded (nothing is evicted), until max_expansions pops, an empty queue, or T_u pops
+ * without improvement.  Equivalent to labs_pq_refine with one seed, B = 1 and a cap never reached
+ * (rotations included when T_r > 0).
+ *   seeds [n][W] uint64, best_seqs [n][W] uint64, best_E [n] int32, stats [n] labs_pq_stats -- device.
+ *   Memory: each resident warp holds max_expansions x (L + 2 T_r) x 16 B of queue records, 24 B per pop
+ *   of run heads, 8 W B per pop of pivots and 2^H_log2 x 8 B of visited set; as many warps run as fit in
+ *   max_workspace_bytes (0: 64 GiB) and the occupancy limit, the rest of the candidates wait for a warp.
+ * Errors: LABS_ERR_INVALID_ARG on a bad configuration; per candidate, stats.status = LABS_ERR_CAPACITY if
+ * its visited set passed 3/4 load (raise H_log2).
+ */
+typedef struct {
+  int32_t L;                   /* 2..576 */
+  int32_t T_r;                 /* rotations per side: 0..64, 2 T_r < L */
+  int32_t H_log2;              /* visited set per candidate: 2^H_log2 slots, 10..30 */
+  int32_t reserved;            /* 0 */
+  int64_t max_expansions;      /* pops per candidate, 1..2^21 - 1 */
+  int64_t T_u;                 /* stop after T_u pops without improvement; <= 0: no limit */
+  int64_t max_workspace_bytes; /* device memory for the resident warps; 0: 64 GiB */
+} labs_pq_indep_cfg;
+
+int labs_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint64_t* seeds, int n, uint64_t* best_seqs,
+                        int32_t* best_E, labs_pq_stats* stats, void* stream);
+
+/*
  * Learned flip proposal (library extension; the paper has no learned component).  A small network --
  * features (s_i, C_k / sqrt(L-k)), three Conv1d(64, kernel 9) layers, Linear(64L -> 256), Linear(256 -> L)
  * -- scores the L positions of a sequence; walks may bias their neighbour choice with it while the exact

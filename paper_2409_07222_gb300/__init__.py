@@ -255,6 +255,22 @@ def labs_legendre_construct(L, params, device=None):
     return seqs, E
 
 
+def labs_pq_independent(L, seeds, max_expansions, T_u=0, T_r=0, H_log2=20, max_workspace_bytes=0, device=None):
+    """Algorithm 2 separately for every seed (device int64 [n, W]): (best words [n, W], best E [n], stats [n])."""
+    s = _dev_words(seeds, L)
+    dev = s.device
+    n = s.shape[0]
+    cfg = _lib.PqIndepCfg()
+    cfg.L, cfg.T_r, cfg.H_log2, cfg.reserved = L, T_r, H_log2, 0
+    cfg.max_expansions, cfg.T_u, cfg.max_workspace_bytes = max_expansions, T_u, max_workspace_bytes
+    best = torch.empty((n, words_per_seq(L)), dtype=torch.int64, device=dev)
+    bE = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty((n, _lib.PQ_STATS_BYTES), dtype=torch.uint8, device=dev)
+    _lib.check(load().labs_pq_independent(context(dev.index), ctypes.byref(cfg), _ptr(s), n, _ptr(best), _ptr(bE),
+                                          _ptr(st), _stream(dev)), "labs_pq_independent")
+    return best, bE, st
+
+
 def pq_stats_numpy(st):
     return st.cpu().numpy().view(PQ_STATS_DTYPE)[0]
 

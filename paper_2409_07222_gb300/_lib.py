@@ -38,6 +38,7 @@ SIGNATURES = {
     "labs_sequence_operators": (_ci, [_P, _P, _ci, _i64, _P, _P, _P, _P, _P]),
     "labs_legendre_family": (_ci, [_ci, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _i64, _P]),
     "labs_legendre_construct": (_ci, [_P, _ci, _P, _i64, _P, _P, _P]),
+    "labs_pq_independent": (_ci, [_P, _P, _P, _ci, _P, _P, _P, _P]),
     "labs_pq_refine": (_ci, [_P, _P, _P, _ci, _P, _P, _P, _P]),
     "labs_chunked_search": (_ci, [_P, _P, _P, ctypes.c_float, _ci, _P, _ci, _P, _P, _P, _P, _P, _P, _P]),
     "labs_policy_param_count": (_ci, [_ci, _P]),
@@ -82,6 +83,15 @@ class PqCfg(ctypes.Structure):
     _fields_ = [
         ("L", _i32), ("B", _i32), ("cap", _i64), ("H_log2", _i32), ("T_r", _i32),
         ("max_expansions", _i64), ("T_u", _i64),
+    ]
+
+
+class PqIndepCfg(ctypes.Structure):
+    """labs_pq_indep_cfg (include/labs.h)."""
+
+    _fields_ = [
+        ("L", _i32), ("T_r", _i32), ("H_log2", _i32), ("reserved", _i32), ("max_expansions", _i64),
+        ("T_u", _i64), ("max_workspace_bytes", _i64),
     ]
 
 

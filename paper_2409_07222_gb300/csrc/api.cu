@@ -252,6 +252,20 @@ int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t
   return labsg::launch_legendre(ctx, L, params, n, seqs, E_out, (cudaStream_t)stream);
 }
 
+int labs_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint64_t* seeds, int n, uint64_t* best_seqs,
+                        int32_t* best_E, labs_pq_stats* stats, void* stream) {
+  if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->T_r < 0 || cfg->T_r > 64 || 2 * cfg->T_r >= cfg->L ||
+      cfg->H_log2 < 10 || cfg->H_log2 > 30 || cfg->max_expansions < 1 || cfg->max_expansions >= (1ll << 21) ||
+      cfg->max_workspace_bytes < 0 || n < 0)
+    return LABS_ERR_INVALID_ARG;
+  if (n > 0 && (!seeds || !aligned8(seeds) || !best_seqs || !aligned8(best_seqs) || !best_E || !aligned4(best_E) ||
+                !stats || !aligned8(stats)))
+    return LABS_ERR_INVALID_ARG;
+  int s = set_device(ctx);
+  if (s != LABS_OK) return s;
+  return labsg::launch_pq_independent(ctx, cfg, seeds, n, best_seqs, best_E, stats, (cudaStream_t)stream);
+}
+
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
   if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;

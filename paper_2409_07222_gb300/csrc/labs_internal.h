@@ -34,7 +34,8 @@ enum WsSlot {
   kWsBatchThresholds = 3,
   kWsPq0 = 4,
   kWsChunkState = 5,
-  kWsChunkIo = 6
+  kWsChunkIo = 6,
+  kWsPqIndep = 7
 };
 
 // Returns a device region of at least `bytes` for `slot`, growing it if needed (not capturable).
@@ -66,6 +67,8 @@ int launch_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_
 int legendre_family(int L, double r_lo, double r_hi, double t_max, int32_t* out, int64_t max_out, int64_t* n_out);
 int launch_legendre(labs_ctx* ctx, int L, const int32_t* params, int64_t n, uint64_t* seqs, int32_t* E_out,
                     cudaStream_t st);
+int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint64_t* seeds, int n,
+                          uint64_t* best_seqs, int32_t* best_E, labs_pq_stats* stats, cudaStream_t st);
 int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                      int32_t* best_E, labs_pq_stats* stats, cudaStream_t st);
 int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,

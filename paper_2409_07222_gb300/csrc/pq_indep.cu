@@ -1,0 +1,473 @@
+// pq_indep.cu -- step 2 with one independent priority queue per candidate (labs_pq_independent): the
+// paper's own parallelisation of Algorithm 2 (every candidate refined on its own, Section 3), with the
+// queue unbounded as in the listing (nothing is evicted) and B = 1 pops per step.
+//
+// GB300 mapping.  One warp per candidate; a candidate's state lives in HBM:
+//   arena  -- every pushed node as a 16-byte record (E, link, fp); the survivors of one pop are appended
+//             as one run sorted by (E, fp, column), so the arena is a set of sorted runs;
+//   runs   -- a binary heap over the runs' current heads keyed by (E, fp): its top is the queue minimum,
+//             a pop advances that run's head (one sift-down), a new run is one sift-up;
+//   pivots -- the sequence of every popped node (a node is stored as its pivot and column, and is made
+//             into a sequence only when popped);
+//   H      -- the candidate's visited set (open addressing, cleared per candidate).
+// A pop scans all L single flips (the dp4a tiles of labs_core.cuh) and, with T_r > 0, the pivot's 2 T_r
+// rotations; survivors are sorted in shared memory (bitonic, one warp) and pushed as one run.  Memory per
+// resident warp is about max_expansions x (L + 2 T_r) x 16 B + 2^H_log2 x 8 B: HBM capacity, not
+// bandwidth, is what this design spends.
+#include <algorithm>
+
+#include "labs_core.cuh"
+#include "labs_internal.h"
+
+namespace labsg {
+namespace {
+
+constexpr int kIWarps = 4;
+constexpr int kIM = 8;
+constexpr int kSortN = 1024;  // survivors of one pop, padded: L + 2 T_r <= 576 + 128
+constexpr uint64_t kEmpty = ~0ull;
+constexpr int kProbeLimit = 1 << 20;
+
+struct Node {  // one queue record: 16 bytes
+  int32_t E;
+  int32_t link;  // pivot * 1024 + column (column < L: flip, else rotation column - L); -1: the seed
+  uint64_t fp;
+};
+
+struct RunHead {  // heap element: the run's current head key and its remaining range in the arena
+  int32_t E;
+  int32_t cur;
+  uint64_t fp;
+  int32_t end;
+  int32_t pad;
+};
+
+struct IndepArgs {
+  int L, W, Tr, width, H_log2;
+  long long max_exp, T_u;
+  long long arena_cap, heap_cap;
+  long long n;
+  const uint64_t* seeds;
+  uint64_t* best_seqs;
+  int32_t* best_E;
+  labs_pq_stats* stats;
+  // per-slot workspaces (slot = resident warp)
+  Node* arena;
+  RunHead* heap;
+  uint64_t* pivots;
+  uint64_t* H;
+  const uint64_t* ztab;
+  unsigned long long* counter;
+};
+
+__device__ __forceinline__ bool kless(int Ea, uint64_t fa, int Eb, uint64_t fb) {
+  return Ea < Eb || (Ea == Eb && fa < fb);
+}
+
+// Visited set of one slot; *err set on an exhausted probe sequence.
+__device__ __forceinline__ bool hs_contains(const uint64_t* H, int log2, uint64_t fp, bool has_empty, int* err) {
+  if (fp == kEmpty) return has_empty;
+  const uint64_t mask = (1ull << log2) - 1;
+  uint64_t s = (fp * kGamma) >> (64 - log2);
+  for (int it = 0; it < kProbeLimit; it++) {
+    const uint64_t v = H[s];
+    if (v == fp) return true;
+    if (v == kEmpty) return false;
+    s = (s + 1) & mask;
+  }
+  *err = 1;
+  return true;
+}
+__device__ __forceinline__ void hs_insert(uint64_t* H, int log2, uint64_t fp, int* err) {
+  const uint64_t mask = (1ull << log2) - 1;
+  uint64_t s = (fp * kGamma) >> (64 - log2);
+  for (int it = 0; it < kProbeLimit; it++) {
+    const unsigned long long old =
+        atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
+    if (old == kEmpty || old == fp) return;
+    s = (s + 1) & mask;
+  }
+  *err = 1;
+}
+
+// Left shift of rotation code c: c < Tr moves the first c + 1 elements to the end, c >= Tr the last
+// c - Tr + 1 to the start.
+__device__ __forceinline__ int rshift(int L, int Tr, int c) {
+  const int r = c < Tr ? c + 1 : L - ((c - Tr + 1) % L);
+  return r % L;
+}
+
+// bits (32-bit words in shared memory) of src with position col + 1 flipped.
+__device__ __forceinline__ void flip_bits(const uint32_t* src, int col, uint32_t* dst) {
+  const int lane = lane_id();
+  if (lane < kBitWords) dst[lane] = src[lane] ^ (lane == (col >> 5) ? 1u << (col & 31) : 0u);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void rotate_bits(const uint32_t* src, int L, int r, uint32_t* dst) {
+  const int lane = lane_id();
+  for (int w = 0; w < kBitWords; w++) {
+    const int i = 32 * w + lane;
+    int bit = 0;
+    if (i < L) {
+      int j = i + r;
+      if (j >= L) j -= L;
+      bit = (src[j >> 5] >> (j & 31)) & 1u;
+    }
+    const unsigned word = __ballot_sync(kFull, bit);
+    if (lane == 0) dst[w] = word;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void words_to_bits(const uint64_t* src, int L, uint32_t* dst) {
+  const int lane = lane_id();
+  if (lane < kBitWords) {
+    const int W32 = (L + 31) >> 5;
+    uint32_t v = 0;
+    if (lane < W32) {
+      const uint64_t x = src[lane >> 1];
+      v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+      const int rem = L - 32 * lane;
+      if (rem < 32) v &= (1u << rem) - 1u;
+    }
+    dst[lane] = v;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void bits_to_words(const uint32_t* src, int L, uint64_t* dst) {
+  const int lane = lane_id();
+  if (lane < ((L + 63) >> 6)) dst[lane] = (uint64_t)src[2 * lane] | ((uint64_t)src[2 * lane + 1] << 32);
+}
+
+__device__ __forceinline__ int energy_bits(const uint32_t* bits, int L) {
+  int e = 0;
+  for (int k = lane_id() + 1; k < L; k += 32) {
+    const int c = corr_lag(bits, L, k);
+    e += c * c;
+  }
+  return warp_sum_i32(e);
+}
+
+__device__ __forceinline__ uint64_t fp_bits(const uint32_t* bits, int L, const uint64_t* ztab) {
+  uint64_t h = 0;
+  for (int i = lane_id(); i < L; i += 32)
+    if (!((bits[i >> 5] >> (i & 31)) & 1u)) h ^= ztab[i];
+  return warp_xor_u64(h);
+}
+
+struct SortKey {  // survivor: (E, fp, column) orders the run; column < 2^16
+  int32_t E;
+  int32_t col;
+  uint64_t fp;
+};
+
+__device__ __forceinline__ bool sk_less(const SortKey& a, const SortKey& b) {
+  if (a.E != b.E) return a.E < b.E;
+  if (a.fp != b.fp) return a.fp < b.fp;
+  return a.col < b.col;
+}
+
+struct __align__(16) IndepSmem {
+  ScanSmem s;
+  uint32_t pbits[kBitWords];  // the pivot
+  uint32_t cbits[kBitWords];  // a child
+  SortKey keys[kSortN];
+  int n_surv;
+};
+
+__global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Layout ly) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  IndepSmem& S = reinterpret_cast<IndepSmem*>(smem_raw)[threadIdx.x >> 5];
+  ScanSmem& sm = S.s;
+  const int lane = lane_id();
+  const long long slot = (long long)blockIdx.x * kIWarps + (threadIdx.x >> 5);
+  Node* arena = a.arena + slot * a.arena_cap;
+  RunHead* heap = a.heap + slot * a.heap_cap;
+  uint64_t* pivots = a.pivots + slot * a.max_exp * a.W;
+  uint64_t* H = a.H + slot * (1ll << a.H_log2);
+  const long long hslots = 1ll << a.H_log2;
+
+  while (true) {
+    unsigned long long cand = 0;
+    if (lane == 0) cand = atomicAdd(a.counter, 1ull);
+    cand = __shfl_sync(kFull, cand, 0);
+    if ((long long)cand >= a.n) break;
+    int err = 0;
+    // ---- reset the visited set, seed the queue
+    for (long long t = lane; t < hslots; t += 32) H[t] = kEmpty;
+    __threadfence_block();
+    __syncwarp();
+    words_to_bits(a.seeds + cand * a.W, a.L, S.pbits);
+    int bestE = energy_bits(S.pbits, a.L);
+    uint64_t bestfp = fp_bits(S.pbits, a.L, a.ztab);
+    bool has_empty = bestfp == kEmpty;
+    if (lane == 0) {
+      if (!has_empty) hs_insert(H, a.H_log2, bestfp, &err);
+      arena[0] = Node{bestE, -1, bestfp};
+      heap[0] = RunHead{bestE, 0, bestfp, 1, 0};
+    }
+    bits_to_words(S.pbits, a.L, a.best_seqs + cand * a.W);
+    __syncwarp();
+    long long heap_n = 1, top = 1, exps = 0, u = 0, surv = 0, improvements = 0, h_size = 1;
+    int stop = 0;
+    while (true) {
+      if (exps >= a.max_exp) stop = 1;
+      else if (heap_n == 0) stop = 2;
+      else if (a.T_u > 0 && u >= a.T_u) stop = 3;
+      if (stop || err) break;
+      // ---- pop: the top run's head; advance the run, sift down (lane 0)
+      int pE = 0, plink = 0;
+      unsigned long long pfp = 0;
+      if (lane == 0) {
+        RunHead h = heap[0];
+        const Node nd = arena[h.cur];
+        pE = nd.E;
+        plink = nd.link;
+        pfp = nd.fp;
+        h.cur++;
+        if (h.cur < h.end) {
+          const Node nx = arena[h.cur];
+          h.E = nx.E;
+          h.fp = nx.fp;
+        } else {
+          heap_n--;
+          h = heap[heap_n];
+        }
+        if (heap_n > 0) {
+          long long i = 0;
+          while (true) {
+            const long long l = 2 * i + 1, r = l + 1;
+            if (l >= heap_n) break;
+            long long c = l;
+            if (r < heap_n && kless(heap[r].E, heap[r].fp, heap[l].E, heap[l].fp)) c = r;
+            if (!kless(heap[c].E, heap[c].fp, h.E, h.fp)) break;
+            heap[i] = heap[c];
+            i = c;
+          }
+          heap[i] = h;
+        }
+      }
+      heap_n = __shfl_sync(kFull, heap_n, 0);
+      pE = __shfl_sync(kFull, pE, 0);
+      plink = __shfl_sync(kFull, plink, 0);
+      pfp = __shfl_sync(kFull, pfp, 0);
+      // ---- the pivot's sequence: the seed, or the child `col` of an earlier pivot
+      if (plink < 0) {
+        words_to_bits(a.seeds + cand * a.W, a.L, S.pbits);
+      } else {
+        words_to_bits(pivots + (long long)(plink >> 10) * a.W, a.L, S.cbits);
+        const int col = plink & 1023;
+        if (col < a.L)
+          flip_bits(S.cbits, col, S.pbits);
+        else
+          rotate_bits(S.cbits, a.L, rshift(a.L, a.Tr, col - a.L), S.pbits);
+      }
+      bits_to_words(S.pbits, a.L, pivots + exps * a.W);
+      // ---- expand: every single flip (dp4a tiles), then the rotations
+      if (lane == 0) S.n_surv = 0;
+      for (int w = lane; w < kBitWords; w += 32) sm.bits[w] = S.pbits[w];
+      __syncwarp();
+      build_table(sm, ly);
+      const bool fast = pack_c8(sm);
+      const int SC = table_sum(sm);
+      build_bytes(sm, ly);
+      for (int base = 0; base < ly.n_tiles; base += 32) {
+        const int tau = base + lane;
+        if (tau < ly.n_tiles) {
+          int cls, q0;
+          tile_of(ly, tau, cls, q0);
+          int acc[kIM];
+          if (fast)
+            scan_tile<kIM, false>(sm, ly, cls, q0, acc);
+          else
+            scan_tile<kIM, true>(sm, ly, cls, q0, acc);
+#pragma unroll
+          for (int j = 0; j < kIM; j++) {
+            const SlotInfo si = slot_info(ly, cls, q0 + j);
+            if (!si.active) continue;
+            const int P = p_from_scratch(sm, ly, cls, q0 + j, si);
+            const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
+            const uint64_t nfp = pfp ^ a.ztab[si.m - 1];
+            if (!hs_contains(H, a.H_log2, nfp, has_empty, &err)) {
+              const int k = atomicAdd(&S.n_surv, 1);
+              S.keys[k] = SortKey{pE + d, si.m - 1, nfp};
+            }
+          }
+        }
+      }
+      __syncwarp();
+      for (int c = 0; c < 2 * a.Tr; c++) {
+        rotate_bits(S.pbits, a.L, rshift(a.L, a.Tr, c), S.cbits);
+        const int e = energy_bits(S.cbits, a.L);
+        const uint64_t h = fp_bits(S.cbits, a.L, a.ztab);
+        if (lane == 0 && !hs_contains(H, a.H_log2, h, has_empty, &err)) S.keys[S.n_surv++] = SortKey{e, a.L + c, h};
+        __syncwarp();
+      }
+      err = __reduce_or_sync(kFull, err);
+      const int ns = S.n_surv;
+      // ---- sort the survivors by (E, fp, column): bitonic over the next power of two
+      int np2 = 1;
+      while (np2 < ns) np2 <<= 1;
+      for (int i = ns + lane; i < np2; i += 32) S.keys[i] = SortKey{INT32_MAX, 0x7fffffff, kEmpty};
+      __syncwarp();
+      for (int k = 2; k <= np2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < np2; i += 32) {
+            const int l = i ^ j;
+            if (l > i) {
+              const SortKey x = S.keys[i], y = S.keys[l];
+              const bool up = (i & k) == 0;
+              if (up ? sk_less(y, x) : sk_less(x, y)) {
+                S.keys[i] = y;
+                S.keys[l] = x;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      // ---- distinct survivors (equal (E, fp): the same sequence) become one run; H receives them
+      int nu = 0;
+      for (int i0 = 0; i0 < ns; i0 += 32) {
+        const int i = i0 + lane;
+        bool keep = false;
+        SortKey x{};
+        if (i < ns) {
+          x = S.keys[i];
+          keep = i == 0 || S.keys[i - 1].E != x.E || S.keys[i - 1].fp != x.fp;
+        }
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int o = nu + __popc(m & ((1u << lane) - 1u));
+          arena[top + o] = Node{x.E, (int)(exps << 10) | x.col, x.fp};
+          if (x.fp == kEmpty)
+            has_empty = true;
+          else
+            hs_insert(H, a.H_log2, x.fp, &err);
+        }
+        nu += __popc(m);
+      }
+      has_empty = __any_sync(kFull, has_empty);
+      err = __reduce_or_sync(kFull, err);
+      __syncwarp();
+      // ---- best, statistics, the new run
+      if (nu > 0 && S.keys[0].E < bestE) {
+        bestE = S.keys[0].E;
+        bestfp = S.keys[0].fp;
+        const int col = S.keys[0].col;
+        if (col < a.L)
+          flip_bits(S.pbits, col, S.cbits);
+        else
+          rotate_bits(S.pbits, a.L, rshift(a.L, a.Tr, col - a.L), S.cbits);
+        bits_to_words(S.cbits, a.L, a.best_seqs + cand * a.W);
+        improvements++;
+        u = 0;
+      } else {
+        u++;
+      }
+      if (nu > 0 && lane == 0) {  // push the run: sift up
+        RunHead h{S.keys[0].E, (int)top, S.keys[0].fp, (int)(top + nu), 0};
+        long long i = heap_n;
+        while (i > 0) {
+          const long long p = (i - 1) >> 1;
+          if (!kless(h.E, h.fp, heap[p].E, heap[p].fp)) break;
+          heap[i] = heap[p];
+          i = p;
+        }
+        heap[i] = h;
+      }
+      if (nu > 0) heap_n++;
+      top += nu;
+      surv += nu;
+      h_size += nu;
+      exps++;
+      __syncwarp();
+      if (h_size * 4 > hslots * 3) err = 1;  // keep the visited set below 3/4 load
+    }
+    if (lane == 0) {
+      a.best_E[cand] = bestE;
+      labs_pq_stats st{};
+      st.expansions = exps;
+      st.rounds = exps;
+      st.survivors = surv;
+      st.admitted = surv;
+      st.evicted = 0;
+      st.h_size = h_size;
+      st.improvements = improvements;
+      st.best_fp = bestfp;
+      st.stop_reason = err ? 0 : stop;
+      st.status = err ? LABS_ERR_CAPACITY : LABS_OK;
+      a.stats[cand] = st;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void indep_ztab_kernel(uint64_t* ztab, int L) {
+  const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)L, 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) ztab[i] = zobrist(zk, i + 1);
+}
+
+}  // namespace
+
+int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint64_t* seeds, int n,
+                          uint64_t* best_seqs, int32_t* best_E, labs_pq_stats* stats, cudaStream_t st) {
+  if (n == 0) return LABS_OK;
+  const int L = cfg->L, W = (L + 63) / 64;
+  Layout ly;
+  if (!make_layout(ly, L, 0, 0, kIM)) return LABS_ERR_INVALID_ARG;
+  IndepArgs a{};
+  a.L = L;
+  a.W = W;
+  a.Tr = cfg->T_r;
+  a.width = L + 2 * cfg->T_r;
+  a.H_log2 = cfg->H_log2;
+  a.max_exp = cfg->max_expansions;
+  a.T_u = cfg->T_u;
+  a.arena_cap = 1 + a.max_exp * a.width;
+  a.heap_cap = a.max_exp + 1;
+  a.n = n;
+  a.seeds = seeds;
+  a.best_seqs = best_seqs;
+  a.best_E = best_E;
+  a.stats = stats;
+  // resident warps: as many slots as the memory budget allows, at most one per candidate
+  const size_t per_slot = (size_t)a.arena_cap * sizeof(Node) + (size_t)a.heap_cap * sizeof(RunHead) +
+                          (size_t)a.max_exp * W * 8 + (8ull << a.H_log2);
+  const size_t smem = sizeof(IndepSmem) * kIWarps;
+  if (cudaFuncSetAttribute(pq_indep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return LABS_ERR_CUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pq_indep_kernel, 32 * kIWarps, smem) != cudaSuccess ||
+      per_sm < 1)
+    return LABS_ERR_CUDA;
+  long long blocks = std::min<long long>((long long)per_sm * ctx->num_sms, ((long long)n + kIWarps - 1) / kIWarps);
+  const size_t budget = cfg->max_workspace_bytes > 0 ? (size_t)cfg->max_workspace_bytes : ((size_t)64 << 30);
+  blocks = std::min<long long>(blocks, (long long)(budget / (per_slot * kIWarps)));
+  if (blocks < 1) return LABS_ERR_NOMEM;
+  const size_t slots = (size_t)blocks * kIWarps;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t oA = take(slots * (size_t)a.arena_cap * sizeof(Node)), oHp = take(slots * (size_t)a.heap_cap * sizeof(RunHead));
+  const size_t oP = take(slots * (size_t)a.max_exp * W * 8), oH = take(slots * (8ull << a.H_log2));
+  const size_t oZ = take(8 * (size_t)L), oC = take(8);
+  char* base = static_cast<char*>(ws_get(ctx, kWsPqIndep, off));
+  if (!base) return LABS_ERR_NOMEM;
+  a.arena = reinterpret_cast<Node*>(base + oA);
+  a.heap = reinterpret_cast<RunHead*>(base + oHp);
+  a.pivots = reinterpret_cast<uint64_t*>(base + oP);
+  a.H = reinterpret_cast<uint64_t*>(base + oH);
+  a.ztab = reinterpret_cast<uint64_t*>(base + oZ);
+  a.counter = reinterpret_cast<unsigned long long*>(base + oC);
+  indep_ztab_kernel<<<(L + 255) / 256, 256, 0, st>>>(reinterpret_cast<uint64_t*>(base + oZ), L);
+  if (cudaMemsetAsync(a.counter, 0, 8, st) != cudaSuccess) return LABS_ERR_CUDA;
+  pq_indep_kernel<<<(unsigned)blocks, 32 * kIWarps, smem, st>>>(a, ly);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace labsg

@@ -55,6 +55,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.WalkCfg) == 104
     assert ctypes.sizeof(_lib.BatchCfg) == 72
     assert ctypes.sizeof(_lib.PqCfg) == 40
+    assert ctypes.sizeof(_lib.PqIndepCfg) == 40
     assert CANDIDATE_DTYPE.itemsize == 96 and WALK_STATS_DTYPE.itemsize == 48
 
 

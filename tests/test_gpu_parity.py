@@ -391,3 +391,39 @@ def test_legendre_bad_parameters_give_no_seed(lg):
     assert list(E[:3]) == [2**31 - 1] * 3
     _, oE = oracle.legendre_construct(13, [(11, 3)])
     assert E[3] == oE[0]
+
+
+# ------------------------------------------------------------------------------------------------
+# Independent queues per candidate (NEXT-2)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L,n,max_exp,T_u,T_r", [(13, 3, 60, 0, 0), (13, 5, 300, 25, 0), (31, 7, 200, 0, 3),
+                                                 (64, 4, 150, 30, 0), (101, 6, 120, 0, 2), (451, 9, 40, 0, 0),
+                                                 (527, 3, 25, 10, 4)])
+def test_pq_independent_equals_single_seed_refinement(lg, L, n, max_exp, T_u, T_r):
+    """Each candidate's result and statistics equal the oracle's Algorithm 2 from that seed alone, B = 1,
+    a cap never reached."""
+    seeds = inp.random_words(n, L, seed=2 * L + n)
+    best, bE, st = lg.labs_pq_independent(L, dev_words(seeds), max_expansions=max_exp, T_u=T_u, T_r=T_r, H_log2=18)
+    torch.cuda.synchronize()
+    best = host_words(best.cpu()).reshape(n, -1)
+    bE = bE.cpu().numpy()
+    stn = st.cpu().numpy().view(lg.PQ_STATS_DTYPE).reshape(n)
+    for q in range(n):
+        ob, oE, ofp, ost = oracle.pq_refine(L, seeds[q:q + 1], 1 << 30, 1, max_exp, T_u, T_r)
+        assert bE[q] == oE and np.array_equal(best[q], ob), q
+        assert int(stn[q]["best_fp"]) == ofp
+        for k in ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements", "stop_reason"):
+            assert int(stn[q][k]) == ost[k], (q, k, int(stn[q][k]), ost[k])
+        assert int(stn[q]["status"]) == 0
+
+
+def test_pq_independent_more_candidates_than_warps(lg):
+    """A workspace budget that admits only a few resident warps: every candidate still gets its own search."""
+    L, n = 21, 40
+    seeds = inp.random_words(n, L, seed=3)
+    best, bE, st = lg.labs_pq_independent(L, dev_words(seeds), max_expansions=50, H_log2=14,
+                                          max_workspace_bytes=4 * 400_000)
+    bE = bE.cpu().numpy()
+    for q in (0, 17, 39):
+        _, oE, _, _ = oracle.pq_refine(L, seeds[q:q + 1], 1 << 30, 1, 50)
+        assert bE[q] == oE
