@@ -312,6 +312,27 @@ def run_pq(args, ws, rank, local):
     return 0
 
 
+def reduce_over_ranks(total_ms, units, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time (MAX) and the units all ranks
+    processed (SUM).  Works on any initialised process group (NCCL on GPUs, gloo on CPUs); identity when
+    torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), int(units)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([int(units)], dtype=torch.int64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
+def shard(rank, n_per_rank):
+    """Walk ids of a rank: [rank * n, (rank + 1) * n); ranks share no walk and need no data exchange."""
+    return rank * n_per_rank, n_per_rank
+
+
 def peaks():
     """Measured peaks of this GPU pool (HBM copy GB/s, dense BF16 TFLOP/s burst and sustained) if the file
     is present, else {} (the caller then uses the fallback figure and says so)."""
@@ -600,7 +621,7 @@ def main():
         thr.copy_(thr_t)  # torch copy outside the library: stays out of the walk-kernel window below
         cfg = lg.make_walk_cfg(L, skew=True, p=p, n_walks=n_walks, flip_budget=budget, T_i=W1["T_i"],
                                seed=W1["seed"], R=R, bloom_log2=W1["bloom_log2"], bloom_k=W1["bloom_k"],
-                               walk_begin=rank * n_walks, E_thr_dev=thr)
+                               walk_begin=shard(rank, n_walks)[0], E_thr_dev=thr)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -637,14 +658,7 @@ def main():
     barrier()
     clk = clocks.stop()
 
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        f = torch.tensor([flips_seen], dtype=torch.int64, device=dev)
-        torch.distributed.all_reduce(f)
-        flips_seen = int(f.item())
+    total_ms, flips_seen = reduce_over_ranks(sum(step_ms), flips_seen, dev)
     expected = args.steps * n_walks * budget * ws
     if flips_seen != expected:
         raise RuntimeError("walks made %d flips, expected %d" % (flips_seen, expected))
@@ -657,18 +671,14 @@ def main():
         cfg = lg.make_walk_cfg(L, skew=True, p=p, n_walks=n_walks, flip_budget=budget, T_i=W1["T_i"],
                                seed=W1["seed"], R=R, bloom_log2=W1["bloom_log2"], bloom_k=W1["bloom_k"],
                                E_thr=lg.LABS_AUTO_THRESHOLD, n_thresh_samples=W1["n_thresh_samples"],
-                               thresh_rank=W1["thresh_rank"], walk_begin=rank * n_walks)
+                               thresh_rank=W1["thresh_rank"], walk_begin=shard(rank, n_walks)[0])
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             out_h, st_h = lg.labs_skew_search_host(cfg, pre_h, device=local)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        tot = sum(e2e_ms)
-        if ws > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
+        tot, _ = reduce_over_ranks(sum(e2e_ms), 0, dev)
         e2e = {"value": args.steps * n_walks * budget * ws / (tot * 1e-3), "unit": METRIC,
                "h2d_bytes_per_step": int(pre_h.nbytes),
                "d2h_bytes_per_step": int(n_walks * R * 96 + 48)}
