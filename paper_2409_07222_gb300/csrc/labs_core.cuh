@@ -244,6 +244,44 @@ __device__ __forceinline__ int corr_lag(const uint32_t* bits, int L, int k) {
   return n - 2 * dis;
 }
 
+// sum_{i=0}^{n-1} a_i b_{i+d} for two sequences given by their bits (n = L - d products, d >= 0):
+// n - 2 popc((a XOR (b >> d)) restricted to the low n bits).
+__device__ __forceinline__ int corr_pair(const uint32_t* a, const uint32_t* b, int L, int d) {
+  const int n = L - d;
+  const int ws = d >> 5, sh = d & 31;
+  const int nw = (n + 31) >> 5;
+  int dis = 0;
+  for (int w = 0; w < nw; w++) {
+    uint32_t x = a[w] ^ __funnelshift_r(b[w + ws], b[w + ws + 1], sh);
+    const int rem = n - 32 * w;
+    if (rem < 32) x &= (1u << rem) - 1u;
+    dis += __popc(x);
+  }
+  return n - 2 * dis;
+}
+
+// P_m = sum_{g >= 1} s_{m-g} s_{m+g} for every position of an unrestricted sequence (both ends valid),
+// into P_out[m - 1] (int16, m = 1..L).  The self-convolution (s * s)[k] = sum_j s_j s_{k-j} counts each
+// product of P_m twice plus s_m^2, so P_m = ((s * s)[2(m-1)] - 1) / 2; and (s * s)[k] is the correlation of
+// s with its reversal r (r_j = s_{L-1-j}) at offset L-1-k, one popcount per 32 products.  rbits: per-warp
+// scratch of kBitWords words for r.
+__device__ inline void p_all_unrestricted(const ScanSmem& sm, int L, uint32_t* rbits, int16_t* P_out) {
+  const int lane = lane_id();
+  for (int w = 0; w < kBitWords; w++) {
+    const int j = 32 * w + lane;
+    const int bit = j < L ? (int)((sm.bits[(L - 1 - j) >> 5] >> ((L - 1 - j) & 31)) & 1u) : 0;
+    const unsigned word = __ballot_sync(kFull, bit);
+    if (lane == 0) rbits[w] = word;
+  }
+  __syncwarp();
+  for (int i = lane; i < L; i += 32) {
+    const int d = L - 1 - 2 * i;
+    const int conv = d >= 0 ? corr_pair(sm.bits, rbits, L, d) : corr_pair(rbits, sm.bits, L, -d);
+    P_out[i] = (int16_t)((conv - 1) / 2);
+  }
+  __syncwarp();
+}
+
 // C_{lambda g} for g = 1..G; lanes split the lags.  Writes C16 (zero-padded to kCLen) and returns E on
 // every lane (sum over the tracked lags; for skew inputs the untracked odd lags are zero).
 __device__ inline int build_table(ScanSmem& sm, const Layout& ly) {

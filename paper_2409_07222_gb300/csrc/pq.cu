@@ -233,8 +233,10 @@ __global__ void pq_round_begin_kernel(PqBufs b) {
 __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layout ly) {
   __shared__ ScanSmem slabs[kPqWarps];
   __shared__ uint32_t rbits_all[kPqWarps][kBitWords];
+  __shared__ int16_t P_all[kPqWarps][kMaxL];
   ScanSmem& sm = slabs[threadIdx.x >> 5];
   uint32_t* rbits = rbits_all[threadIdx.x >> 5];
+  int16_t* Pm = P_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const PqState* st = b.st;
   const int nb = st->b;
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
     const bool fast = pack_c8(sm);
     const int SC = table_sum(sm);
     build_bytes(sm, ly);
+    p_all_unrestricted(sm, b.L, rbits, Pm);
     const int E = PE[q];
     const uint64_t fp = Pfp[q];
     for (int base = 0; base < ly.n_tiles; base += 32) {
@@ -264,8 +267,7 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
         for (int j = 0; j < kPqM; j++) {
           const SlotInfo si = slot_info(ly, cls, q0 + j);
           if (!si.active) continue;
-          const int P = p_from_scratch(sm, ly, cls, q0 + j, si);
-          const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
+          const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, Pm[si.m - 1]);
           const uint64_t nfp = fp ^ b.ztab[si.m - 1];
           const size_t di = (size_t)q * b.width + (si.m - 1);
           b.dE[di] = h_contains(b, nfp) ? INT32_MAX : E + d;

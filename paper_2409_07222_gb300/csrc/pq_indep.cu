@@ -174,6 +174,7 @@ struct __align__(16) IndepSmem {
   uint32_t pbits[kBitWords];  // the pivot
   uint32_t cbits[kBitWords];  // a child
   SortKey keys[kSortN];
+  int16_t P[kMaxL];  // P_m of the pivot's neighbours
   int n_surv;
 };
 
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       const bool fast = pack_c8(sm);
       const int SC = table_sum(sm);
       build_bytes(sm, ly);
+      p_all_unrestricted(sm, a.L, S.cbits, S.P);
       for (int base = 0; base < ly.n_tiles; base += 32) {
         const int tau = base + lane;
         if (tau < ly.n_tiles) {
@@ -287,8 +289,7 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
           for (int j = 0; j < kIM; j++) {
             const SlotInfo si = slot_info(ly, cls, q0 + j);
             if (!si.active) continue;
-            const int P = p_from_scratch(sm, ly, cls, q0 + j, si);
-            const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
+            const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, S.P[si.m - 1]);
             const uint64_t nfp = pfp ^ a.ztab[si.m - 1];
             if (!hs_contains(H, a.H_log2, nfp, has_empty, &err)) {
               const int k = atomicAdd(&S.n_surv, 1);
