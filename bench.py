@@ -48,11 +48,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
-    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre"],
+    ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre",
+                             "exhaustive"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
                          "network: the proposal network's inference alone; operators: the end-element operators; "
-                         "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate")
+                         "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate; exhaustive: all skew sequences of L = 37 and 61")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -421,6 +422,49 @@ def run_operators(args, ws, rank, local):
     return 0
 
 
+def run_exhaustive(args, ws, rank, local):
+    """Exhaustive skew enumeration: every skew-symmetric sequence of L = 37 (2^19 assignments, the small
+    configuration) and of L = 61 (2^31), minimum energy, optimum count and argmin, as assignments per
+    second.  Each assignment is evaluated from scratch in two 64-bit words in both of the kernel's passes:
+    two 64-bit popcounts (counted as four 32-bit ones) per even lag."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    lg.load()
+    res, t_tot, popc_tot, n_tot = [], 0.0, 0, 0
+    for L in (inp.EXHAUSTIVE_37["L"], 61):
+        k = (L - 1) // 2
+        lg.labs_skew_exhaustive(L)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        minE, cnt, arg, _ = lg.labs_skew_exhaustive(L)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        n = 1 << (k + 1)
+        t_tot += t
+        n_tot += n
+        popc_tot += 2 * n * 4 * ((L - 1) // 2)  # two passes, four 32-bit popcounts per even lag
+        res.append({"L": L, "assignments": n, "seconds": t, "min_E": int(minE.cpu()[0]), "count": int(cnt.cpu()[0]),
+                    "argmin_free_bits": int(arg.cpu()[0]), "F": round(L * L / (2.0 * int(minE.cpu()[0])), 4)})
+    peak = SMS * 16 * SM_MAX_MHZ * 1e6 / 1e9
+    ach = popc_tot / t_tot / 1e9
+    line = {"metric": "assignments/s", "value": n_tot / t_tot, "unit": "assignments/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": t_tot * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "exhaustive_skew_L37_L61", "lengths": [r["L"] for r in res]},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpopc/s", "frac": ach / peak,
+                         "traffic": None, "kernel": "exh_min_kernel + exh_count_kernel",
+                         "work": "2 passes x (L-1)/2 even lags x 4 popcounts per assignment; "
+                                 "peak = 152 SMs x 16 POPC/clk x 2070 MHz"},
+            "per_length": res}
+    print(json.dumps(line))
+    return 0
+
+
 def run_pq_indep(args, ws, rank, local):
     """Step 2 with one queue per candidate: the 4,096 best distinct states of a step-1 search at L (as in
     the pq workload) each refined alone, B = 1, unbounded queue, --pq-indep-pops pops each."""
@@ -586,6 +630,8 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "exhaustive":
+        return run_exhaustive(args, ws, rank, local)
     if args.workload == "pq_indep":
         return run_pq_indep(args, ws, rank, local)
     if args.workload == "legendre":
