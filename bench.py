@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
     ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre",
-                             "exhaustive"],
+                             "exhaustive", "energy", "deltas"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
                          "network: the proposal network's inference alone; operators: the end-element operators; "
-                         "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate; exhaustive: all skew sequences of L = 37 and 61")
+                         "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate; exhaustive: all skew sequences of L = 37 and 61; energy / deltas: the energy batch and the "
+                         "neighbour scan entry points alone")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -422,6 +423,77 @@ def run_operators(args, ws, rank, local):
     return 0
 
 
+def _time_calls(fn, reps=10, warm=3):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps * 1e-3
+
+
+def run_energy(args, ws, rank, local):
+    """labs_energy_batch on 2^22 random sequences of L = 451 (the sieve sample's shape, 4x larger): all
+    C_k and E; one popcount per 32 products of each lag, 268 MB of sequences read per call."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    lg.load()
+    L, n = W1["L"], 1 << 22
+    w = torch.from_numpy(inp.random_words(n, L, seed=21).view(np.int64)).to(torch.device("cuda", local))
+    t = _time_calls(lambda: lg.labs_energy_batch(w, L))
+    popc = n * sum(-(-(L - k) // 32) for k in range(1, L))
+    peak = SMS * 16 * SM_MAX_MHZ * 1e6 / 1e9
+    line = {"metric": "energies/s", "value": n / t, "unit": "energies/s", "n_gpus": 1, "steps": 10, "warmup": 3,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": "energy_batch_L451_2^22seq", "L": L, "n": n},
+            "roofline": {"bound": "alu", "achieved": popc / t / 1e9, "peak": peak, "unit": "Gpopc/s",
+                         "frac": popc / t / 1e9 / peak, "traffic": None, "kernel": "energy_batch_kernel",
+                         "work": "sum_k ceil((L-k)/32) popcounts per sequence; input %.0f MB per call, "
+                                 "%.2f TB/s" % (n * 64 / 1e6, n * 64 / t / 1e12)}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_deltas(args, ws, rank, local):
+    """labs_flip_deltas on 2^16 skew-symmetric sequences of L = 451 with p = 24: Delta E of every free
+    neighbour (202 pair flips x 225 even lags per sequence), tables built in the call."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+
+    torch.cuda.set_device(local)
+    lg.load()
+    L, p, n = W1["L"], W1["p"], 1 << 16
+    pre = torch.from_numpy(inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"]).view(np.int64)).to(
+        torch.device("cuda", local))
+    cfg = lg.make_walk_cfg(L, skew=True, p=p, n_walks=n, flip_budget=1, seed=5, R=1, E_thr=lg.INT32_MAX)
+    out, _, _ = lg.labs_skew_search(cfg, pre, with_walk_stats=False)  # skew sequences one flip from a start
+    cand = lg.candidates_numpy(out, n, 1).reshape(-1)
+    W = (L + 63) // 64
+    seqs = torch.from_numpy(np.ascontiguousarray(cand["seq"][:, :W]).view(np.int64)).to(torch.device("cuda", local))
+    t = _time_calls(lambda: lg.labs_flip_deltas(seqs, L, skew=True, p=p))
+    terms = n * terms_per_flip(L, p)
+    peak = SMS * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    line = {"metric": "neighbour evaluations/s", "value": n * 202 / t, "unit": "evaluations/s", "n_gpus": 1,
+            "steps": 10, "warmup": 3, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "flip_deltas_skew_L451_p24_2^16seq", "L": L, "p": p, "n": n},
+            "roofline": {"bound": "alu", "achieved": terms / t / 1e9, "peak": peak, "unit": "Gop/s",
+                         "frac": terms / t / 1e9 / peak, "traffic": None, "kernel": "flip_deltas_kernel",
+                         "work": "45450 neighbour-lag multiply-adds per sequence (as the walk's step)"}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_exhaustive(args, ws, rank, local):
     """Exhaustive skew enumeration: every skew-symmetric sequence of L = 37 (2^19 assignments, the small
     configuration) and of L = 61 (2^31), minimum energy, optimum count and argmin, as assignments per
@@ -630,6 +702,10 @@ def main():
         return run_mixed(args, ws, rank, local)
     if args.workload == "pq":
         return run_pq(args, ws, rank, local)
+    if args.workload == "energy":
+        return run_energy(args, ws, rank, local)
+    if args.workload == "deltas":
+        return run_deltas(args, ws, rank, local)
     if args.workload == "exhaustive":
         return run_exhaustive(args, ws, rank, local)
     if args.workload == "pq_indep":

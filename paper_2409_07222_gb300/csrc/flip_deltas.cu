@@ -18,7 +18,10 @@ __global__ void __launch_bounds__(32 * kFdWarps) flip_deltas_kernel(const uint64
                                                                      const int32_t* __restrict__ Cin, int L, int64_t n,
                                                                      int skew, int p, int32_t* __restrict__ dE) {
   __shared__ ScanSmem slabs[kFdWarps];
+  __shared__ int16_t P_all[kFdWarps][kMaxL];
+  __shared__ uint32_t xb_all[kFdWarps][kBitWords], rb_all[kFdWarps][kBitWords];
   ScanSmem& sm = slabs[threadIdx.x >> 5];
+  int16_t* Pm = P_all[threadIdx.x >> 5];
   const int lane = lane_id();
   Layout ly;
   make_layout(ly, L, skew, p, M);  // validated by the host launcher
@@ -38,6 +41,7 @@ __global__ void __launch_bounds__(32 * kFdWarps) flip_deltas_kernel(const uint64
     const bool fast = pack_c8(sm);
     const int SC = table_sum(sm);
     build_bytes(sm, ly);
+    p_all(sm, ly, xb_all[threadIdx.x >> 5], rb_all[threadIdx.x >> 5], Pm);
     int32_t* out = dE + q * L;
     for (int i = lane; i < L; i += 32) out[i] = INT32_MAX;
     __syncwarp();
@@ -56,8 +60,7 @@ __global__ void __launch_bounds__(32 * kFdWarps) flip_deltas_kernel(const uint64
         for (int j = 0; j < M; j++) {
           SlotInfo si = slot_info(ly, cls, q0 + j);
           if (!si.active) continue;
-          int P = p_from_scratch(sm, ly, cls, q0 + j, si);
-          out[si.m - 1] = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, P);
+          out[si.m - 1] = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, Pm[si.m - 1]);
         }
       }
     }

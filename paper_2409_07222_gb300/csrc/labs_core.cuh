@@ -260,26 +260,49 @@ __device__ __forceinline__ int corr_pair(const uint32_t* a, const uint32_t* b, i
   return n - 2 * dis;
 }
 
-// P_m = sum_{g >= 1} s_{m-g} s_{m+g} for every position of an unrestricted sequence (both ends valid),
-// into P_out[m - 1] (int16, m = 1..L).  The self-convolution (s * s)[k] = sum_j s_j s_{k-j} counts each
-// product of P_m twice plus s_m^2, so P_m = ((s * s)[2(m-1)] - 1) / 2; and (s * s)[k] is the correlation of
-// s with its reversal r (r_j = s_{L-1-j}) at offset L-1-k, one popcount per 32 products.  rbits: per-warp
-// scratch of kBitWords words for r.
-__device__ inline void p_all_unrestricted(const ScanSmem& sm, int L, uint32_t* rbits, int16_t* P_out) {
+// P_m = sum_{g} s_{m - lambda g} s_{m + lambda g} over the lags with both ends inside 1..L -- for a skew
+// layout without the pair's own lag gd = c - m -- for every position m, into P_out[m - 1] (int16).
+// Per position class (every position for lambda = 1, each parity for lambda = 2) the class sequence x
+// (x_j = s at class index j) has the self-convolution (x * x)[k] = sum_j x_j x_{k-j}, which counts each
+// product of P twice plus x_j^2: P = ((x * x)[2j] - 1) / 2.  (x * x)[k] is the correlation of x with its
+// reversal at offset n-1-k, one popcount per 32 products.  xb, rb: per-warp scratch of kBitWords words.
+__device__ inline void p_all(const ScanSmem& sm, const Layout& ly, uint32_t* xb, uint32_t* rb, int16_t* P_out) {
   const int lane = lane_id();
-  for (int w = 0; w < kBitWords; w++) {
-    const int j = 32 * w + lane;
-    const int bit = j < L ? (int)((sm.bits[(L - 1 - j) >> 5] >> ((L - 1 - j) & 31)) & 1u) : 0;
-    const unsigned word = __ballot_sync(kFull, bit);
-    if (lane == 0) rbits[w] = word;
+  for (int cls = 0; cls < ly.ncls; cls++) {
+    const int b = ly.skew ? (cls ? 1 : 2) : 1;  // first position of the class
+    const int n = ly.skew ? (b == 1 ? (ly.L + 1) / 2 : ly.L / 2) : ly.L;
+    for (int w = 0; w < kBitWords; w++) {  // x and its reversal
+      const int j = 32 * w + lane;
+      int bx = 0, br = 0;
+      if (j < n) {
+        const int i = ly.lam * j + b, ir = ly.lam * (n - 1 - j) + b;
+        bx = (int)((sm.bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1u);
+        br = (int)((sm.bits[(ir - 1) >> 5] >> ((ir - 1) & 31)) & 1u);
+      }
+      const unsigned wx = __ballot_sync(kFull, bx), wr = __ballot_sync(kFull, br);
+      if (lane == 0) {
+        xb[w] = wx;
+        rb[w] = wr;
+      }
+    }
+    __syncwarp();
+    for (int j = lane; j < n; j += 32) {
+      const int d = n - 1 - 2 * j;
+      const int conv = d >= 0 ? corr_pair(xb, rb, n, d) : corr_pair(rb, xb, n, -d);
+      int P = (conv - 1) / 2;
+      const int m = ly.lam * j + b;
+      if (ly.skew && m < ly.c) {  // the pair (m, m') is not a product of P_m
+        const int gd = ly.c - m;
+        if (j - gd >= 0 && j + gd < n) {
+          const int x0 = (int)((xb[(j - gd) >> 5] >> ((j - gd) & 31)) & 1u);
+          const int x1 = (int)((xb[(j + gd) >> 5] >> ((j + gd) & 31)) & 1u);
+          P -= (x0 == x1) ? 1 : -1;
+        }
+      }
+      P_out[m - 1] = (int16_t)P;
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  for (int i = lane; i < L; i += 32) {
-    const int d = L - 1 - 2 * i;
-    const int conv = d >= 0 ? corr_pair(sm.bits, rbits, L, d) : corr_pair(rbits, sm.bits, L, -d);
-    P_out[i] = (int16_t)((conv - 1) / 2);
-  }
-  __syncwarp();
 }
 
 // C_{lambda g} for g = 1..G; lanes split the lags.  Writes C16 (zero-padded to kCLen) and returns E on

@@ -234,9 +234,11 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
   __shared__ ScanSmem slabs[kPqWarps];
   __shared__ uint32_t rbits_all[kPqWarps][kBitWords];
   __shared__ int16_t P_all[kPqWarps][kMaxL];
+  __shared__ uint32_t xbits_all[kPqWarps][kBitWords];
   ScanSmem& sm = slabs[threadIdx.x >> 5];
   uint32_t* rbits = rbits_all[threadIdx.x >> 5];
   int16_t* Pm = P_all[threadIdx.x >> 5];
+  uint32_t* xbits = xbits_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const PqState* st = b.st;
   const int nb = st->b;
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
     const bool fast = pack_c8(sm);
     const int SC = table_sum(sm);
     build_bytes(sm, ly);
-    p_all_unrestricted(sm, b.L, rbits, Pm);
+    p_all(sm, ly, xbits, rbits, Pm);
     const int E = PE[q];
     const uint64_t fp = Pfp[q];
     for (int base = 0; base < ly.n_tiles; base += 32) {

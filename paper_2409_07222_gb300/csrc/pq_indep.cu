@@ -175,6 +175,7 @@ struct __align__(16) IndepSmem {
   uint32_t cbits[kBitWords];  // a child
   SortKey keys[kSortN];
   int16_t P[kMaxL];  // P_m of the pivot's neighbours
+  uint32_t xb[kBitWords];
   int n_surv;
 };
 
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       const bool fast = pack_c8(sm);
       const int SC = table_sum(sm);
       build_bytes(sm, ly);
-      p_all_unrestricted(sm, a.L, S.cbits, S.P);
+      p_all(sm, ly, S.xb, S.cbits, S.P);
       for (int base = 0; base < ly.n_tiles; base += 32) {
         const int tau = base + lane;
         if (tau < ly.n_tiles) {
