@@ -99,6 +99,10 @@ struct Layout {
   int NGh;    // groups of lag range 0 (range 1, when H = 2, is [NGh, NGend))
   int NGend;  // padded end of the groups (C = 0 beyond NG)
   int n_tasks;
+  // ceil(2^16 / tasks of the class): for 0 <= n <= 32, (n * fold_magic) >> 16 = n / tasks exactly (the
+  // error n * (magic * tasks - 2^16) stays below 32 * tasks < 2^16), so a lane splits a class's tasks
+  // without a divide
+  int fold_magic[2];
 };
 
 // word offset of class `cls` inside the fwd/bwd arrays (class 1 exists only for skew walks)
@@ -150,6 +154,10 @@ __host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, 
   }
   ly.Qr = qmax_end + ((2 - (qmax_end & 3)) & 3);
   ly.n_tasks = ly.n_tiles * H;
+  for (int cls = 0; cls < 2; cls++) {
+    const int nt = ly.ntiles[cls] * H;
+    ly.fold_magic[cls] = nt > 0 ? ((1 << 16) + nt - 1) / nt : 0;
+  }
   if (H == 1) {
     ly.NGh = ((ly.NG + ly.R - 1) / ly.R) * ly.R;
     ly.NGend = ly.NGh;
@@ -489,18 +497,19 @@ __device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bo
   int dsum = 0;
   bool ok = true;
   for (int u = lane_id(); u < ly.NG; u += 32) {
-    const uint32_t y4 = __funnelshift_r(Fw[wf + u], Fw[wf + u + 1], sf) + __funnelshift_r(Bw[wb + u], Bw[wb + u + 1], sb);
+    uint32_t y4 = __funnelshift_r(Fw[wf + u], Fw[wf + u + 1], sf) + __funnelshift_r(Bw[wb + u], Bw[wb + u + 1], sb);
+    // the pair's own product is not part of C: lag gd drops s_m' from its byte, which holds
+    // (s_m' + 1) + (the other end + 1 or a pad 1), so the byte stays in 0..4 and no borrow crosses bytes
+    const int eg = gd - 1 - 4 * u;
+    if ((unsigned)eg < 4u) y4 -= (uint32_t)s_mp << (8 * eg);
     const uint32_t lo = C16w[2 * u], hi = C16w[2 * u + 1];
     int c[4] = {(int)(int16_t)(lo & 0xffffu), (int)lo >> 16, (int)(int16_t)(hi & 0xffffu), (int)hi >> 16};
+    dsum += as * ((int)__dp4a(y4, 0x01010101u, 0u) - 8);  // sum of the four y
     uint32_t c8 = 0;
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-      int y = (int)((y4 >> (8 * e)) & 0xffu) - 2;
-      if (4 * u + e + 1 == gd) y -= s_mp;  // the pair's own product is not part of C
-      const int d = as * y;
-      c[e] += d;
-      dsum += d;
-      ok &= (c[e] >= -127 && c[e] <= 127);
+      c[e] += as * ((int)((y4 >> (8 * e)) & 0xffu) - 2);
+      ok &= (unsigned)(c[e] + 127) <= 254u;
       c8 |= ((uint32_t)c[e] & 0xffu) << (8 * e);
     }
     C16w[2 * u] = ((uint32_t)c[0] & 0xffffu) | ((uint32_t)c[1] << 16);

@@ -6,7 +6,9 @@
 //   expand   -- one warp per popped node: its correlation table, the all-position dp4a scan and a
 //               visited-set lookup per neighbour, written to a dense [pop][position] survivor array;
 //   compact  -- stable compaction of the survivors (pop order, position);
-//   sort     -- stable LSD radix sort by fingerprint bytes then energy bytes: order (E', fp', pop, pos);
+//   sort     -- stable LSD radix sort by the fingerprint's high 32 bits then the energy bytes (passes
+//               whose byte is the same in every key are skipped), then runs of equal (E', fp' >> 32)
+//               ordered by (fp', pop, pos) in place: order (E', fp', pop, pos);
 //   dedup    -- stable compaction keeping the first of equal (E', fp');
 //   best     -- strict improvement test on the smallest survivor;
 //   merge    -- merge path of (open set minus the pops) with the survivors into the other buffer, cut at
@@ -34,6 +36,9 @@ struct PqState {
   long long expansions, rounds, survivors, admitted, evicted, h_size, improvements, u;
   unsigned long long best_fp;
   int b, cur, stop, best_E, error, h_has_empty, pad0, pad1;
+  // OR and AND of the sort keys' 32-bit halves (fingerprint high half, energy) over this sort's input:
+  // a radix byte that is equal in every key orders nothing and its pass is skipped
+  unsigned fph_or, fph_and, e_or, e_and;
 };
 
 struct PqBufs {
@@ -324,24 +329,46 @@ __device__ __forceinline__ long long compact_n(const PqBufs& b) {
   return MODE == 0 ? b.st->n_dense : b.st->nS;
 }
 
+// Radix passes of the sort: 0..3 the bytes of fp >> 32, 4..7 the bytes of E (least significant first).
+// Bit p of the mask is set when pass p runs; pass p reads buffer popc(mask below p) & 1.
+__device__ __forceinline__ unsigned sort_mask(const PqState* st) {
+  const unsigned vf = st->fph_or ^ st->fph_and, ve = st->e_or ^ st->e_and;
+  unsigned m = 0;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    if ((vf >> (8 * p)) & 255u) m |= 1u << p;
+    if ((ve >> (8 * p)) & 255u) m |= 1u << (p + 4);
+  }
+  return m;
+}
+__device__ __forceinline__ int sort_src(unsigned mask, int pass) { return __popc(mask & ((1u << pass) - 1u)) & 1; }
+__device__ __forceinline__ int sort_final(const PqState* st) { return __popc(sort_mask(st)) & 1; }
+
 template <int MODE>
-__device__ __forceinline__ bool compact_flag(const PqBufs& b, long long e) {
+__device__ __forceinline__ bool compact_flag(const PqBufs& b, long long e, int fin) {
   if (MODE == 0) return b.dE[e] != INT32_MAX;
-  return e == 0 || b.sE[0][e] != b.sE[0][e - 1] || b.sfp[0][e] != b.sfp[0][e - 1];
+  return e == 0 || b.sE[fin][e] != b.sE[fin][e - 1] || b.sfp[fin][e] != b.sfp[fin][e - 1];
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(256) compact_count_kernel(PqBufs b) {
   const long long n = compact_n<MODE>(b);
   const long long base = (long long)blockIdx.x * kTile;
+  if (MODE == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // the sort that follows starts its key summary
+    b.st->fph_or = 0u;
+    b.st->fph_and = ~0u;
+    b.st->e_or = 0u;
+    b.st->e_and = ~0u;
+  }
   if (base >= n) {  // blocks past this round's count still publish a zero for the scan
     if (threadIdx.x == 0) b.bsum[blockIdx.x] = 0;
     return;
   }
+  const int fin = MODE == 1 ? sort_final(b.st) : 0;
   int c = 0;
   for (int r = 0; r < 4; r++) {
     const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
-    if (e < n && compact_flag<MODE>(b, e)) c++;
+    if (e < n && compact_flag<MODE>(b, e, fin)) c++;
   }
   c = __reduce_add_sync(kFull, c);
   __shared__ int ws[8];
@@ -388,11 +415,13 @@ __global__ void __launch_bounds__(256) compact_scatter_kernel(PqBufs b) {
   const long long base = (long long)blockIdx.x * kTile;
   if (base >= n) return;
   __shared__ int wcount[8][4];
+  __shared__ unsigned wkey[8][4];
   const int w = threadIdx.x >> 5, lane = lane_id();
+  const int fin = MODE == 1 ? sort_final(b.st) : 0;
   bool fl[4];
   for (int r = 0; r < 4; r++) {
     const long long e = base + w * 128 + r * 32 + lane;
-    fl[r] = e < n && compact_flag<MODE>(b, e);
+    fl[r] = e < n && compact_flag<MODE>(b, e, fin);
     const unsigned m = __ballot_sync(kFull, fl[r]);
     if (lane == 0) wcount[w][r] = __popc(m);
   }
@@ -410,30 +439,67 @@ __global__ void __launch_bounds__(256) compact_scatter_kernel(PqBufs b) {
         b.sfp[0][o] = b.dfp[e];
         b.sidx[0][o] = (int32_t)e;
       } else {
-        b.uE[o] = b.sE[0][e];
-        b.ufp[o] = b.sfp[0][e];
-        b.uidx[o] = b.sidx[0][e];
+        b.uE[o] = b.sE[fin][e];
+        b.ufp[o] = b.sfp[fin][e];
+        b.uidx[o] = b.sidx[fin][e];
       }
     }
     off += __popc(m);
   }
+  if (MODE == 0) {  // the block's share of the key summary
+    unsigned fo = 0u, fa = ~0u, eo = 0u, ea = ~0u;
+    for (int r = 0; r < 4; r++) {
+      const long long e = base + w * 128 + r * 32 + lane;
+      if (fl[r]) {
+        const unsigned fh = (unsigned)(b.dfp[e] >> 32), ev = (unsigned)b.dE[e];
+        fo |= fh;
+        fa &= fh;
+        eo |= ev;
+        ea &= ev;
+      }
+    }
+    fo = __reduce_or_sync(kFull, fo);
+    fa = __reduce_and_sync(kFull, fa);
+    eo = __reduce_or_sync(kFull, eo);
+    ea = __reduce_and_sync(kFull, ea);
+    if (lane == 0) {
+      wkey[w][0] = fo;
+      wkey[w][1] = fa;
+      wkey[w][2] = eo;
+      wkey[w][3] = ea;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int ww = 1; ww < 8; ww++) {
+        fo |= wkey[ww][0];
+        fa &= wkey[ww][1];
+        eo |= wkey[ww][2];
+        ea &= wkey[ww][3];
+      }
+      atomicOr(&b.st->fph_or, fo);
+      atomicAnd(&b.st->fph_and, fa);
+      atomicOr(&b.st->e_or, eo);
+      atomicAnd(&b.st->e_and, ea);
+    }
+  }
 }
 
-// Radix digit of element e of buffer `src` at pass `pass` (0..7: fingerprint bytes, 8..11: energy bytes).
+// Radix digit of element e of buffer `src` at pass `pass` (0..3: bytes of fp >> 32, 4..7: energy bytes).
 __device__ __forceinline__ unsigned radix_digit(const PqBufs& b, int src, long long e, int pass) {
-  if (pass < 8) return (unsigned)(b.sfp[src][e] >> (8 * pass)) & 255u;
-  return ((unsigned)b.sE[src][e] >> (8 * (pass - 8))) & 255u;
+  if (pass < 4) return (unsigned)(b.sfp[src][e] >> (32 + 8 * pass)) & 255u;
+  return ((unsigned)b.sE[src][e] >> (8 * (pass - 4))) & 255u;
 }
 
 __global__ void __launch_bounds__(256) radix_hist_kernel(PqBufs b, int pass) {
   const long long n = b.st->nS;
   const long long nblk = tiles_of(n);
   const long long base = (long long)blockIdx.x * kTile;
-  if (base >= n) return;
+  const unsigned mask = sort_mask(b.st);
+  if (base >= n || !((mask >> pass) & 1u)) return;
   __shared__ unsigned h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
-  const int src = pass & 1;
+  const int src = sort_src(mask, pass);
   for (int r = 0; r < 4; r++) {
     const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
     if (e < n) atomicAdd(&h[radix_digit(b, src, e, pass)], 1u);
@@ -448,7 +514,8 @@ constexpr int kSeg = 4096;
 
 __device__ __forceinline__ long long radix_count_len(const PqBufs& b) { return 256 * tiles_of(b.st->nS); }
 
-__global__ void __launch_bounds__(256) seg_reduce_kernel(PqBufs b) {
+__global__ void __launch_bounds__(256) seg_reduce_kernel(PqBufs b, int pass) {
+  if (!((sort_mask(b.st) >> pass) & 1u)) return;
   const long long n = radix_count_len(b);
   const long long lo = (long long)blockIdx.x * kSeg;
   unsigned s = 0;
@@ -465,7 +532,8 @@ __global__ void __launch_bounds__(256) seg_reduce_kernel(PqBufs b) {
   }
 }
 
-__global__ void __launch_bounds__(1024) seg_scan_sums_kernel(unsigned* a, int n) {
+__global__ void __launch_bounds__(1024) seg_scan_sums_kernel(unsigned* a, int n, const PqState* st, int pass) {
+  if (!((sort_mask(st) >> pass) & 1u)) return;
   __shared__ unsigned part[1024];
   const int t = threadIdx.x;
   const int chunk = (n + 1023) / 1024;
@@ -488,10 +556,10 @@ __global__ void __launch_bounds__(1024) seg_scan_sums_kernel(unsigned* a, int n)
   }
 }
 
-__global__ void __launch_bounds__(256) seg_down_kernel(PqBufs b) {
+__global__ void __launch_bounds__(256) seg_down_kernel(PqBufs b, int pass) {
   const long long n = radix_count_len(b);
   const long long lo = (long long)blockIdx.x * kSeg;
-  if (lo >= n) return;
+  if (lo >= n || !((sort_mask(b.st) >> pass) & 1u)) return;
   // thread t owns entries lo + 16t .. lo + 16t + 15
   const long long first = lo + 16 * threadIdx.x;
   unsigned v[16], s = 0;
@@ -525,10 +593,11 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) 
   const long long n = b.st->nS;
   const long long nblk = tiles_of(n);
   const long long base = (long long)blockIdx.x * kTile;
-  if (base >= n) return;
+  const unsigned mask = sort_mask(b.st);
+  if (base >= n || !((mask >> pass) & 1u)) return;
   __shared__ unsigned cnt[8][256];
   const int w = threadIdx.x >> 5, lane = lane_id();
-  const int src = pass & 1, dst = src ^ 1;
+  const int src = sort_src(mask, pass), dst = src ^ 1;
   for (int d = threadIdx.x; d < 8 * 256; d += 256) (&cnt[0][0])[d] = 0;
   __syncthreads();
   unsigned dig[4];
@@ -562,6 +631,37 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) 
     __syncwarp();
     if (dig[r] < 256u && lane == __ffs(peers) - 1) cnt[w][dig[r]] += __popc(peers);
     __syncwarp();
+  }
+}
+
+// After the radix passes the keys are ordered by (E, fp >> 32) and, within equal pairs, by input order
+// (pop, pos).  Each run of equal (E, fp >> 32) is put in (fp, pop, pos) order in place by the thread at
+// its start (runs are disjoint; they are short, fingerprints being uniform 64-bit keys).
+__global__ void __launch_bounds__(256) sort_fixup_kernel(PqBufs b) {
+  const long long n = b.st->nS;
+  const int f = sort_final(b.st);
+  int32_t* E = b.sE[f];
+  uint64_t* fp = b.sfp[f];
+  int32_t* ix = b.sidx[f];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < n; i += (long long)gridDim.x * blockDim.x) {
+    const int Ei = E[i];
+    const unsigned hi = (unsigned)(fp[i] >> 32);
+    if (E[i + 1] != Ei || (unsigned)(fp[i + 1] >> 32) != hi) continue;
+    if (i > 0 && E[i - 1] == Ei && (unsigned)(fp[i - 1] >> 32) == hi) continue;
+    long long j = i + 2;
+    while (j < n && E[j] == Ei && (unsigned)(fp[j] >> 32) == hi) j++;
+    for (long long a = i + 1; a < j; a++) {  // insertion sort of [i, j) by (fp, index)
+      const uint64_t kf = fp[a];
+      const int32_t ki = ix[a];
+      long long c = a;
+      while (c > i && (fp[c - 1] > kf || (fp[c - 1] == kf && ix[c - 1] > ki))) {
+        fp[c] = fp[c - 1];
+        ix[c] = ix[c - 1];
+        c--;
+      }
+      fp[c] = kf;
+      ix[c] = ki;
+    }
   }
 }
 
@@ -742,13 +842,14 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
     issue_compact<0>(b, max_n, &dst->nS, st);
     const int nseg = (int)((256ll * nb + kSeg - 1) / kSeg);
-    for (int pass = 0; pass < 12; pass++) {
+    for (int pass = 0; pass < 8; pass++) {
       radix_hist_kernel<<<nb, 256, 0, st>>>(b, pass);
-      seg_reduce_kernel<<<nseg, 256, 0, st>>>(b);
-      seg_scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nseg);
-      seg_down_kernel<<<nseg, 256, 0, st>>>(b);
+      seg_reduce_kernel<<<nseg, 256, 0, st>>>(b, pass);
+      seg_scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nseg, b.st, pass);
+      seg_down_kernel<<<nseg, 256, 0, st>>>(b, pass);
       radix_scatter_kernel<<<nb, 256, 0, st>>>(b, pass);
     }
+    sort_fixup_kernel<<<(unsigned)std::min<long long>((max_n + 255) / 256, (long long)ctx->num_sms * 8), 256, 0, st>>>(b);
     issue_compact<1>(b, max_n, &dst->nU, st);
   };
   sort_and_dedup(n_seeds);

@@ -27,6 +27,7 @@ constexpr int kIM = 8;
 constexpr int kSortN = 1024;  // survivors of one pop, padded: L + 2 T_r <= 576 + 128
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kProbeLimit = 1 << 20;
+constexpr int kInsBatch = 4;  // visited-set inserts in flight per lane
 
 struct Node {  // one queue record: 16 bytes
   int32_t E;
@@ -64,30 +65,44 @@ __device__ __forceinline__ bool kless(int Ea, uint64_t fa, int Eb, uint64_t fb) 
   return Ea < Eb || (Ea == Eb && fa < fb);
 }
 
-// Visited set of one slot; *err set on an exhausted probe sequence.
-__device__ __forceinline__ bool hs_contains(const uint64_t* H, int log2, uint64_t fp, bool has_empty, int* err) {
-  if (fp == kEmpty) return has_empty;
+// Visited set of one slot (open addressing, linear probing); *err set on an exhausted probe sequence.
+// The first probe of several keys is issued by the caller, all at once, so that their latencies
+// overlap; these continue a key's probe sequence after a first slot that held another key.
+__device__ __forceinline__ uint64_t hs_home(uint64_t fp, int log2) { return (fp * kGamma) >> (64 - log2); }
+__device__ __forceinline__ bool hs_contains_from(const uint64_t* H, int log2, uint64_t fp, uint64_t s, int* err) {
   const uint64_t mask = (1ull << log2) - 1;
-  uint64_t s = (fp * kGamma) >> (64 - log2);
-  for (int it = 0; it < kProbeLimit; it++) {
+  for (int it = 1; it < kProbeLimit; it++) {
+    s = (s + 1) & mask;
     const uint64_t v = H[s];
     if (v == fp) return true;
     if (v == kEmpty) return false;
-    s = (s + 1) & mask;
   }
   *err = 1;
   return true;
 }
-__device__ __forceinline__ void hs_insert(uint64_t* H, int log2, uint64_t fp, int* err) {
+__device__ __forceinline__ void hs_insert_from(uint64_t* H, int log2, uint64_t fp, uint64_t s, int* err) {
   const uint64_t mask = (1ull << log2) - 1;
-  uint64_t s = (fp * kGamma) >> (64 - log2);
-  for (int it = 0; it < kProbeLimit; it++) {
+  for (int it = 1; it < kProbeLimit; it++) {
+    s = (s + 1) & mask;
     const unsigned long long old =
         atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
     if (old == kEmpty || old == fp) return;
-    s = (s + 1) & mask;
   }
   *err = 1;
+}
+__device__ __forceinline__ bool hs_contains(const uint64_t* H, int log2, uint64_t fp, bool has_empty, int* err) {
+  if (fp == kEmpty) return has_empty;
+  const uint64_t s = hs_home(fp, log2);
+  const uint64_t v = H[s];
+  if (v == fp) return true;
+  if (v == kEmpty) return false;
+  return hs_contains_from(H, log2, fp, s, err);
+}
+__device__ __forceinline__ void hs_insert(uint64_t* H, int log2, uint64_t fp, int* err) {
+  const uint64_t s = hs_home(fp, log2);
+  const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
+  if (old == kEmpty || old == fp) return;
+  hs_insert_from(H, log2, fp, s, err);
 }
 
 // Left shift of rotation code c: c < Tr moves the first c + 1 elements to the end, c >= Tr the last
@@ -286,15 +301,32 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
             scan_tile<kIM, false>(sm, ly, cls, q0, acc);
           else
             scan_tile<kIM, true>(sm, ly, cls, q0, acc);
+          // the tile's Delta E and fingerprints, then the first visited-set probe of all of them at
+          // once (independent loads), then the rare longer probe sequences
+          int dv[kIM], mv[kIM];
+          uint64_t fv[kIM], hv[kIM];
 #pragma unroll
           for (int j = 0; j < kIM; j++) {
             const SlotInfo si = slot_info(ly, cls, q0 + j);
-            if (!si.active) continue;
-            const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, S.P[si.m - 1]);
-            const uint64_t nfp = pfp ^ a.ztab[si.m - 1];
-            if (!hs_contains(H, a.H_log2, nfp, has_empty, &err)) {
+            mv[j] = si.active ? si.m : 0;
+            dv[j] = si.active ? finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, S.P[si.m - 1]) : 0;
+            fv[j] = si.active ? pfp ^ a.ztab[si.m - 1] : kEmpty;
+          }
+#pragma unroll
+          for (int j = 0; j < kIM; j++) hv[j] = (mv[j] && fv[j] != kEmpty) ? H[hs_home(fv[j], a.H_log2)] : kEmpty;
+#pragma unroll
+          for (int j = 0; j < kIM; j++) {
+            if (!mv[j]) continue;
+            bool seen;
+            if (fv[j] == kEmpty)
+              seen = has_empty;
+            else if (hv[j] == fv[j] || hv[j] == kEmpty)
+              seen = hv[j] == fv[j];
+            else
+              seen = hs_contains_from(H, a.H_log2, fv[j], hs_home(fv[j], a.H_log2), &err);
+            if (!seen) {
               const int k = atomicAdd(&S.n_surv, 1);
-              S.keys[k] = SortKey{pE + d, si.m - 1, nfp};
+              S.keys[k] = SortKey{pE + dv[j], mv[j] - 1, fv[j]};
             }
           }
         }
@@ -314,41 +346,56 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       while (np2 < ns) np2 <<= 1;
       for (int i = ns + lane; i < np2; i += 32) S.keys[i] = SortKey{INT32_MAX, 0x7fffffff, kEmpty};
       __syncwarp();
+      // every substage compares np2 / 2 disjoint pairs (i, i + j), i with bit j clear: pair p maps to i
+      // by inserting a zero at bit j, so every lane has a pair in every iteration
       for (int k = 2; k <= np2; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = lane; i < np2; i += 32) {
-            const int l = i ^ j;
-            if (l > i) {
-              const SortKey x = S.keys[i], y = S.keys[l];
-              const bool up = (i & k) == 0;
-              if (up ? sk_less(y, x) : sk_less(x, y)) {
-                S.keys[i] = y;
-                S.keys[l] = x;
-              }
+          for (int pr = lane; pr < (np2 >> 1); pr += 32) {
+            const int i = ((pr & ~(j - 1)) << 1) | (pr & (j - 1));
+            const int l = i | j;
+            const SortKey x = S.keys[i], y = S.keys[l];
+            const bool up = (i & k) == 0;
+            if (up ? sk_less(y, x) : sk_less(x, y)) {
+              S.keys[i] = y;
+              S.keys[l] = x;
             }
           }
           __syncwarp();
         }
       // ---- distinct survivors (equal (E, fp): the same sequence) become one run; H receives them
       int nu = 0;
-      for (int i0 = 0; i0 < ns; i0 += 32) {
-        const int i = i0 + lane;
-        bool keep = false;
-        SortKey x{};
-        if (i < ns) {
-          x = S.keys[i];
-          keep = i == 0 || S.keys[i - 1].E != x.E || S.keys[i - 1].fp != x.fp;
+      for (int i0 = 0; i0 < ns; i0 += 32 * kInsBatch) {
+        // kInsBatch keys per lane: their first compare-and-swap all in flight at once
+        bool ins[kInsBatch];
+        uint64_t fk[kInsBatch];
+        unsigned long long old[kInsBatch];
+#pragma unroll
+        for (int r = 0; r < kInsBatch; r++) {
+          const int i = i0 + 32 * r + lane;
+          bool keep = false;
+          SortKey x{};
+          if (i < ns) {
+            x = S.keys[i];
+            keep = i == 0 || S.keys[i - 1].E != x.E || S.keys[i - 1].fp != x.fp;
+          }
+          const unsigned m = __ballot_sync(kFull, keep);
+          if (keep) {
+            const int o = nu + __popc(m & ((1u << lane) - 1u));
+            arena[top + o] = Node{x.E, (int)(exps << 10) | x.col, x.fp};
+            if (x.fp == kEmpty) has_empty = true;
+          }
+          nu += __popc(m);
+          ins[r] = keep && x.fp != kEmpty;
+          fk[r] = x.fp;
         }
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (keep) {
-          const int o = nu + __popc(m & ((1u << lane) - 1u));
-          arena[top + o] = Node{x.E, (int)(exps << 10) | x.col, x.fp};
-          if (x.fp == kEmpty)
-            has_empty = true;
-          else
-            hs_insert(H, a.H_log2, x.fp, &err);
-        }
-        nu += __popc(m);
+#pragma unroll
+        for (int r = 0; r < kInsBatch; r++)
+          old[r] = ins[r] ? atomicCAS(reinterpret_cast<unsigned long long*>(&H[hs_home(fk[r], a.H_log2)]),
+                                      (unsigned long long)kEmpty, fk[r])
+                          : (unsigned long long)kEmpty;
+#pragma unroll
+        for (int r = 0; r < kInsBatch; r++)
+          if (ins[r] && old[r] != kEmpty && old[r] != fk[r]) hs_insert_from(H, a.H_log2, fk[r], hs_home(fk[r], a.H_log2), &err);
       }
       has_empty = __any_sync(kFull, has_empty);
       err = __reduce_or_sync(kFull, err);

@@ -151,8 +151,9 @@ __device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, 
   const int nt = ly.ntiles[pf.cls] * H;          // tasks of the class
   const int task0 = (pf.cls ? ly.ntiles[0] : 0) * H;
   const int qt = ly.tile_first[pf.cls];
-  int tl = lane_id() % nt, k = lane_id() / nt;
-  const int step_t = 32 % nt, step_k = 32 / nt;
+  const int mg = ly.fold_magic[pf.cls];
+  int k = (lane_id() * mg) >> 16, tl = lane_id() - k * nt;
+  const int step_k = (32 * mg) >> 16, step_t = 32 - step_k * nt;
   for (; k < MH;) {
     const int task = task0 + tl;
     const int q = qt + (tl / H) * M + (tl % H) * MH + k;
@@ -417,9 +418,15 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           else
             scan_range<M, true>(sm, ly, cls, q0, u_begin, u_end, acc);
         }
+        // H = 2: the two lanes of a tile hold partial sums over the two lag ranges, and each needs the
+        // totals of its own MH slots only: it sends the partner's half and adds what it receives
         if (H == 2) {
 #pragma unroll
-          for (int j = 0; j < M; j++) acc[j] += __shfl_xor_sync(kFull, acc[j], 1);
+          for (int k = 0; k < MH; k++) {
+            const int send = h ? acc[k] : acc[MH + k];
+            const int keep = h ? acc[MH + k] : acc[k];
+            acc[k] = keep + __shfl_xor_sync(kFull, send, 1);
+          }
         }
         // finish: keys of this pass's neighbours, then their minimum by a tree of strict comparisons
         // (the slots of a pass are in increasing m, so the left operand wins ties: smallest (key, m))
@@ -431,7 +438,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           const int pk = sl_k[t * 32 + lane];
           const int code = pk & 31;
           const int m = m_first + ly.lam * k;
-          const int a = (H == 2 && h) ? acc[MH + k] : acc[k];
+          const int a = acc[k];
           const int d = (pk >> 5) - ((code & 30) - 8) * (a - 2 * SC);
           int key = d;
           if (BIASED) {

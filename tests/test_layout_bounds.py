@@ -40,9 +40,11 @@ def layout(L, skew, p, M, H=1):
     else:
         half = (NG + 1) // 2; NGh = -(-half // R) * R; rest = NG - NGh
         NGend = NGh + (-(-rest // R) * R if rest > 0 else 0)
+    ntiles = [sum(1 for t in tiles if t[0] == cls) for cls in range(2)]
     ok = (qmax_end + 4 * NGend + 8 < cap and Qr + 4 * NGend + 8 < cap and 2 * qmax_end < cap
           and 4 * NGend <= kCLen)
-    return dict(lam=lam, G=G, NG=NG, c=c, mlast=mlast, tiles=tiles, Qr=Qr, cap=cap, ok=ok, NGh=NGh, NGend=NGend, R=R)
+    return dict(lam=lam, G=G, NG=NG, c=c, mlast=mlast, tiles=tiles, Qr=Qr, cap=cap, ok=ok, NGh=NGh, NGend=NGend, R=R,
+                ntiles=ntiles)
 
 
 
@@ -117,3 +119,23 @@ def test_every_length_fits_some_variant():
     for L in range(3, 577):
         for skew in ((0, 1) if L % 2 else (0,)):
             assert any(layout(L, skew, 0, M, H)["ok"] for M, H in VARIANTS), (L, skew)
+
+
+def test_fold_entry_split_without_divide():
+    """The P fold gives lane n (0..31) its first (slot k, task tl) of a class as k = (n * magic) >> 16,
+    tl = n - k * tasks, and steps by the same split of 32, with magic = ceil(2^16 / tasks): that must be
+    n // tasks for every class of every accepted layout."""
+    seen = 0
+    for M, H in VARIANTS:
+        for L, skew, p in _cases():
+            ly = layout(L, skew, p, M, H)
+            if not ly["ok"]:
+                continue
+            for n in ly["ntiles"]:
+                nt = n * H
+                if nt == 0:
+                    continue
+                magic = ((1 << 16) + nt - 1) // nt
+                assert all((e * magic) >> 16 == e // nt for e in range(33)), (L, skew, p, M, H, nt)
+                seen += 1
+    assert seen > 1000
