@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--pq-hlog2", type=int, default=28)
     ap.add_argument("--pq-tr", type=int, default=0, help="pq workload: MAKE_ROTATIONS per side (0: off)")
     ap.add_argument("--pq-indep-pops", type=int, default=500, help="pq_indep workload: pops per candidate")
+    ap.add_argument("--pq-indep-hlog2", type=int, default=20,
+                    help="pq_indep workload: log2 of each candidate's visited-set slots")
     return ap.parse_args()
 
 
@@ -566,7 +568,7 @@ def run_pq_indep(args, ws, rank, local):
     for it in range(max(1, args.warmup) + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        best, bE, st = lg.labs_pq_independent(L, seeds, max_expansions=pops, H_log2=20)
+        best, bE, st = lg.labs_pq_independent(L, seeds, max_expansions=pops, H_log2=args.pq_indep_hlog2)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     t = statistics.mean(times[-args.steps:])
@@ -578,7 +580,7 @@ def run_pq_indep(args, ws, rank, local):
             "warmup": max(1, args.warmup), "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "step2_independent_L%d_4096candidates_%dpops" % (L, pops), "L": L,
-                       "candidates": int(len(pick)), "pops_each": pops, "H_slots_log2": 20,
+                       "candidates": int(len(pick)), "pops_each": pops, "H_slots_log2": args.pq_indep_hlog2,
                        "seed_best_E": int(cand["E"][pick].min()), "best_E": int(bE.min().cpu()),
                        "improved_candidates": int((stn["improvements"] > 0).sum()),
                        "status_nonzero": int((stn["status"] != 0).sum())},

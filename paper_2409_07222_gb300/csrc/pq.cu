@@ -838,21 +838,21 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   pq_state_init_kernel<<<1, 1, 0, st>>>(dst, n_seeds);
   pq_seed_kernel<<<(unsigned)std::min<long long>((n_seeds + kPqWarps - 1) / kPqWarps, ctx->num_sms * 16), 32 * kPqWarps,
                    0, st>>>(b, n_seeds);
-  auto sort_and_dedup = [&](long long max_n) {
+  auto sort_and_dedup = [&](long long max_n, cudaStream_t s) {
     const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
-    issue_compact<0>(b, max_n, &dst->nS, st);
+    issue_compact<0>(b, max_n, &dst->nS, s);
     const int nseg = (int)((256ll * nb + kSeg - 1) / kSeg);
     for (int pass = 0; pass < 8; pass++) {
-      radix_hist_kernel<<<nb, 256, 0, st>>>(b, pass);
-      seg_reduce_kernel<<<nseg, 256, 0, st>>>(b, pass);
-      seg_scan_sums_kernel<<<1, 1024, 0, st>>>(b.bsum, nseg, b.st, pass);
-      seg_down_kernel<<<nseg, 256, 0, st>>>(b, pass);
-      radix_scatter_kernel<<<nb, 256, 0, st>>>(b, pass);
+      radix_hist_kernel<<<nb, 256, 0, s>>>(b, pass);
+      seg_reduce_kernel<<<nseg, 256, 0, s>>>(b, pass);
+      seg_scan_sums_kernel<<<1, 1024, 0, s>>>(b.bsum, nseg, b.st, pass);
+      seg_down_kernel<<<nseg, 256, 0, s>>>(b, pass);
+      radix_scatter_kernel<<<nb, 256, 0, s>>>(b, pass);
     }
-    sort_fixup_kernel<<<(unsigned)std::min<long long>((max_n + 255) / 256, (long long)ctx->num_sms * 8), 256, 0, st>>>(b);
-    issue_compact<1>(b, max_n, &dst->nU, st);
+    sort_fixup_kernel<<<(unsigned)std::min<long long>((max_n + 255) / 256, (long long)ctx->num_sms * 8), 256, 0, s>>>(b);
+    issue_compact<1>(b, max_n, &dst->nU, s);
   };
-  sort_and_dedup(n_seeds);
+  sort_and_dedup(n_seeds, st);
   pq_seed_admit_kernel<<<(unsigned)std::min<long long>((std::min<long long>(n_seeds, cfg->cap) + 255) / 256, 4096), 256, 0,
                          st>>>(b);
   pq_seed_finish_kernel<<<1, 1, 0, st>>>(b);
@@ -862,17 +862,39 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   const unsigned exp_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->B + kPqWarps - 1) / kPqWarps,
                                                                         (long long)ctx->num_sms * 8));
   const unsigned merge_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->cap + 255) / 256, 65535));
+  // Every round issues the same launches with the same arguments (a round's sizes and stop state live
+  // in device memory), so one round is captured as a CUDA graph and replayed: about 50 launches per
+  // round become one.
+  if (cudaGetLastError() != cudaSuccess) return LABS_ERR_CUDA;
+  if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return LABS_ERR_CUDA;
+  if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LABS_ERR_CUDA;
+  {
+    cudaStream_t cs = ctx->capture_stream;
+    pq_round_begin_kernel<<<1, 1, 0, cs>>>(b);
+    pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, cs>>>(b, ly);
+    sort_and_dedup((long long)cfg->B * width, cs);
+    pq_best_kernel<<<1, 1, 0, cs>>>(b);
+    pq_merge_kernel<<<merge_blocks, 256, 0, cs>>>(b);
+    pq_round_end_kernel<<<1, 1, 0, cs>>>(b);
+  }
+  cudaGraph_t round_graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &round_graph);
+  cudaGraphExec_t round_exec = nullptr;
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&round_exec, round_graph, 0);
+  if (round_graph) cudaGraphDestroy(round_graph);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return LABS_ERR_CUDA;
+  }
   int* hstop = nullptr;
-  if (cudaMallocHost(&hstop, sizeof(int)) != cudaSuccess) return LABS_ERR_NOMEM;
+  if (cudaMallocHost(&hstop, sizeof(int)) != cudaSuccess) {
+    cudaGraphExecDestroy(round_exec);
+    return LABS_ERR_NOMEM;
+  }
   int status = LABS_OK;
   for (long long r = 0; r < max_rounds; r++) {
-    pq_round_begin_kernel<<<1, 1, 0, st>>>(b);
-    pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, st>>>(b, ly);
-    sort_and_dedup((long long)cfg->B * width);
-    pq_best_kernel<<<1, 1, 0, st>>>(b);
-    pq_merge_kernel<<<merge_blocks, 256, 0, st>>>(b);
-    pq_round_end_kernel<<<1, 1, 0, st>>>(b);
-    if (cudaGetLastError() != cudaSuccess) {
+    if (cudaGraphLaunch(round_exec, st) != cudaSuccess) {
       status = LABS_ERR_CUDA;
       break;
     }
@@ -891,6 +913,7 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   if (cudaMemcpyAsync(best_seq, b.best_seq, 8 * W, cudaMemcpyDeviceToDevice, st) != cudaSuccess) status = LABS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) status = LABS_ERR_CUDA;
   cudaFreeHost(hstop);
+  cudaGraphExecDestroy(round_exec);
   return status;
 }
 
