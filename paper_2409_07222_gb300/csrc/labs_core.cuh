@@ -212,7 +212,43 @@ __device__ __forceinline__ int s_at(const ScanSmem& sm, const Layout& ly, int i)
 }
 
 // Byte windows from the packed bits (whole arrays, pads included).
+// Bytes of positions p .. p+3: byte e = s + 1 (0 or 2) for position p + e inside 1..L, else the pad 1;
+// rev: byte e holds position p + 3 - e.  Bits above L - 1 are zero in sm.bits.
+__device__ __forceinline__ uint32_t nibble_bytes(const ScanSmem& sm, int L, int p, bool rev) {
+  if (p > L || p + 3 < 1) return 0x01010101u;  // no position of the window inside 1..L
+  const int b = p - 1;  // bit index of position p: -3 <= b <= L - 1
+  uint32_t x;
+  if (b >= 0) {
+    const int wi = b >> 5;
+    x = __funnelshift_r(sm.bits[wi], wi + 1 < kBitWords ? sm.bits[wi + 1] : 0u, b & 31) & 0xFu;
+  } else {
+    x = (sm.bits[0] << (-b)) & 0xFu;
+  }
+  const int lo = max(0, 1 - p), hi = max(0, p + 3 - L);  // invalid positions at the low / high end
+  const uint32_t v = ((0xFu << lo) & (0xFu >> hi)) & 0xFu;
+  uint32_t xv = x & v, pad = v ^ 0xFu;
+  if (rev) {
+    xv = __brev(xv) >> 28;
+    pad = __brev(pad) >> 28;
+  }
+  // nibble -> one bit per byte: n * 0x204081 puts bit e at 7e + e = 8e, without carries
+  return 2u * ((xv * 0x204081u) & 0x01010101u) + ((pad * 0x204081u) & 0x01010101u);
+}
+
+// lambda = 1: class index t is position t - kQOff + 1, so every word is four consecutive positions.
+__device__ inline void build_bytes_linear(ScanSmem& sm, const Layout& ly) {
+  for (int w = lane_id(); w < kDirBytes / 4; w += 32) {
+    sm.fwd[w] = nibble_bytes(sm, ly.L, 4 * w - kQOff + 1, false);
+    sm.bwd[w] = nibble_bytes(sm, ly.L, ly.Qr - 4 * w - kQOff + 1 - 3, true);
+  }
+  __syncwarp();
+}
+
 __device__ inline void build_bytes(ScanSmem& sm, const Layout& ly) {
+  if (!ly.skew) {
+    build_bytes_linear(sm, ly);
+    return;
+  }
   const int lane = lane_id();
   const int words_per_cls = (ly.skew ? kClassBytes : kDirBytes) / 4;
   for (int cls = 0; cls < ly.ncls; cls++) {

@@ -92,38 +92,42 @@ __device__ __forceinline__ void pq_child(const uint64_t* src, const PqBufs& b, i
 
 __device__ __forceinline__ uint64_t h_slot(uint64_t fp, int log2) { return (fp * kGamma) >> (64 - log2); }
 
-__device__ __forceinline__ bool h_contains(const PqBufs& b, uint64_t fp) {
-  if (fp == kEmptyKey) return b.st->h_has_empty != 0;
+// Continues the probe sequence of fp after slot s, whose key was another one.
+__device__ __forceinline__ bool h_contains_after(const PqBufs& b, uint64_t fp, uint64_t s) {
   const uint64_t mask = (1ull << b.H_log2) - 1;
-  uint64_t s = h_slot(fp, b.H_log2);
-  for (int it = 0; it < kMaxProbe; it++) {
+  for (int it = 1; it < kMaxProbe; it++) {
+    s = (s + 1) & mask;
     const uint64_t v = b.H[s];
     if (v == fp) return true;
     if (v == kEmptyKey) return false;
-    s = (s + 1) & mask;
   }
   atomicExch(&b.st->error, 1);  // probe limit: the set is too full (reported as a capacity error)
   return true;
 }
 
-__device__ __forceinline__ void h_insert(const PqBufs& b, uint64_t fp) {
-  if (fp == kEmptyKey) {
-    if (atomicExch(&b.st->h_has_empty, 1) == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), 1ull);
-    return;
-  }
+__device__ __forceinline__ bool h_contains(const PqBufs& b, uint64_t fp) {
+  if (fp == kEmptyKey) return b.st->h_has_empty != 0;
+  const uint64_t s = h_slot(fp, b.H_log2);
+  const uint64_t v = b.H[s];
+  if (v == fp) return true;
+  if (v == kEmptyKey) return false;
+  return h_contains_after(b, fp, s);
+}
+
+// Inserts fp; returns 1 when it was not there yet (the caller counts insertions into h_size in bulk).
+__device__ __forceinline__ int h_insert(const PqBufs& b, uint64_t fp) {
+  if (fp == kEmptyKey) return atomicExch(&b.st->h_has_empty, 1) == 0 ? 1 : 0;
   const uint64_t mask = (1ull << b.H_log2) - 1;
   uint64_t s = h_slot(fp, b.H_log2);
   for (int it = 0; it < kMaxProbe; it++) {
     const unsigned long long old =
         atomicCAS(reinterpret_cast<unsigned long long*>(&b.H[s]), (unsigned long long)kEmptyKey, fp);
-    if (old == kEmptyKey) {
-      atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), 1ull);
-      return;
-    }
-    if (old == fp) return;
+    if (old == kEmptyKey) return 1;
+    if (old == fp) return 0;
     s = (s + 1) & mask;
   }
   atomicExch(&b.st->error, 1);
+  return 0;
 }
 
 __device__ __forceinline__ bool key_lt(int Ea, uint64_t fa, int Eb, uint64_t fb) {
@@ -183,17 +187,25 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_seed_kernel(PqBufs b, int n_
   }
 }
 
+// Adds a block's insertion counts to h_size with one atomic per warp (every thread of the block calls it).
+__device__ __forceinline__ void h_count(const PqBufs& b, int inserted) {
+  const int w = __reduce_add_sync(kFull, inserted);
+  if (lane_id() == 0 && w) atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), (unsigned long long)w);
+}
+
 // Admits the sorted, de-duplicated seeds: the cap smallest become the open set and enter H.
 __global__ void pq_seed_admit_kernel(PqBufs b) {
   PqState* st = b.st;
   const long long n = min((long long)st->nU, b.cap);
+  int ins = 0;
   for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
     const int q = b.uidx[o];
     b.PE[0][o] = b.uE[o];
     b.Pfp[0][o] = b.ufp[o];
     for (int t = 0; t < b.W; t++) b.Pseq[0][o * b.W + t] = b.seeds[(size_t)q * b.W + t];
-    h_insert(b, b.ufp[o]);
+    ins += h_insert(b, b.ufp[o]);
   }
+  h_count(b, ins);
 }
 
 __global__ void pq_seed_finish_kernel(PqBufs b) {
@@ -270,15 +282,32 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
           scan_tile<kPqM, false>(sm, ly, cls, q0, acc);
         else
           scan_tile<kPqM, true>(sm, ly, cls, q0, acc);
+        // the tile's Delta E and fingerprints, then the first visited-set probe of all of them at once
+        // (independent loads), then the rare longer probe sequences
+        int dv[kPqM], mv[kPqM];
+        uint64_t fv[kPqM], hv[kPqM];
 #pragma unroll
         for (int j = 0; j < kPqM; j++) {
           const SlotInfo si = slot_info(ly, cls, q0 + j);
-          if (!si.active) continue;
-          const int d = finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, Pm[si.m - 1]);
-          const uint64_t nfp = fp ^ b.ztab[si.m - 1];
-          const size_t di = (size_t)q * b.width + (si.m - 1);
-          b.dE[di] = h_contains(b, nfp) ? INT32_MAX : E + d;
-          b.dfp[di] = nfp;
+          mv[j] = si.active ? si.m : 0;
+          dv[j] = si.active ? finish_delta(sm, ly, cls, q0 + j, si, acc[j], SC, Pm[si.m - 1]) : 0;
+          fv[j] = si.active ? fp ^ b.ztab[si.m - 1] : kEmptyKey;
+        }
+#pragma unroll
+        for (int j = 0; j < kPqM; j++) hv[j] = (mv[j] && fv[j] != kEmptyKey) ? b.H[h_slot(fv[j], b.H_log2)] : kEmptyKey;
+#pragma unroll
+        for (int j = 0; j < kPqM; j++) {
+          if (!mv[j]) continue;
+          bool seen;
+          if (fv[j] == kEmptyKey)
+            seen = st->h_has_empty != 0;
+          else if (hv[j] == fv[j] || hv[j] == kEmptyKey)
+            seen = hv[j] == fv[j];
+          else
+            seen = h_contains_after(b, fv[j], h_slot(fv[j], b.H_log2));
+          const size_t di = (size_t)q * b.width + (mv[j] - 1);
+          b.dE[di] = seen ? INT32_MAX : E + dv[j];
+          b.dfp[di] = fv[j];
         }
       }
     }
@@ -685,9 +714,9 @@ __global__ void pq_best_kernel(PqBufs b) {
 }
 
 // Number of open-set (rest) entries among the first o merged outputs.
-__device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
-                                                 const uint64_t* Ufp, long long nU, long long o) {
-  long long lo = max(0ll, o - nU), hi = min(o, nR);
+// The search may start from any [lo, hi] that contains the answer (the predicate is monotone in mid).
+__device__ __forceinline__ long long merge_split_in(const int32_t* RE, const uint64_t* Rfp, const int32_t* UE,
+                                                    const uint64_t* Ufp, long long o, long long lo, long long hi) {
   while (lo < hi) {
     const long long mid = (lo + hi) >> 1;
     const long long ui = o - mid - 1;
@@ -699,6 +728,17 @@ __device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64
   return lo;
 }
 
+__device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
+                                                 const uint64_t* Ufp, long long nU, long long o) {
+  return merge_split_in(RE, Rfp, UE, Ufp, o, max(0ll, o - nU), min(o, nR));
+}
+
+// Merge path in tiles: a block takes kMergeTile consecutive outputs and finds the tile's two ends by
+// full searches (two threads); each thread then finds its own output's source by a search inside the
+// tile's ranges only (log2 kMergeTile steps on data the tile shares), consecutive threads writing
+// consecutive outputs.
+constexpr int kMergeTile = 2048;
+
 __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
   const PqState* st = b.st;
   if (st->b == 0) return;
@@ -708,22 +748,32 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
   const int32_t* RE = b.PE[cur] + nb;
   const uint64_t* Rfp = b.Pfp[cur] + nb;
   const uint64_t* Rseq = b.Pseq[cur] + nb * b.W;
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < nOut; o += (long long)gridDim.x * blockDim.x) {
-    const long long a = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o);
-    const long long ui = o - a;
-    const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
-    if (from_rest) {
-      b.PE[nxt][o] = RE[a];
-      b.Pfp[nxt][o] = Rfp[a];
-      for (int t = 0; t < b.W; t++) b.Pseq[nxt][o * b.W + t] = Rseq[a * b.W + t];
-    } else {
-      const int q = b.uidx[ui] / b.width, col = b.uidx[ui] % b.width;
-      b.PE[nxt][o] = b.uE[ui];
-      b.Pfp[nxt][o] = b.ufp[ui];
-      pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
-      h_insert(b, b.ufp[ui]);
+  __shared__ long long split[2];
+  int ins = 0;
+  for (long long o0 = (long long)blockIdx.x * kMergeTile; o0 < nOut; o0 += (long long)gridDim.x * kMergeTile) {
+    const long long o1 = min(o0 + kMergeTile, nOut);
+    __syncthreads();  // the previous tile's ends are no longer read
+    if (threadIdx.x < 2) split[threadIdx.x] = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, threadIdx.x ? o1 : o0);
+    __syncthreads();
+    const long long ra = split[0], rb = split[1], ua = o0 - ra, ub = o1 - rb;
+    for (long long o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+      const long long a = merge_split_in(RE, Rfp, b.uE, b.ufp, o, max(ra, o - ub), min(rb, o - ua));
+      const long long ui = o - a;
+      const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
+      if (from_rest) {
+        b.PE[nxt][o] = RE[a];
+        b.Pfp[nxt][o] = Rfp[a];
+        for (int t = 0; t < b.W; t++) b.Pseq[nxt][o * b.W + t] = Rseq[a * b.W + t];
+      } else {
+        const int q = b.uidx[ui] / b.width, col = b.uidx[ui] % b.width;
+        b.PE[nxt][o] = b.uE[ui];
+        b.Pfp[nxt][o] = b.ufp[ui];
+        pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
+        ins += h_insert(b, b.ufp[ui]);
+      }
     }
   }
+  h_count(b, ins);
 }
 
 __global__ void pq_round_end_kernel(PqBufs b) {
@@ -861,7 +911,8 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   const long long max_rounds = (cfg->max_expansions + cfg->B - 1) / cfg->B + 1;
   const unsigned exp_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->B + kPqWarps - 1) / kPqWarps,
                                                                         (long long)ctx->num_sms * 8));
-  const unsigned merge_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->cap + 255) / 256, 65535));
+  const unsigned merge_blocks =
+      (unsigned)std::max(1ll, std::min<long long>((cfg->cap + kMergeTile - 1) / kMergeTile, (long long)ctx->num_sms * 16));
   // Every round issues the same launches with the same arguments (a round's sizes and stop state live
   // in device memory), so one round is captured as a CUDA graph and replayed: about 50 launches per
   // round become one.

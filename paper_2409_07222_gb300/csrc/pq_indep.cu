@@ -24,10 +24,11 @@ namespace {
 
 constexpr int kIWarps = 4;
 constexpr int kIM = 8;
-constexpr int kSortN = 1024;  // survivors of one pop, padded: L + 2 T_r <= 576 + 128
+constexpr int kSortN = 1024;  // most survivors of one pop, padded to a power of two: L + 2 T_r <= 576 + 128
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kProbeLimit = 1 << 20;
 constexpr int kInsBatch = 4;  // visited-set inserts in flight per lane
+constexpr int kMaxTr = 64;    // rotations per side (the library's bound on T_r)
 
 struct Node {  // one queue record: 16 bytes
   int32_t E;
@@ -59,6 +60,7 @@ struct IndepArgs {
   uint64_t* H;
   const uint64_t* ztab;
   unsigned long long* counter;
+  int smem_stride;  // bytes of shared memory per warp: IndepSmem + the sort buffer
 };
 
 __device__ __forceinline__ bool kless(int Ea, uint64_t fa, int Eb, uint64_t fb) {
@@ -172,23 +174,24 @@ __device__ __forceinline__ uint64_t fp_bits(const uint32_t* bits, int L, const u
   return warp_xor_u64(h);
 }
 
-struct SortKey {  // survivor: (E, fp, column) orders the run; column < 2^16
-  int32_t E;
-  int32_t col;
-  uint64_t fp;
-};
-
-__device__ __forceinline__ bool sk_less(const SortKey& a, const SortKey& b) {
-  if (a.E != b.E) return a.E < b.E;
-  if (a.fp != b.fp) return a.fp < b.fp;
-  return a.col < b.col;
+// A survivor of one pop as one 64-bit key: E (26 bits: E < L^3 / 3 < 2^26 for L <= 576), the top 28
+// bits of its fingerprint, its column (10 bits).  Unsigned order is (E, fp >> 36, column); runs of equal
+// (E, fp >> 36) are then put in (fp, column) order, so the survivors end in (E, fp, column) order.  The
+// fingerprint itself is the pivot's with the column's key (a flip) or the rotation's, kept aside.
+constexpr uint64_t kPadKey = ~0ull;
+__device__ __forceinline__ uint64_t pack_key(int E, uint64_t fp, int col) {
+  return ((uint64_t)(uint32_t)E << 38) | ((fp >> 36) << 10) | (uint64_t)col;
 }
+__device__ __forceinline__ int key_E(uint64_t k) { return (int)(k >> 38); }
+__device__ __forceinline__ int key_col(uint64_t k) { return (int)(k & 1023u); }
 
+// Per-warp shared memory: this fixed part, then the survivors' sort buffer of np2 keys (the next power
+// of two of L + 2 T_r, at most kSortN), so that shorter queues leave room for more resident warps.
 struct __align__(16) IndepSmem {
   ScanSmem s;
+  uint64_t rfp[2 * kMaxTr];   // fingerprints of the pivot's rotations (columns L ..)
   uint32_t pbits[kBitWords];  // the pivot
   uint32_t cbits[kBitWords];  // a child
-  SortKey keys[kSortN];
   int16_t P[kMaxL];  // P_m of the pivot's neighbours
   uint32_t xb[kBitWords];
   int n_surv;
@@ -196,7 +199,9 @@ struct __align__(16) IndepSmem {
 
 __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Layout ly) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  IndepSmem& S = reinterpret_cast<IndepSmem*>(smem_raw)[threadIdx.x >> 5];
+  unsigned char* wbase = smem_raw + (size_t)(threadIdx.x >> 5) * a.smem_stride;
+  IndepSmem& S = *reinterpret_cast<IndepSmem*>(wbase);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(wbase + sizeof(IndepSmem));
   ScanSmem& sm = S.s;
   const int lane = lane_id();
   const long long slot = (long long)blockIdx.x * kIWarps + (threadIdx.x >> 5);
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
               seen = hs_contains_from(H, a.H_log2, fv[j], hs_home(fv[j], a.H_log2), &err);
             if (!seen) {
               const int k = atomicAdd(&S.n_surv, 1);
-              S.keys[k] = SortKey{pE + dv[j], mv[j] - 1, fv[j]};
+              keys[k] = pack_key(pE + dv[j], fv[j], mv[j] - 1);
             }
           }
         }
@@ -336,15 +341,19 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         rotate_bits(S.pbits, a.L, rshift(a.L, a.Tr, c), S.cbits);
         const int e = energy_bits(S.cbits, a.L);
         const uint64_t h = fp_bits(S.cbits, a.L, a.ztab);
-        if (lane == 0 && !hs_contains(H, a.H_log2, h, has_empty, &err)) S.keys[S.n_surv++] = SortKey{e, a.L + c, h};
+        if (lane == 0) {
+          S.rfp[c] = h;
+          if (!hs_contains(H, a.H_log2, h, has_empty, &err)) keys[S.n_surv++] = pack_key(e, h, a.L + c);
+        }
         __syncwarp();
       }
       err = __reduce_or_sync(kFull, err);
       const int ns = S.n_surv;
-      // ---- sort the survivors by (E, fp, column): bitonic over the next power of two
+      // ---- sort the survivors by (E, fp, column): bitonic over the next power of two on the packed keys
+      auto fp_of = [&](int col) -> uint64_t { return col < a.L ? pfp ^ a.ztab[col] : S.rfp[col - a.L]; };
       int np2 = 1;
       while (np2 < ns) np2 <<= 1;
-      for (int i = ns + lane; i < np2; i += 32) S.keys[i] = SortKey{INT32_MAX, 0x7fffffff, kEmpty};
+      for (int i = ns + lane; i < np2; i += 32) keys[i] = kPadKey;
       __syncwarp();
       // every substage compares np2 / 2 disjoint pairs (i, i + j), i with bit j clear: pair p maps to i
       // by inserting a zero at bit j, so every lane has a pair in every iteration
@@ -353,17 +362,38 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
           for (int pr = lane; pr < (np2 >> 1); pr += 32) {
             const int i = ((pr & ~(j - 1)) << 1) | (pr & (j - 1));
             const int l = i | j;
-            const SortKey x = S.keys[i], y = S.keys[l];
+            const uint64_t x = keys[i], y = keys[l];
             const bool up = (i & k) == 0;
-            if (up ? sk_less(y, x) : sk_less(x, y)) {
-              S.keys[i] = y;
-              S.keys[l] = x;
+            if (up ? y < x : x < y) {
+              keys[i] = y;
+              keys[l] = x;
             }
           }
           __syncwarp();
         }
+      // runs of equal (E, fp >> 36), if any, into (fp, column) order (one lane; such runs are rare)
+      bool tie = false;
+      for (int i = lane; i + 1 < ns; i += 32) tie |= (keys[i] >> 10) == (keys[i + 1] >> 10);
+      if (__any_sync(kFull, tie)) {
+        if (lane == 0)
+          for (int i = 1; i < ns; i++) {
+            const uint64_t kx = keys[i];
+            const uint64_t fx = fp_of(key_col(kx));
+            int c = i;
+            while (c > 0 && (keys[c - 1] >> 10) == (kx >> 10)) {
+              const uint64_t fy = fp_of(key_col(keys[c - 1]));
+              if (fy < fx || (fy == fx && key_col(keys[c - 1]) < key_col(kx))) break;
+              keys[c] = keys[c - 1];
+              c--;
+            }
+            keys[c] = kx;
+          }
+        __syncwarp();
+      }
       // ---- distinct survivors (equal (E, fp): the same sequence) become one run; H receives them
       int nu = 0;
+      int carryE = 0;  // the element before this lane-0's: last lane's of the previous 32
+      uint64_t carryF = 0;
       for (int i0 = 0; i0 < ns; i0 += 32 * kInsBatch) {
         // kInsBatch keys per lane: their first compare-and-swap all in flight at once
         bool ins[kInsBatch];
@@ -372,21 +402,32 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
 #pragma unroll
         for (int r = 0; r < kInsBatch; r++) {
           const int i = i0 + 32 * r + lane;
-          bool keep = false;
-          SortKey x{};
+          int xE = 0, xc = 0;
+          uint64_t xf = 0;
           if (i < ns) {
-            x = S.keys[i];
-            keep = i == 0 || S.keys[i - 1].E != x.E || S.keys[i - 1].fp != x.fp;
+            const uint64_t kx = keys[i];
+            xE = key_E(kx);
+            xc = key_col(kx);
+            xf = fp_of(xc);
           }
+          int pE = __shfl_up_sync(kFull, xE, 1);
+          uint64_t pf = __shfl_up_sync(kFull, xf, 1);
+          if (lane == 0) {
+            pE = carryE;
+            pf = carryF;
+          }
+          carryE = __shfl_sync(kFull, xE, 31);
+          carryF = __shfl_sync(kFull, xf, 31);
+          const bool keep = i < ns && (i == 0 || pE != xE || pf != xf);
           const unsigned m = __ballot_sync(kFull, keep);
           if (keep) {
             const int o = nu + __popc(m & ((1u << lane) - 1u));
-            arena[top + o] = Node{x.E, (int)(exps << 10) | x.col, x.fp};
-            if (x.fp == kEmpty) has_empty = true;
+            arena[top + o] = Node{xE, (int)(exps << 10) | xc, xf};
+            if (xf == kEmpty) has_empty = true;
           }
           nu += __popc(m);
-          ins[r] = keep && x.fp != kEmpty;
-          fk[r] = x.fp;
+          ins[r] = keep && xf != kEmpty;
+          fk[r] = xf;
         }
 #pragma unroll
         for (int r = 0; r < kInsBatch; r++)
@@ -401,10 +442,12 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       err = __reduce_or_sync(kFull, err);
       __syncwarp();
       // ---- best, statistics, the new run
-      if (nu > 0 && S.keys[0].E < bestE) {
-        bestE = S.keys[0].E;
-        bestfp = S.keys[0].fp;
-        const int col = S.keys[0].col;
+      const int E0 = nu > 0 ? key_E(keys[0]) : INT32_MAX, col0 = nu > 0 ? key_col(keys[0]) : 0;
+      const uint64_t fp0 = nu > 0 ? fp_of(col0) : 0;
+      if (nu > 0 && E0 < bestE) {
+        bestE = E0;
+        bestfp = fp0;
+        const int col = col0;
         if (col < a.L)
           flip_bits(S.pbits, col, S.cbits);
         else
@@ -416,7 +459,7 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         u++;
       }
       if (nu > 0 && lane == 0) {  // push the run: sift up
-        RunHead h{S.keys[0].E, (int)top, S.keys[0].fp, (int)(top + nu), 0};
+        RunHead h{E0, (int)top, fp0, (int)(top + nu), 0};
         long long i = heap_n;
         while (i > 0) {
           const long long p = (i - 1) >> 1;
@@ -484,7 +527,11 @@ int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uin
   // resident warps: as many slots as the memory budget allows, at most one per candidate
   const size_t per_slot = (size_t)a.arena_cap * sizeof(Node) + (size_t)a.heap_cap * sizeof(RunHead) +
                           (size_t)a.max_exp * W * 8 + (8ull << a.H_log2);
-  const size_t smem = sizeof(IndepSmem) * kIWarps;
+  int np2max = 1;  // a pop's survivors (at most width) are sorted over the next power of two
+  while (np2max < a.width) np2max <<= 1;
+  if (np2max > kSortN || cfg->T_r > kMaxTr) return LABS_ERR_INVALID_ARG;
+  a.smem_stride = (int)((sizeof(IndepSmem) + sizeof(uint64_t) * np2max + 15) & ~size_t(15));
+  const size_t smem = (size_t)a.smem_stride * kIWarps;
   if (cudaFuncSetAttribute(pq_indep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return LABS_ERR_CUDA;
   int per_sm = 0;
