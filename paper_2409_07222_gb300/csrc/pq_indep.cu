@@ -4,16 +4,20 @@
 //
 // GB300 mapping.  One warp per candidate; a candidate's state lives in HBM:
 //   arena  -- every pushed node as a 16-byte record (E, link, fp); the survivors of one pop are appended
-//             as one run sorted by (E, fp, column), so the arena is a set of sorted runs;
-//   runs   -- a binary heap over the runs' current heads keyed by (E, fp): its top is the queue minimum,
-//             a pop advances that run's head (one sift-down), a new run is one sift-up;
+//             as one run, in no particular order;
+//   runs   -- a binary heap over the runs keyed by each run's smallest (E, fp): its top is the queue
+//             minimum.  A pop takes that node out of its run (the run's last node fills the gap), finds
+//             the run's new smallest by one warp-wide rescan (at most L + 2 T_r records) and sifts down;
+//             a new run is one sift-up.  Keys (E, fp) are distinct in a queue (the visited set admits a
+//             sequence once), so the pop order is that of the sequential definition;
 //   pivots -- the sequence of every popped node (a node is stored as its pivot and column, and is made
 //             into a sequence only when popped);
 //   H      -- the candidate's visited set (open addressing, cleared per candidate).
 // A pop scans all L single flips (the dp4a tiles of labs_core.cuh) and, with T_r > 0, the pivot's 2 T_r
-// rotations; survivors are sorted in shared memory (bitonic, one warp) and pushed as one run.  Memory per
-// resident warp is about max_expansions x (L + 2 T_r) x 16 B + 2^H_log2 x 8 B: HBM capacity, not
-// bandwidth, is what this design spends.
+// rotations (a rotation equal to a flip child or to an earlier rotation is the same sequence and is
+// dropped, as the ordered dedup keeps the smaller column).  Memory per resident warp is about
+// max_expansions x (L + 2 T_r) x 16 B + 2^H_log2 x 8 B: HBM capacity, not bandwidth, is what this design
+// spends.
 #include <algorithm>
 
 #include "labs_core.cuh"
@@ -24,10 +28,9 @@ namespace {
 
 constexpr int kIWarps = 4;
 constexpr int kIM = 8;
-constexpr int kSortN = 1024;  // most survivors of one pop, padded to a power of two: L + 2 T_r <= 576 + 128
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kProbeLimit = 1 << 20;
-constexpr int kInsBatch = 4;  // visited-set inserts in flight per lane
+constexpr int kInsBatch = 16;  // visited-set inserts in flight per lane (a pop's run: <= 704 / 32 + 1)
 constexpr int kMaxTr = 64;    // rotations per side (the library's bound on T_r)
 
 struct Node {  // one queue record: 16 bytes
@@ -36,12 +39,12 @@ struct Node {  // one queue record: 16 bytes
   uint64_t fp;
 };
 
-struct RunHead {  // heap element: the run's current head key and its remaining range in the arena
+struct RunHead {  // heap element: the run's smallest key, where it is, and the run's live range
   int32_t E;
-  int32_t cur;
+  int32_t cur;  // arena index of the smallest node
   uint64_t fp;
-  int32_t end;
-  int32_t pad;
+  int32_t end;    // live nodes are [begin, end)
+  int32_t begin;
 };
 
 struct IndepArgs {
@@ -57,10 +60,11 @@ struct IndepArgs {
   Node* arena;
   RunHead* heap;
   uint64_t* pivots;
+  uint32_t* tables;  // per popped pivot: its C table (2 NG words of int16 pairs) and P_m (ceil(L/2) words)
+  int tab_words;
   uint64_t* H;
   const uint64_t* ztab;
   unsigned long long* counter;
-  int smem_stride;  // bytes of shared memory per warp: IndepSmem + the sort buffer
 };
 
 __device__ __forceinline__ bool kless(int Ea, uint64_t fa, int Eb, uint64_t fb) {
@@ -174,19 +178,35 @@ __device__ __forceinline__ uint64_t fp_bits(const uint32_t* bits, int L, const u
   return warp_xor_u64(h);
 }
 
-// A survivor of one pop as one 64-bit key: E (26 bits: E < L^3 / 3 < 2^26 for L <= 576), the top 28
-// bits of its fingerprint, its column (10 bits).  Unsigned order is (E, fp >> 36, column); runs of equal
-// (E, fp >> 36) are then put in (fp, column) order, so the survivors end in (E, fp, column) order.  The
-// fingerprint itself is the pivot's with the column's key (a flip) or the rotation's, kept aside.
-constexpr uint64_t kPadKey = ~0ull;
-__device__ __forceinline__ uint64_t pack_key(int E, uint64_t fp, int col) {
-  return ((uint64_t)(uint32_t)E << 38) | ((fp >> 36) << 10) | (uint64_t)col;
+// The warp's smallest (E, fp) over the lanes' candidates (bi >= 0; keys distinct) and its index, on every
+// lane.
+__device__ __forceinline__ void warp_argmin(int bE, uint64_t bf, int bi, int& E, uint64_t& fp, int& idx) {
+  const int mE = __reduce_min_sync(kFull, bE);
+  const unsigned mhi = __reduce_min_sync(kFull, bE == mE ? (unsigned)(bf >> 32) : 0xffffffffu);
+  const bool on = bE == mE && (unsigned)(bf >> 32) == mhi;
+  const unsigned mlo = __reduce_min_sync(kFull, on ? (unsigned)bf : 0xffffffffu);
+  const unsigned who = __ballot_sync(kFull, on && (unsigned)bf == mlo && bi >= 0);
+  E = mE;
+  fp = ((uint64_t)mhi << 32) | mlo;
+  idx = __shfl_sync(kFull, bi, __ffs(who) - 1);
 }
-__device__ __forceinline__ int key_E(uint64_t k) { return (int)(k >> 38); }
-__device__ __forceinline__ int key_col(uint64_t k) { return (int)(k & 1023u); }
 
-// Per-warp shared memory: this fixed part, then the survivors' sort buffer of np2 keys (the next power
-// of two of L + 2 T_r, at most kSortN), so that shorter queues leave room for more resident warps.
+// Smallest (E, fp) of arena nodes [begin, end) (non-empty, keys distinct) and its index, on every lane.
+__device__ __forceinline__ void run_min(const Node* arena, int begin, int end, int& E, uint64_t& fp, int& idx) {
+  int bE = INT32_MAX, bi = -1;
+  uint64_t bf = ~0ull;
+  for (int i = begin + lane_id(); i < end; i += 32) {
+    const Node x = arena[i];
+    if (kless(x.E, x.fp, bE, bf)) {
+      bE = x.E;
+      bf = x.fp;
+      bi = i;
+    }
+  }
+  warp_argmin(bE, bf, bi, E, fp, idx);
+}
+
+// Per-warp shared memory.
 struct __align__(16) IndepSmem {
   ScanSmem s;
   uint64_t rfp[2 * kMaxTr];   // fingerprints of the pivot's rotations (columns L ..)
@@ -199,15 +219,14 @@ struct __align__(16) IndepSmem {
 
 __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Layout ly) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* wbase = smem_raw + (size_t)(threadIdx.x >> 5) * a.smem_stride;
-  IndepSmem& S = *reinterpret_cast<IndepSmem*>(wbase);
-  uint64_t* keys = reinterpret_cast<uint64_t*>(wbase + sizeof(IndepSmem));
+  IndepSmem& S = reinterpret_cast<IndepSmem*>(smem_raw)[threadIdx.x >> 5];
   ScanSmem& sm = S.s;
   const int lane = lane_id();
   const long long slot = (long long)blockIdx.x * kIWarps + (threadIdx.x >> 5);
   Node* arena = a.arena + slot * a.arena_cap;
   RunHead* heap = a.heap + slot * a.heap_cap;
   uint64_t* pivots = a.pivots + slot * a.max_exp * a.W;
+  uint32_t* tables = a.tables + slot * a.max_exp * a.tab_words;
   uint64_t* H = a.H + slot * (1ll << a.H_log2);
   const long long hslots = 1ll << a.H_log2;
 
@@ -239,21 +258,20 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       else if (heap_n == 0) stop = 2;
       else if (a.T_u > 0 && u >= a.T_u) stop = 3;
       if (stop || err) break;
-      // ---- pop: the top run's head; advance the run, sift down (lane 0)
-      int pE = 0, plink = 0;
-      unsigned long long pfp = 0;
+      // ---- pop: the top run's smallest node; the run's last node fills its place, the run's new
+      //      smallest by a rescan (warp), then the sift-down (lane 0)
+      RunHead h = heap[0];
+      const Node nd = arena[h.cur];
+      const int pE = nd.E, plink = nd.link;
+      const uint64_t pfp = nd.fp;
+      __syncwarp();
+      if (lane == 0 && h.cur != h.end - 1) arena[h.cur] = arena[h.end - 1];
+      __syncwarp();
+      h.end--;
+      const bool alive = h.end > h.begin;
+      if (alive) run_min(arena, h.begin, h.end, h.E, h.fp, h.cur);
       if (lane == 0) {
-        RunHead h = heap[0];
-        const Node nd = arena[h.cur];
-        pE = nd.E;
-        plink = nd.link;
-        pfp = nd.fp;
-        h.cur++;
-        if (h.cur < h.end) {
-          const Node nx = arena[h.cur];
-          h.E = nx.E;
-          h.fp = nx.fp;
-        } else {
+        if (!alive) {
           heap_n--;
           h = heap[heap_n];
         }
@@ -272,9 +290,6 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         }
       }
       heap_n = __shfl_sync(kFull, heap_n, 0);
-      pE = __shfl_sync(kFull, pE, 0);
-      plink = __shfl_sync(kFull, plink, 0);
-      pfp = __shfl_sync(kFull, pfp, 0);
       // ---- the pivot's sequence: the seed, or the child `col` of an earlier pivot
       if (plink < 0) {
         words_to_bits(a.seeds + cand * a.W, a.L, S.pbits);
@@ -287,15 +302,50 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
           rotate_bits(S.cbits, a.L, rshift(a.L, a.Tr, col - a.L), S.pbits);
       }
       bits_to_words(S.pbits, a.L, pivots + exps * a.W);
-      // ---- expand: every single flip (dp4a tiles), then the rotations
+      // ---- the pivot's correlation table and P_m: a flip child's from its parent's (kept with every
+      //      popped pivot) by one O(L) update, the seed's and a rotation's from scratch
       if (lane == 0) S.n_surv = 0;
-      for (int w = lane; w < kBitWords; w += 32) sm.bits[w] = S.pbits[w];
-      __syncwarp();
-      build_table(sm, ly);
-      const bool fast = pack_c8(sm);
+      bool fast;
+      uint32_t* ptab = tables + exps * a.tab_words;
+      const int pcol = plink & 1023;
+      if (plink >= 0 && pcol < a.L) {
+        const uint32_t* par = tables + (long long)(plink >> 10) * a.tab_words;
+        uint32_t* C16w = reinterpret_cast<uint32_t*>(sm.C16);
+        uint32_t* Pw = reinterpret_cast<uint32_t*>(S.P);
+        for (int w = lane; w < 2 * ly.NG; w += 32) C16w[w] = par[w];
+        for (int w = lane; w < (a.L + 1) / 2; w += 32) Pw[w] = par[2 * ly.NG + w];
+        for (int w = lane; w < kBitWords; w += 32) sm.bits[w] = S.cbits[w];  // the parent
+        __syncwarp();
+        build_bytes(sm, ly);
+        // P_m of the child: flipping f changes the product s_f s_{2m-f} of every m != f (pads: 0)
+        const int f = pcol + 1;
+        const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm.fwd);
+        const int qf = pos_q(ly, f), sf = (int)Fc[qf] - 1;
+        for (int m = lane + 1; m <= a.L; m += 32)
+          if (m != f) S.P[m - 1] = (int16_t)(S.P[m - 1] - 2 * sf * ((int)Fc[max(2 * pos_q(ly, m) - qf, 0)] - 1));
+        __syncwarp();
+        table_update(sm, ly, f, &fast);
+        if (lane == 0) flip_position(sm, ly, f);
+        __syncwarp();
+      } else {
+        for (int w = lane; w < kBitWords; w += 32) sm.bits[w] = S.pbits[w];
+        __syncwarp();
+        build_table(sm, ly);
+        fast = pack_c8(sm);
+        build_bytes(sm, ly);
+        p_all(sm, ly, S.xb, S.cbits, S.P);
+      }
       const int SC = table_sum(sm);
-      build_bytes(sm, ly);
-      p_all(sm, ly, S.xb, S.cbits, S.P);
+      {
+        const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16);
+        const uint32_t* Pw = reinterpret_cast<const uint32_t*>(S.P);
+        for (int w = lane; w < 2 * ly.NG; w += 32) ptab[w] = C16w[w];
+        for (int w = lane; w < (a.L + 1) / 2; w += 32) ptab[2 * ly.NG + w] = Pw[w];
+      }
+      Node* run = arena + top;
+      const int link0 = (int)(exps << 10);
+      int rE = INT32_MAX, ri = -1;  // this lane's smallest survivor (the run's head comes from these)
+      uint64_t rf = ~0ull;
       for (int base = 0; base < ly.n_tiles; base += 32) {
         const int tau = base + lane;
         if (tau < ly.n_tiles) {
@@ -331,103 +381,53 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
               seen = hs_contains_from(H, a.H_log2, fv[j], hs_home(fv[j], a.H_log2), &err);
             if (!seen) {
               const int k = atomicAdd(&S.n_surv, 1);
-              keys[k] = pack_key(pE + dv[j], fv[j], mv[j] - 1);
+              run[k] = Node{pE + dv[j], link0 | (mv[j] - 1), fv[j]};
+              if (kless(pE + dv[j], fv[j], rE, rf)) {
+                rE = pE + dv[j];
+                rf = fv[j];
+                ri = (int)top + k;
+              }
             }
           }
         }
       }
       __syncwarp();
+      // ---- the rotations: a rotation equal to a flip child or to an earlier rotation is dropped
       for (int c = 0; c < 2 * a.Tr; c++) {
         rotate_bits(S.pbits, a.L, rshift(a.L, a.Tr, c), S.cbits);
         const int e = energy_bits(S.cbits, a.L);
-        const uint64_t h = fp_bits(S.cbits, a.L, a.ztab);
+        const uint64_t hf = fp_bits(S.cbits, a.L, a.ztab);
+        bool dup = false;
+        for (int j = lane; j < a.L; j += 32) dup |= (hf ^ pfp) == a.ztab[j];
+        for (int j = lane; j < c; j += 32) dup |= S.rfp[j] == hf;
+        dup = __any_sync(kFull, dup);
         if (lane == 0) {
-          S.rfp[c] = h;
-          if (!hs_contains(H, a.H_log2, h, has_empty, &err)) keys[S.n_surv++] = pack_key(e, h, a.L + c);
+          S.rfp[c] = hf;
+          if (!dup && !hs_contains(H, a.H_log2, hf, has_empty, &err)) {
+            const int k = S.n_surv++;
+            run[k] = Node{e, link0 | (a.L + c), hf};
+            if (kless(e, hf, rE, rf)) {
+              rE = e;
+              rf = hf;
+              ri = (int)top + k;
+            }
+          }
         }
         __syncwarp();
       }
       err = __reduce_or_sync(kFull, err);
-      const int ns = S.n_surv;
-      // ---- sort the survivors by (E, fp, column): bitonic over the next power of two on the packed keys
-      auto fp_of = [&](int col) -> uint64_t { return col < a.L ? pfp ^ a.ztab[col] : S.rfp[col - a.L]; };
-      int np2 = 1;
-      while (np2 < ns) np2 <<= 1;
-      for (int i = ns + lane; i < np2; i += 32) keys[i] = kPadKey;
-      __syncwarp();
-      // every substage compares np2 / 2 disjoint pairs (i, i + j), i with bit j clear: pair p maps to i
-      // by inserting a zero at bit j, so every lane has a pair in every iteration
-      for (int k = 2; k <= np2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int pr = lane; pr < (np2 >> 1); pr += 32) {
-            const int i = ((pr & ~(j - 1)) << 1) | (pr & (j - 1));
-            const int l = i | j;
-            const uint64_t x = keys[i], y = keys[l];
-            const bool up = (i & k) == 0;
-            if (up ? y < x : x < y) {
-              keys[i] = y;
-              keys[l] = x;
-            }
-          }
-          __syncwarp();
-        }
-      // runs of equal (E, fp >> 36), if any, into (fp, column) order (one lane; such runs are rare)
-      bool tie = false;
-      for (int i = lane; i + 1 < ns; i += 32) tie |= (keys[i] >> 10) == (keys[i + 1] >> 10);
-      if (__any_sync(kFull, tie)) {
-        if (lane == 0)
-          for (int i = 1; i < ns; i++) {
-            const uint64_t kx = keys[i];
-            const uint64_t fx = fp_of(key_col(kx));
-            int c = i;
-            while (c > 0 && (keys[c - 1] >> 10) == (kx >> 10)) {
-              const uint64_t fy = fp_of(key_col(keys[c - 1]));
-              if (fy < fx || (fy == fx && key_col(keys[c - 1]) < key_col(kx))) break;
-              keys[c] = keys[c - 1];
-              c--;
-            }
-            keys[c] = kx;
-          }
-        __syncwarp();
-      }
-      // ---- distinct survivors (equal (E, fp): the same sequence) become one run; H receives them
-      int nu = 0;
-      int carryE = 0;  // the element before this lane-0's: last lane's of the previous 32
-      uint64_t carryF = 0;
-      for (int i0 = 0; i0 < ns; i0 += 32 * kInsBatch) {
-        // kInsBatch keys per lane: their first compare-and-swap all in flight at once
+      const int nu = S.n_surv;
+      // ---- H receives the run: kInsBatch keys per lane, their first compare-and-swap in flight at once
+      for (int i0 = 0; i0 < nu; i0 += 32 * kInsBatch) {
         bool ins[kInsBatch];
         uint64_t fk[kInsBatch];
         unsigned long long old[kInsBatch];
 #pragma unroll
         for (int r = 0; r < kInsBatch; r++) {
           const int i = i0 + 32 * r + lane;
-          int xE = 0, xc = 0;
-          uint64_t xf = 0;
-          if (i < ns) {
-            const uint64_t kx = keys[i];
-            xE = key_E(kx);
-            xc = key_col(kx);
-            xf = fp_of(xc);
-          }
-          int pE = __shfl_up_sync(kFull, xE, 1);
-          uint64_t pf = __shfl_up_sync(kFull, xf, 1);
-          if (lane == 0) {
-            pE = carryE;
-            pf = carryF;
-          }
-          carryE = __shfl_sync(kFull, xE, 31);
-          carryF = __shfl_sync(kFull, xf, 31);
-          const bool keep = i < ns && (i == 0 || pE != xE || pf != xf);
-          const unsigned m = __ballot_sync(kFull, keep);
-          if (keep) {
-            const int o = nu + __popc(m & ((1u << lane) - 1u));
-            arena[top + o] = Node{xE, (int)(exps << 10) | xc, xf};
-            if (xf == kEmpty) has_empty = true;
-          }
-          nu += __popc(m);
-          ins[r] = keep && xf != kEmpty;
-          fk[r] = xf;
+          fk[r] = i < nu ? run[i].fp : kEmpty;
+          if (i < nu && fk[r] == kEmpty) has_empty = true;
+          ins[r] = i < nu && fk[r] != kEmpty;
         }
 #pragma unroll
         for (int r = 0; r < kInsBatch; r++)
@@ -440,14 +440,14 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
       }
       has_empty = __any_sync(kFull, has_empty);
       err = __reduce_or_sync(kFull, err);
-      __syncwarp();
       // ---- best, statistics, the new run
-      const int E0 = nu > 0 ? key_E(keys[0]) : INT32_MAX, col0 = nu > 0 ? key_col(keys[0]) : 0;
-      const uint64_t fp0 = nu > 0 ? fp_of(col0) : 0;
+      int E0 = INT32_MAX, i0 = 0;
+      uint64_t fp0 = 0;
+      if (nu > 0) warp_argmin(rE, rf, ri, E0, fp0, i0);
       if (nu > 0 && E0 < bestE) {
         bestE = E0;
         bestfp = fp0;
-        const int col = col0;
+        const int col = arena[i0].link & 1023;
         if (col < a.L)
           flip_bits(S.pbits, col, S.cbits);
         else
@@ -459,15 +459,15 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         u++;
       }
       if (nu > 0 && lane == 0) {  // push the run: sift up
-        RunHead h{E0, (int)top, fp0, (int)(top + nu), 0};
+        const RunHead nh{E0, i0, fp0, (int)(top + nu), (int)top};
         long long i = heap_n;
         while (i > 0) {
-          const long long p = (i - 1) >> 1;
-          if (!kless(h.E, h.fp, heap[p].E, heap[p].fp)) break;
-          heap[i] = heap[p];
-          i = p;
+          const long long pp = (i - 1) >> 1;
+          if (!kless(nh.E, nh.fp, heap[pp].E, heap[pp].fp)) break;
+          heap[i] = heap[pp];
+          i = pp;
         }
-        heap[i] = h;
+        heap[i] = nh;
       }
       if (nu > 0) heap_n++;
       top += nu;
@@ -525,13 +525,11 @@ int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uin
   a.best_E = best_E;
   a.stats = stats;
   // resident warps: as many slots as the memory budget allows, at most one per candidate
+  a.tab_words = 2 * ly.NG + (L + 1) / 2;
   const size_t per_slot = (size_t)a.arena_cap * sizeof(Node) + (size_t)a.heap_cap * sizeof(RunHead) +
-                          (size_t)a.max_exp * W * 8 + (8ull << a.H_log2);
-  int np2max = 1;  // a pop's survivors (at most width) are sorted over the next power of two
-  while (np2max < a.width) np2max <<= 1;
-  if (np2max > kSortN || cfg->T_r > kMaxTr) return LABS_ERR_INVALID_ARG;
-  a.smem_stride = (int)((sizeof(IndepSmem) + sizeof(uint64_t) * np2max + 15) & ~size_t(15));
-  const size_t smem = (size_t)a.smem_stride * kIWarps;
+                          (size_t)a.max_exp * W * 8 + (size_t)a.max_exp * a.tab_words * 4 + (8ull << a.H_log2);
+  if (cfg->T_r > kMaxTr) return LABS_ERR_INVALID_ARG;
+  const size_t smem = sizeof(IndepSmem) * kIWarps;
   if (cudaFuncSetAttribute(pq_indep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return LABS_ERR_CUDA;
   int per_sm = 0;
@@ -551,6 +549,7 @@ int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uin
   };
   const size_t oA = take(slots * (size_t)a.arena_cap * sizeof(Node)), oHp = take(slots * (size_t)a.heap_cap * sizeof(RunHead));
   const size_t oP = take(slots * (size_t)a.max_exp * W * 8), oH = take(slots * (8ull << a.H_log2));
+  const size_t oT = take(slots * (size_t)a.max_exp * a.tab_words * 4);
   const size_t oZ = take(8 * (size_t)L), oC = take(8);
   char* base = static_cast<char*>(ws_get(ctx, kWsPqIndep, off));
   if (!base) return LABS_ERR_NOMEM;
@@ -558,6 +557,7 @@ int launch_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uin
   a.heap = reinterpret_cast<RunHead*>(base + oHp);
   a.pivots = reinterpret_cast<uint64_t*>(base + oP);
   a.H = reinterpret_cast<uint64_t*>(base + oH);
+  a.tables = reinterpret_cast<uint32_t*>(base + oT);
   a.ztab = reinterpret_cast<uint64_t*>(base + oZ);
   a.counter = reinterpret_cast<unsigned long long*>(base + oC);
   indep_ztab_kernel<<<(L + 255) / 256, 256, 0, st>>>(reinterpret_cast<uint64_t*>(base + oZ), L);
