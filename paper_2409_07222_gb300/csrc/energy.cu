@@ -1,9 +1,12 @@
 // energy.cu -- labs_energy_batch: C_k and E = sum C_k^2 for a batch of bit-packed sequences
 // (Section 1 definitions; ENERGY in Algorithms 1 and 2).
 //
-// One warp per sequence: the 64-bit words are staged in shared memory as 32-bit words, lanes split
-// the lags, and each lag is a popcount of x XOR (x >> k) over ceil((L-k)/32) words.  The arithmetic
-// is integer popcount work (about (L-1) * L / 64 popc per sequence); 8 B per word in, 4 B out.
+// One warp per sequence, the sequence's W32 32-bit words held in registers by every lane.  Lane l takes
+// the lags k = 32 j + l (j = 0 .. W32 - 1): for a given j every lane's word offset is j and its bit shift
+// is l, so the loops over j and the words unroll at compile time (W32 is a template parameter) and each
+// 32 products cost one funnel shift, one XOR, one popcount and one add.  C_k = (L - k) - 2 d, where d
+// counts the disagreeing pairs (s_i != s_{i+k}, i < L - k): the popcounts run over whole words, and the
+// positions past L - k (where the shifted word is zero) are taken out with prefix popcounts.
 #include "labs_core.cuh"
 #include "labs_internal.h"
 
@@ -12,38 +15,68 @@ namespace {
 
 constexpr int kEnergyWarps = 8;
 
+template <int W32>
 __global__ void __launch_bounds__(32 * kEnergyWarps) energy_batch_kernel(const uint64_t* __restrict__ seqs, int L,
                                                                           int64_t n, int32_t* __restrict__ E_out,
                                                                           int32_t* __restrict__ C_out) {
-  __shared__ uint32_t bits_all[kEnergyWarps][kBitWords];
-  uint32_t* bits = bits_all[threadIdx.x >> 5];
+  __shared__ uint32_t bits_all[kEnergyWarps][W32 + 1];
+  __shared__ int pre_all[kEnergyWarps][W32 + 1];  // pre[m] = ones in words 0 .. m-1
+  uint32_t* sb = bits_all[threadIdx.x >> 5];
+  int* pre = pre_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const int W = (L + 63) >> 6;
-  const int W32 = (L + 31) >> 5;
   const int64_t warps_total = (int64_t)gridDim.x * kEnergyWarps;
   for (int64_t q = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); q < n; q += warps_total) {
     const uint64_t* src = seqs + q * W;
-    if (lane < kBitWords) {
-      uint32_t v = 0;
-      if (lane < W32) {
-        uint64_t x = src[lane >> 1];
-        v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
-        int rem = L - 32 * lane;
-        if (rem < 32) v &= (1u << rem) - 1u;
-      }
-      bits[lane] = v;
+    uint32_t v = 0;
+    if (lane < W32) {
+      const uint64_t x = src[lane >> 1];
+      v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+      const int rem = L - 32 * lane;
+      if (rem < 32) v &= (1u << rem) - 1u;
     }
+    // inclusive prefix of the words' popcounts over lanes 0 .. W32-1
+    int c1 = __popc(v);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, c1, o);
+      if (lane >= o) c1 += t;
+    }
+    if (lane <= W32) sb[lane] = lane < W32 ? v : 0u;
+    if (lane < W32) pre[lane + 1] = c1;
+    if (lane == 0) pre[0] = 0;
     __syncwarp();
+    uint32_t b[W32 + 1];
+#pragma unroll
+    for (int w = 0; w <= W32; w++) b[w] = sb[w];
     int e = 0;
-    for (int k = lane + 1; k < L; k += 32) {
-      int c = corr_lag(bits, L, k);
-      if (C_out) C_out[q * (L - 1) + (k - 1)] = c;
-      e += c * c;
+#pragma unroll
+    for (int j = 0; j < W32; j++) {
+      const int k = 32 * j + lane;
+      int d = 0;
+#pragma unroll
+      for (int w = 0; w + j < W32; w++) d += __popc(b[w] ^ __funnelshift_r(b[w + j], b[w + j + 1], lane));
+      if (k >= 1 && k < L) {
+        // the words cover positions [0, 32 (W32 - j)); past t = L - k the shifted word is zero, so
+        // the popcount also counted the ones of s there
+        const int t = L - k;
+        const int pt = pre[t >> 5] + __popc(sb[t >> 5] & ((1u << (t & 31)) - 1u));
+        d -= pre[W32 - j] - pt;
+        const int c = t - 2 * d;
+        if (C_out) C_out[q * (L - 1) + (k - 1)] = c;
+        e += c * c;
+      }
     }
     e = warp_sum_i32(e);
     if (lane == 0) E_out[q] = e;
     __syncwarp();
   }
+}
+
+template <int W32>
+void launch_energy_w(const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out, unsigned blocks,
+                     cudaStream_t st) {
+  energy_batch_kernel<W32><<<blocks, 32 * kEnergyWarps, 0, st>>>(seqs, L, n, E_out, C_out);
 }
 
 }  // namespace
@@ -54,7 +87,28 @@ int launch_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, i
   int64_t blocks = (n + kEnergyWarps - 1) / kEnergyWarps;
   int64_t cap = (int64_t)ctx->num_sms * 16;
   if (blocks > cap) blocks = cap;
-  energy_batch_kernel<<<(unsigned)blocks, 32 * kEnergyWarps, 0, st>>>(seqs, L, n, E_out, C_out);
+  const unsigned nb = (unsigned)blocks;
+  switch ((L + 31) >> 5) {
+    case 1: launch_energy_w<1>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 2: launch_energy_w<2>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 3: launch_energy_w<3>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 4: launch_energy_w<4>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 5: launch_energy_w<5>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 6: launch_energy_w<6>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 7: launch_energy_w<7>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 8: launch_energy_w<8>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 9: launch_energy_w<9>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 10: launch_energy_w<10>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 11: launch_energy_w<11>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 12: launch_energy_w<12>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 13: launch_energy_w<13>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 14: launch_energy_w<14>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 15: launch_energy_w<15>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 16: launch_energy_w<16>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 17: launch_energy_w<17>(seqs, L, n, E_out, C_out, nb, st); break;
+    case 18: launch_energy_w<18>(seqs, L, n, E_out, C_out, nb, st); break;
+    default: return LABS_ERR_INVALID_ARG;
+  }
   return cuda_status(cudaGetLastError());
 }
 
