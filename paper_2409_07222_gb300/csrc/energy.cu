@@ -1,13 +1,10 @@
 // energy.cu -- labs_energy_batch: C_k and E = sum C_k^2 for a batch of bit-packed sequences
 // (Section 1 definitions; ENERGY in Algorithms 1 and 2).
 //
-// One warp per sequence, the sequence's W32 32-bit words held in registers by every lane.  Lane l takes
-// the lags k = 32 j + l (j = 0 .. W32 - 1): for a given j every lane's word offset is j and its bit shift
-// is l, so the loops over j and the words unroll at compile time (W32 is a template parameter) and each
-// 32 products cost one funnel shift, one XOR, one popcount and one add.  C_k = (L - k) - 2 d, where d
-// counts the disagreeing pairs (s_i != s_{i+k}, i < L - k): the popcounts run over whole words, and the
-// positions past L - k (where the shifted word is zero) are taken out with prefix popcounts.
-#include "labs_core.cuh"
+// One warp per sequence, the sequence's W32 32-bit words held in registers by every lane
+// (energy_words.cuh: one funnel shift, XOR, popcount and add per 32 products).  8 B per word in,
+// 4 B out (plus the C_k when asked for).
+#include "energy_words.cuh"
 #include "labs_internal.h"
 
 namespace labsg {
@@ -20,7 +17,7 @@ __global__ void __launch_bounds__(32 * kEnergyWarps) energy_batch_kernel(const u
                                                                           int64_t n, int32_t* __restrict__ E_out,
                                                                           int32_t* __restrict__ C_out) {
   __shared__ uint32_t bits_all[kEnergyWarps][W32 + 1];
-  __shared__ int pre_all[kEnergyWarps][W32 + 1];  // pre[m] = ones in words 0 .. m-1
+  __shared__ int pre_all[kEnergyWarps][W32 + 1];
   uint32_t* sb = bits_all[threadIdx.x >> 5];
   int* pre = pre_all[threadIdx.x >> 5];
   const int lane = lane_id();
@@ -28,48 +25,20 @@ __global__ void __launch_bounds__(32 * kEnergyWarps) energy_batch_kernel(const u
   const int64_t warps_total = (int64_t)gridDim.x * kEnergyWarps;
   for (int64_t q = (int64_t)blockIdx.x * kEnergyWarps + (threadIdx.x >> 5); q < n; q += warps_total) {
     const uint64_t* src = seqs + q * W;
-    uint32_t v = 0;
-    if (lane < W32) {
-      const uint64_t x = src[lane >> 1];
-      v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
-      const int rem = L - 32 * lane;
-      if (rem < 32) v &= (1u << rem) - 1u;
-    }
-    // inclusive prefix of the words' popcounts over lanes 0 .. W32-1
-    int c1 = __popc(v);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, c1, o);
-      if (lane >= o) c1 += t;
-    }
-    if (lane <= W32) sb[lane] = lane < W32 ? v : 0u;
-    if (lane < W32) pre[lane + 1] = c1;
-    if (lane == 0) pre[0] = 0;
-    __syncwarp();
-    uint32_t b[W32 + 1];
-#pragma unroll
-    for (int w = 0; w <= W32; w++) b[w] = sb[w];
-    int e = 0;
-#pragma unroll
-    for (int j = 0; j < W32; j++) {
-      const int k = 32 * j + lane;
-      int d = 0;
-#pragma unroll
-      for (int w = 0; w + j < W32; w++) d += __popc(b[w] ^ __funnelshift_r(b[w + j], b[w + j + 1], lane));
-      if (k >= 1 && k < L) {
-        // the words cover positions [0, 32 (W32 - j)); past t = L - k the shifted word is zero, so
-        // the popcount also counted the ones of s there
-        const int t = L - k;
-        const int pt = pre[t >> 5] + __popc(sb[t >> 5] & ((1u << (t & 31)) - 1u));
-        d -= pre[W32 - j] - pt;
-        const int c = t - 2 * d;
-        if (C_out) C_out[q * (L - 1) + (k - 1)] = c;
-        e += c * c;
+    __syncwarp();  // the previous sequence's readers of sb are done
+    if (lane <= W32) {
+      uint32_t v = 0;
+      if (lane < W32) {
+        const uint64_t x = src[lane >> 1];
+        v = (lane & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+        const int rem = L - 32 * lane;
+        if (rem < 32) v &= (1u << rem) - 1u;
       }
+      sb[lane] = v;
     }
-    e = warp_sum_i32(e);
-    if (lane == 0) E_out[q] = e;
     __syncwarp();
+    const int e = energy_words<W32>(sb, L, pre, C_out ? C_out + q * (L - 1) : nullptr);
+    if (lane == 0) E_out[q] = e;
   }
 }
 

@@ -212,19 +212,29 @@ __device__ __forceinline__ int s_at(const ScanSmem& sm, const Layout& ly, int i)
 }
 
 // Byte windows from the packed bits (whole arrays, pads included).
-// Bytes of positions p .. p+3: byte e = s + 1 (0 or 2) for position p + e inside 1..L, else the pad 1;
-// rev: byte e holds position p + 3 - e.  Bits above L - 1 are zero in sm.bits.
-__device__ __forceinline__ uint32_t nibble_bytes(const ScanSmem& sm, int L, int p, bool rev) {
-  if (p > L || p + 3 < 1) return 0x01010101u;  // no position of the window inside 1..L
-  const int b = p - 1;  // bit index of position p: -3 <= b <= L - 1
+// Bytes of positions p, p+d, p+2d, p+3d (d = 1 or 2): byte e = s + 1 (0 or 2) for a position inside
+// 1..L, else the pad 1; rev: byte e holds position p + (3 - e) d.  Bits at and above L are zero in
+// sm.bits.  Every other bit of the window is taken for d = 2 (the positions of one parity class).
+__device__ __forceinline__ uint32_t window_bytes(const ScanSmem& sm, int L, int p, int d, bool rev) {
+  const int plast = p + 3 * d;
+  if (p > L || plast < 1) return 0x01010101u;  // no position of the window inside 1..L
+  const int b = p - 1;  // bit index of position p: -3d <= b <= L - 1
   uint32_t x;
   if (b >= 0) {
     const int wi = b >> 5;
-    x = __funnelshift_r(sm.bits[wi], wi + 1 < kBitWords ? sm.bits[wi + 1] : 0u, b & 31) & 0xFu;
+    x = __funnelshift_r(sm.bits[wi], wi + 1 < kBitWords ? sm.bits[wi + 1] : 0u, b & 31);
   } else {
-    x = (sm.bits[0] << (-b)) & 0xFu;
+    x = sm.bits[0] << (-b);
   }
-  const int lo = max(0, 1 - p), hi = max(0, p + 3 - L);  // invalid positions at the low / high end
+  if (d == 2) {  // bits 0, 2, 4, 6 -> bits 0..3
+    x &= 0x55u;
+    x = (x | (x >> 1)) & 0x33u;
+    x = (x | (x >> 2)) & 0x0Fu;
+  } else {
+    x &= 0xFu;
+  }
+  const int lo = p < 1 ? (1 - p + d - 1) / d : 0;          // invalid positions at the low end
+  const int hi = plast > L ? (plast - L + d - 1) / d : 0;  // and at the high end
   const uint32_t v = ((0xFu << lo) & (0xFu >> hi)) & 0xFu;
   uint32_t xv = x & v, pad = v ^ 0xFu;
   if (rev) {
@@ -235,39 +245,17 @@ __device__ __forceinline__ uint32_t nibble_bytes(const ScanSmem& sm, int L, int 
   return 2u * ((xv * 0x204081u) & 0x01010101u) + ((pad * 0x204081u) & 0x01010101u);
 }
 
-// lambda = 1: class index t is position t - kQOff + 1, so every word is four consecutive positions.
-__device__ inline void build_bytes_linear(ScanSmem& sm, const Layout& ly) {
-  for (int w = lane_id(); w < kDirBytes / 4; w += 32) {
-    sm.fwd[w] = nibble_bytes(sm, ly.L, 4 * w - kQOff + 1, false);
-    sm.bwd[w] = nibble_bytes(sm, ly.L, ly.Qr - 4 * w - kQOff + 1 - 3, true);
-  }
-  __syncwarp();
-}
-
+// The forward and reversed byte windows of every class: class index t is position q_pos(cls, t), i.e.
+// lambda (t - kQOff) + first position of the class, so every word is four positions lambda apart.
 __device__ inline void build_bytes(ScanSmem& sm, const Layout& ly) {
-  if (!ly.skew) {
-    build_bytes_linear(sm, ly);
-    return;
-  }
-  const int lane = lane_id();
   const int words_per_cls = (ly.skew ? kClassBytes : kDirBytes) / 4;
   for (int cls = 0; cls < ly.ncls; cls++) {
     uint32_t* F = sm.fwd + cls_words(cls);
     uint32_t* B = sm.bwd + cls_words(cls);
-    for (int w = lane; w < words_per_cls; w += 32) {
-      uint32_t fw = 0, bw = 0;
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        int t = 4 * w + e;
-        int i = q_pos(ly, cls, t);
-        uint32_t fb = (i >= 1 && i <= ly.L) ? (seq_bit(sm, i) ? 2u : 0u) : 1u;
-        int ib = q_pos(ly, cls, ly.Qr - t);
-        uint32_t bb = (ib >= 1 && ib <= ly.L) ? (seq_bit(sm, ib) ? 2u : 0u) : 1u;
-        fw |= fb << (8 * e);
-        bw |= bb << (8 * e);
-      }
-      F[w] = fw;
-      B[w] = bw;
+    const int first = q_pos(ly, cls, kQOff);  // position of class index kQOff
+    for (int w = lane_id(); w < words_per_cls; w += 32) {
+      F[w] = window_bytes(sm, ly.L, first + ly.lam * (4 * w - kQOff), ly.lam, false);
+      B[w] = window_bytes(sm, ly.L, first + ly.lam * (ly.Qr - 4 * w - 3 - kQOff), ly.lam, true);
     }
   }
   __syncwarp();

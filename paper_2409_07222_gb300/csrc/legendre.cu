@@ -4,9 +4,9 @@
 // chi(j) = +1 if j is a non-zero quadratic residue mod p, -1 otherwise (j = 0 included), with the exact
 // energy of each.  labs_legendre_family enumerates the parameter family on the host; the device builds
 // the sequences (one warp each: the non-zero squares k^2 mod p, k <= (p-1)/2, marked in a shared-memory
-// bitmap, then one bitmap test per position and ballots into words) and their energies like
-// labs_energy_batch.
-#include "labs_core.cuh"
+// bitmap, then one bitmap test per position and ballots into words) and their energies as in
+// labs_energy_batch (energy_words.cuh).
+#include "energy_words.cuh"
 #include "labs_internal.h"
 
 namespace labsg {
@@ -14,34 +14,48 @@ namespace {
 
 constexpr int kLegWarps = 8;
 
-__device__ __forceinline__ bool prime_dev(int v) {
-  if (v < 2) return false;
-  for (int d = 2; d * d <= v; d++)
-    if (v % d == 0) return false;
-  return true;
+// Primality of 0 .. 32 kPrimeWords - 1 as a bitmap, filled on the host and passed by value.
+constexpr int kPrimeWords = 19;  // covers every p <= L <= 576
+struct PrimeBits {
+  uint32_t w[kPrimeWords];
+};
+
+// x mod p for 0 <= x < 2^24, 2 <= p < 2^10, through a float reciprocal: the quotient estimate is off by at
+// most one either way, which the two corrections take out.
+__device__ __forceinline__ int mod_small(int x, int p, float rp) {
+  const int q = (int)((float)x * rp);
+  int r = x - q * p;
+  if (r < 0) r += p;
+  if (r >= p) r -= p;
+  return r;
 }
 
-
+// NW: 32-bit words of L bits.
+template <int NW>
 __global__ void __launch_bounds__(32 * kLegWarps) legendre_kernel(int L, const int32_t* __restrict__ params, int64_t n,
-                                                                 uint64_t* __restrict__ seqs, int32_t* __restrict__ E_out) {
+                                                                 uint64_t* __restrict__ seqs, int32_t* __restrict__ E_out,
+                                                                 const __grid_constant__ PrimeBits primes) {
+  __shared__ int pre_all[kLegWarps][kBitWords + 1];
   __shared__ uint32_t bits_all[kLegWarps][kBitWords];
   __shared__ uint32_t qr_all[kLegWarps][kBitWords];  // bit j: j is a non-zero square mod p
   uint32_t* bits = bits_all[threadIdx.x >> 5];
   uint32_t* qr = qr_all[threadIdx.x >> 5];
+  int* pre = pre_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const int W = (L + 63) >> 6;
   const int64_t warps_total = (int64_t)gridDim.x * kLegWarps;
   for (int64_t q = (int64_t)blockIdx.x * kLegWarps + (threadIdx.x >> 5); q < n; q += warps_total) {
     const int p = params[2 * q], off = params[2 * q + 1];
-    if (p < 2 || p > L || off < 0 || off >= p || !prime_dev(p)) {  // not a seed of this length: E = INT32_MAX
+    if (p < 2 || p > L || off < 0 || off >= p || !((primes.w[p >> 5] >> (p & 31)) & 1u)) {  // not a seed: E = INT32_MAX
       if (seqs && lane < W) seqs[q * W + lane] = 0;
       if (E_out && lane == 0) E_out[q] = INT32_MAX;
       continue;
     }
     if (lane < kBitWords) qr[lane] = 0u;
+    const float rp = __frcp_rn((float)p);
     __syncwarp();
     for (int k = lane + 1; 2 * k <= p - 1; k += 32) {  // the squares of 1..(p-1)/2 cover every residue
-      const int r = (k * k) % p;
+      const int r = mod_small(k * k, p, rp);
       atomicOr(&qr[r >> 5], 1u << (r & 31));
     }
     __syncwarp();
@@ -56,12 +70,7 @@ __global__ void __launch_bounds__(32 * kLegWarps) legendre_kernel(int L, const i
       if (j >= p) j -= p;
     }
     __syncwarp();
-    int e = 0;
-    for (int k = lane + 1; k < L; k += 32) {
-      const int c = corr_lag(bits, L, k);
-      e += c * c;
-    }
-    e = warp_sum_i32(e);
+    const int e = energy_words<NW>(bits, L, pre, nullptr);
     if (seqs && lane < W) seqs[q * W + lane] = (uint64_t)bits[2 * lane] | ((uint64_t)bits[2 * lane + 1] << 32);
     if (E_out && lane == 0) E_out[q] = e;
     __syncwarp();
@@ -101,7 +110,21 @@ int launch_legendre(labs_ctx* ctx, int L, const int32_t* params, int64_t n, uint
                     cudaStream_t st) {
   if (n == 0) return LABS_OK;
   const int64_t blocks = std::min<int64_t>((n + kLegWarps - 1) / kLegWarps, (int64_t)ctx->num_sms * 32);
-  legendre_kernel<<<(unsigned)blocks, 32 * kLegWarps, 0, st>>>(L, params, n, seqs, E_out);
+  const unsigned nb = (unsigned)blocks;
+  PrimeBits pb{};
+  for (int v = 0; v < 32 * kPrimeWords; v++)
+    if (is_prime(v)) pb.w[v >> 5] |= 1u << (v & 31);
+#define LABS_LEG_CASE(NWC)                                                             \
+  case NWC:                                                                          \
+    legendre_kernel<NWC><<<nb, 32 * kLegWarps, 0, st>>>(L, params, n, seqs, E_out, pb); \
+    break;
+  switch ((L + 31) >> 5) {
+    LABS_LEG_CASE(1) LABS_LEG_CASE(2) LABS_LEG_CASE(3) LABS_LEG_CASE(4) LABS_LEG_CASE(5) LABS_LEG_CASE(6)
+    LABS_LEG_CASE(7) LABS_LEG_CASE(8) LABS_LEG_CASE(9) LABS_LEG_CASE(10) LABS_LEG_CASE(11) LABS_LEG_CASE(12)
+    LABS_LEG_CASE(13) LABS_LEG_CASE(14) LABS_LEG_CASE(15) LABS_LEG_CASE(16) LABS_LEG_CASE(17) LABS_LEG_CASE(18)
+    default: return LABS_ERR_INVALID_ARG;
+  }
+#undef LABS_LEG_CASE
   return cuda_status(cudaGetLastError());
 }
 

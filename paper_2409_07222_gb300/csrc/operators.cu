@@ -4,25 +4,16 @@
 //
 // One warp per input sequence.  Lane w owns 32-bit word w of the sequence and of each variant: an append
 // sets bit L, a prepend shifts every word up by one bit, a removal clears the last bit or shifts down by
-// one.  Each variant's energy is then the Section 1 definition evaluated like labs_energy_batch (lanes
-// split the lags, one popcount per 32 products).  Six variants per input: 6 (L+-1)^2/64 popcounts.
-#include "labs_core.cuh"
+// one.  Each variant's energy is then the Section 1 definition evaluated as in labs_energy_batch
+// (energy_words.cuh: the variant held in registers, one popcount per 32 products).  Six variants per
+// input: about 6 (L+-1)^2/64 popcounts.
+#include "energy_words.cuh"
 #include "labs_internal.h"
 
 namespace labsg {
 namespace {
 
 constexpr int kOpWarps = 8;
-
-// Energy of the sequence in bits (length L, zero beyond), on every lane.
-__device__ __forceinline__ int bits_energy(const uint32_t* bits, int L) {
-  int e = 0;
-  for (int k = lane_id() + 1; k < L; k += 32) {
-    const int c = corr_lag(bits, L, k);
-    e += c * c;
-  }
-  return warp_sum_i32(e);
-}
 
 // Writes the variant in vbits (length Lv) as packed 64-bit words.
 __device__ __forceinline__ void store_words(const uint32_t* vbits, int Lv, uint64_t* dst) {
@@ -31,14 +22,18 @@ __device__ __forceinline__ void store_words(const uint32_t* vbits, int Lv, uint6
   if (lane < W) dst[lane] = (uint64_t)vbits[2 * lane] | ((uint64_t)vbits[2 * lane + 1] << 32);
 }
 
+// NW: 32-bit words of the longer variants (L + 1 bits), so every variant fits with a zero word after it.
+template <int NW>
 __global__ void __launch_bounds__(32 * kOpWarps) operators_kernel(const uint64_t* __restrict__ seqs, int L, int64_t n,
                                                                   uint64_t* __restrict__ grow, int32_t* __restrict__ E_grow,
                                                                   uint64_t* __restrict__ shrink,
                                                                   int32_t* __restrict__ E_shrink) {
   __shared__ uint32_t sb[kOpWarps][kBitWords];
   __shared__ uint32_t vb[kOpWarps][kBitWords];
+  __shared__ int pre_all[kOpWarps][kBitWords + 1];
   uint32_t* bits = sb[threadIdx.x >> 5];
   uint32_t* v = vb[threadIdx.x >> 5];
+  int* pre = pre_all[threadIdx.x >> 5];
   const int lane = lane_id();
   const int W = (L + 63) >> 6, Wg = (L + 64) >> 6, Ws = (L + 62) >> 6;
   const int W32 = (L + 31) >> 5;
@@ -69,7 +64,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) operators_kernel(const uint64_t
         v[lane] = w;
       }
       __syncwarp();
-      const int E = bits_energy(v, L + 1);
+      const int E = energy_words<NW>(v, L + 1, pre, nullptr);
       if (grow) store_words(v, L + 1, grow + (q * 4 + var) * Wg);
       if (E_grow && lane == 0) E_grow[q * 4 + var] = E;
       __syncwarp();
@@ -87,7 +82,7 @@ __global__ void __launch_bounds__(32 * kOpWarps) operators_kernel(const uint64_t
         v[lane] = w;
       }
       __syncwarp();
-      const int E = bits_energy(v, L - 1);
+      const int E = energy_words<NW>(v, L - 1, pre, nullptr);
       if (shrink) store_words(v, L - 1, shrink + (q * 2 + var) * Ws);
       if (E_shrink && lane == 0) E_shrink[q * 2 + var] = E;
       __syncwarp();
@@ -100,8 +95,19 @@ __global__ void __launch_bounds__(32 * kOpWarps) operators_kernel(const uint64_t
 int launch_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
                               uint64_t* shrink, int32_t* E_shrink, cudaStream_t st) {
   if (n == 0) return LABS_OK;
-  const int64_t blocks = std::min<int64_t>((n + kOpWarps - 1) / kOpWarps, (int64_t)ctx->num_sms * 32);
-  operators_kernel<<<(unsigned)blocks, 32 * kOpWarps, 0, st>>>(seqs, L, n, grow, E_grow, shrink, E_shrink);
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + kOpWarps - 1) / kOpWarps, (int64_t)ctx->num_sms * 32);
+#define LABS_OPS_CASE(NWC)                                                                                   \
+  case NWC:                                                                                                \
+    operators_kernel<NWC><<<blocks, 32 * kOpWarps, 0, st>>>(seqs, L, n, grow, E_grow, shrink, E_shrink); \
+    break;
+  switch ((L + 32) >> 5) {  // words of L + 1 bits
+    LABS_OPS_CASE(1) LABS_OPS_CASE(2) LABS_OPS_CASE(3) LABS_OPS_CASE(4) LABS_OPS_CASE(5) LABS_OPS_CASE(6)
+    LABS_OPS_CASE(7) LABS_OPS_CASE(8) LABS_OPS_CASE(9) LABS_OPS_CASE(10) LABS_OPS_CASE(11) LABS_OPS_CASE(12)
+    LABS_OPS_CASE(13) LABS_OPS_CASE(14) LABS_OPS_CASE(15) LABS_OPS_CASE(16) LABS_OPS_CASE(17) LABS_OPS_CASE(18)
+    LABS_OPS_CASE(19)
+    default: return LABS_ERR_INVALID_ARG;
+  }
+#undef LABS_OPS_CASE
   return cuda_status(cudaGetLastError());
 }
 

@@ -756,20 +756,40 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
     if (threadIdx.x < 2) split[threadIdx.x] = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, threadIdx.x ? o1 : o0);
     __syncthreads();
     const long long ra = split[0], rb = split[1], ua = o0 - ra, ub = o1 - rb;
-    for (long long o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
-      const long long a = merge_split_in(RE, Rfp, b.uE, b.ufp, o, max(ra, o - ub), min(rb, o - ua));
-      const long long ui = o - a;
-      const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
-      if (from_rest) {
-        b.PE[nxt][o] = RE[a];
-        b.Pfp[nxt][o] = Rfp[a];
-        for (int t = 0; t < b.W; t++) b.Pseq[nxt][o * b.W + t] = Rseq[a * b.W + t];
-      } else {
-        const int q = b.uidx[ui] / b.width, col = b.uidx[ui] % b.width;
-        b.PE[nxt][o] = b.uE[ui];
-        b.Pfp[nxt][o] = b.ufp[ui];
-        pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
-        ins += h_insert(b, b.ufp[ui]);
+    // (the tile loop runs every warp over 32 consecutive outputs at a time, so that the sequences, 8 B
+    // per word, are copied by the warp together: lane l moves word l mod W of output l / W, and so on)
+    for (long long ob = o0 + (threadIdx.x & ~31); ob < o1; ob += blockDim.x) {
+      const long long o = ob + lane_id();
+      int kind = 0, src = 0, col = 0;  // kind: 0 none, 1 open set entry src, 2 flip col of pivot src, 3 rotation
+      if (o < o1) {
+        const long long a = merge_split_in(RE, Rfp, b.uE, b.ufp, o, max(ra, o - ub), min(rb, o - ua));
+        const long long ui = o - a;
+        const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
+        if (from_rest) {
+          b.PE[nxt][o] = RE[a];
+          b.Pfp[nxt][o] = Rfp[a];
+          kind = 1;
+          src = (int)a;
+        } else {
+          const int q = b.uidx[ui] / b.width;
+          col = b.uidx[ui] % b.width;
+          b.PE[nxt][o] = b.uE[ui];
+          b.Pfp[nxt][o] = b.ufp[ui];
+          kind = col < b.L ? 2 : 3;
+          src = q;
+          if (kind == 3) pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
+          ins += h_insert(b, b.ufp[ui]);
+        }
+      }
+      for (int t = lane_id(); t < 32 * b.W; t += 32) {
+        const int oo = t / b.W, word = t - oo * b.W;
+        const int k2 = __shfl_sync(kFull, kind, oo), s2 = __shfl_sync(kFull, src, oo), c2 = __shfl_sync(kFull, col, oo);
+        if (k2 == 1) {
+          b.Pseq[nxt][(ob + oo) * b.W + word] = Rseq[(long long)s2 * b.W + word];
+        } else if (k2 == 2) {
+          const uint64_t wv = b.Pseq[cur][(size_t)s2 * b.W + word];
+          b.Pseq[nxt][(ob + oo) * b.W + word] = wv ^ (word == (c2 >> 6) ? 1ull << (c2 & 63) : 0ull);
+        }
       }
     }
   }
