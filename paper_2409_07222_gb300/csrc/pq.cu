@@ -734,9 +734,10 @@ __device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64
 }
 
 // Merge path in tiles: a block takes kMergeTile consecutive outputs and finds the tile's two ends by
-// full searches (two threads); each thread then finds its own output's source by a search inside the
-// tile's ranges only (log2 kMergeTile steps on data the tile shares), consecutive threads writing
-// consecutive outputs.
+// full searches (two threads); the tile's keys of both inputs (kMergeTile in all) are then staged in
+// shared memory, and each thread finds its own output's source by a search there.  Warps write 32
+// consecutive outputs at a time and copy their sequences together (lane l moves word l mod W of output
+// l / W, and so on), so every store is coalesced.
 constexpr int kMergeTile = 2048;
 
 __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
@@ -749,36 +750,56 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
   const uint64_t* Rfp = b.Pfp[cur] + nb;
   const uint64_t* Rseq = b.Pseq[cur] + nb * b.W;
   __shared__ long long split[2];
+  __shared__ int32_t sE[kMergeTile];   // the tile's open-set keys at [0, nr), survivor keys at [nr, nr + nu)
+  __shared__ uint64_t sF[kMergeTile];
   int ins = 0;
   for (long long o0 = (long long)blockIdx.x * kMergeTile; o0 < nOut; o0 += (long long)gridDim.x * kMergeTile) {
     const long long o1 = min(o0 + kMergeTile, nOut);
-    __syncthreads();  // the previous tile's ends are no longer read
+    __syncthreads();  // the previous tile's ends and keys are no longer read
     if (threadIdx.x < 2) split[threadIdx.x] = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, threadIdx.x ? o1 : o0);
     __syncthreads();
-    const long long ra = split[0], rb = split[1], ua = o0 - ra, ub = o1 - rb;
-    // (the tile loop runs every warp over 32 consecutive outputs at a time, so that the sequences, 8 B
-    // per word, are copied by the warp together: lane l moves word l mod W of output l / W, and so on)
+    const long long ra = split[0], ua = o0 - ra;
+    const int nr = (int)(split[1] - ra), nu = (int)(o1 - split[1] - ua);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      sE[i] = RE[ra + i];
+      sF[i] = Rfp[ra + i];
+    }
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+      sE[nr + i] = b.uE[ua + i];
+      sF[nr + i] = b.ufp[ua + i];
+    }
+    __syncthreads();
     for (long long ob = o0 + (threadIdx.x & ~31); ob < o1; ob += blockDim.x) {
       const long long o = ob + lane_id();
       int kind = 0, src = 0, col = 0;  // kind: 0 none, 1 open set entry src, 2 flip col of pivot src, 3 rotation
       if (o < o1) {
-        const long long a = merge_split_in(RE, Rfp, b.uE, b.ufp, o, max(ra, o - ub), min(rb, o - ua));
-        const long long ui = o - a;
-        const bool from_rest = a < nR && (ui >= nU || key_lt(RE[a], Rfp[a], b.uE[ui], b.ufp[ui]));
+        const int ol = (int)(o - o0);
+        int lo = max(0, ol - nu), hi = min(ol, nr);  // open-set entries among the tile's first ol outputs
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          const int uj = nr + ol - mid - 1;
+          if (key_lt(sE[mid], sF[mid], sE[uj], sF[uj]))
+            lo = mid + 1;
+          else
+            hi = mid;
+        }
+        const int al = lo, ul = ol - lo;
+        const bool from_rest = al < nr && (ul >= nu || key_lt(sE[al], sF[al], sE[nr + ul], sF[nr + ul]));
         if (from_rest) {
-          b.PE[nxt][o] = RE[a];
-          b.Pfp[nxt][o] = Rfp[a];
+          b.PE[nxt][o] = sE[al];
+          b.Pfp[nxt][o] = sF[al];
           kind = 1;
-          src = (int)a;
+          src = (int)(ra + al);
         } else {
+          const long long ui = ua + ul;
           const int q = b.uidx[ui] / b.width;
           col = b.uidx[ui] % b.width;
-          b.PE[nxt][o] = b.uE[ui];
-          b.Pfp[nxt][o] = b.ufp[ui];
+          b.PE[nxt][o] = sE[nr + ul];
+          b.Pfp[nxt][o] = sF[nr + ul];
           kind = col < b.L ? 2 : 3;
           src = q;
           if (kind == 3) pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
-          ins += h_insert(b, b.ufp[ui]);
+          ins += h_insert(b, sF[nr + ul]);
         }
       }
       for (int t = lane_id(); t < 32 * b.W; t += 32) {
