@@ -30,7 +30,6 @@ constexpr int kIWarps = 4;
 constexpr int kIM = 8;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kProbeLimit = 1 << 20;
-constexpr int kInsBatch = 16;  // visited-set inserts in flight per lane (a pop's run: <= 704 / 32 + 1)
 constexpr int kMaxTr = 64;    // rotations per side (the library's bound on T_r)
 
 struct Node {  // one queue record: 16 bytes
@@ -72,20 +71,10 @@ __device__ __forceinline__ bool kless(int Ea, uint64_t fa, int Eb, uint64_t fb) 
 }
 
 // Visited set of one slot (open addressing, linear probing); *err set on an exhausted probe sequence.
-// The first probe of several keys is issued by the caller, all at once, so that their latencies
-// overlap; these continue a key's probe sequence after a first slot that held another key.
+// The first compare-and-swap of several keys is issued by the caller, all at once, so that their
+// latencies overlap; the _from forms continue a key's probe sequence after a first slot that held
+// another key.
 __device__ __forceinline__ uint64_t hs_home(uint64_t fp, int log2) { return (fp * kGamma) >> (64 - log2); }
-__device__ __forceinline__ bool hs_contains_from(const uint64_t* H, int log2, uint64_t fp, uint64_t s, int* err) {
-  const uint64_t mask = (1ull << log2) - 1;
-  for (int it = 1; it < kProbeLimit; it++) {
-    s = (s + 1) & mask;
-    const uint64_t v = H[s];
-    if (v == fp) return true;
-    if (v == kEmpty) return false;
-  }
-  *err = 1;
-  return true;
-}
 __device__ __forceinline__ void hs_insert_from(uint64_t* H, int log2, uint64_t fp, uint64_t s, int* err) {
   const uint64_t mask = (1ull << log2) - 1;
   for (int it = 1; it < kProbeLimit; it++) {
@@ -96,19 +85,37 @@ __device__ __forceinline__ void hs_insert_from(uint64_t* H, int log2, uint64_t f
   }
   *err = 1;
 }
-__device__ __forceinline__ bool hs_contains(const uint64_t* H, int log2, uint64_t fp, bool has_empty, int* err) {
-  if (fp == kEmpty) return has_empty;
-  const uint64_t s = hs_home(fp, log2);
-  const uint64_t v = H[s];
-  if (v == fp) return true;
-  if (v == kEmpty) return false;
-  return hs_contains_from(H, log2, fp, s, err);
-}
 __device__ __forceinline__ void hs_insert(uint64_t* H, int log2, uint64_t fp, int* err) {
   const uint64_t s = hs_home(fp, log2);
   const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
   if (old == kEmpty || old == fp) return;
   hs_insert_from(H, log2, fp, s, err);
+}
+// Insert-if-absent, continuing after slot s (whose key was another one): true when fp was inserted.
+__device__ __forceinline__ bool hs_add_from(uint64_t* H, int log2, uint64_t fp, uint64_t s, int* err) {
+  const uint64_t mask = (1ull << log2) - 1;
+  for (int it = 1; it < kProbeLimit; it++) {
+    s = (s + 1) & mask;
+    const unsigned long long old =
+        atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
+    if (old == kEmpty) return true;
+    if (old == fp) return false;
+  }
+  *err = 1;
+  return false;
+}
+// Insert-if-absent (the key ~0 by the flag has_empty): true when fp was inserted.
+__device__ __forceinline__ bool hs_add(uint64_t* H, int log2, uint64_t fp, bool& has_empty, int* err) {
+  if (fp == kEmpty) {
+    const bool fresh = !has_empty;
+    has_empty = true;
+    return fresh;
+  }
+  const uint64_t s = hs_home(fp, log2);
+  const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&H[s]), (unsigned long long)kEmpty, fp);
+  if (old == kEmpty) return true;
+  if (old == fp) return false;
+  return hs_add_from(H, log2, fp, s, err);
 }
 
 // Left shift of rotation code c: c < Tr moves the first c + 1 elements to the end, c >= Tr the last
@@ -209,7 +216,6 @@ __device__ __forceinline__ void run_min(const Node* arena, int begin, int end, i
 // Per-warp shared memory.
 struct __align__(16) IndepSmem {
   ScanSmem s;
-  uint64_t rfp[2 * kMaxTr];   // fingerprints of the pivot's rotations (columns L ..)
   uint32_t pbits[kBitWords];  // the pivot
   uint32_t cbits[kBitWords];  // a child
   int16_t P[kMaxL];  // P_m of the pivot's neighbours
@@ -356,10 +362,14 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
             scan_tile<kIM, false>(sm, ly, cls, q0, acc);
           else
             scan_tile<kIM, true>(sm, ly, cls, q0, acc);
-          // the tile's Delta E and fingerprints, then the first visited-set probe of all of them at
-          // once (independent loads), then the rare longer probe sequences
+          // the tile's Delta E and fingerprints, then an insert-if-absent of each neighbour into the
+          // visited set, the first compare-and-swap of all of them in flight at once: a neighbour is a
+          // survivor when its key was absent.  Inserting while other neighbours are still tested changes
+          // none of their answers: their keys differ, and inserts only fill empty slots, which no probe
+          // sequence of a present key crosses.
           int dv[kIM], mv[kIM];
-          uint64_t fv[kIM], hv[kIM];
+          uint64_t fv[kIM];
+          unsigned long long hv[kIM];
 #pragma unroll
           for (int j = 0; j < kIM; j++) {
             const SlotInfo si = slot_info(ly, cls, q0 + j);
@@ -368,18 +378,24 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
             fv[j] = si.active ? pfp ^ a.ztab[si.m - 1] : kEmpty;
           }
 #pragma unroll
-          for (int j = 0; j < kIM; j++) hv[j] = (mv[j] && fv[j] != kEmpty) ? H[hs_home(fv[j], a.H_log2)] : kEmpty;
+          for (int j = 0; j < kIM; j++)
+            hv[j] = (mv[j] && fv[j] != kEmpty)
+                        ? atomicCAS(reinterpret_cast<unsigned long long*>(&H[hs_home(fv[j], a.H_log2)]),
+                                    (unsigned long long)kEmpty, fv[j])
+                        : (unsigned long long)kEmpty;
 #pragma unroll
           for (int j = 0; j < kIM; j++) {
             if (!mv[j]) continue;
-            bool seen;
-            if (fv[j] == kEmpty)
-              seen = has_empty;
-            else if (hv[j] == fv[j] || hv[j] == kEmpty)
-              seen = hv[j] == fv[j];
-            else
-              seen = hs_contains_from(H, a.H_log2, fv[j], hs_home(fv[j], a.H_log2), &err);
-            if (!seen) {
+            bool fresh;
+            if (fv[j] == kEmpty) {
+              fresh = !has_empty;
+              has_empty = true;
+            } else if (hv[j] == kEmpty || hv[j] == fv[j]) {
+              fresh = hv[j] == kEmpty;
+            } else {
+              fresh = hs_add_from(H, a.H_log2, fv[j], hs_home(fv[j], a.H_log2), &err);
+            }
+            if (fresh) {
               const int k = atomicAdd(&S.n_surv, 1);
               run[k] = Node{pE + dv[j], link0 | (mv[j] - 1), fv[j]};
               if (kless(pE + dv[j], fv[j], rE, rf)) {
@@ -391,19 +407,15 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
           }
         }
       }
-      __syncwarp();
-      // ---- the rotations: a rotation equal to a flip child or to an earlier rotation is dropped
+      has_empty = __any_sync(kFull, has_empty);
+      // ---- the rotations, after the flips: one equal to a flip child or to an earlier rotation finds
+      //      its key in the visited set (the same sequence; the smaller column is kept)
       for (int c = 0; c < 2 * a.Tr; c++) {
         rotate_bits(S.pbits, a.L, rshift(a.L, a.Tr, c), S.cbits);
         const int e = energy_bits(S.cbits, a.L);
         const uint64_t hf = fp_bits(S.cbits, a.L, a.ztab);
-        bool dup = false;
-        for (int j = lane; j < a.L; j += 32) dup |= (hf ^ pfp) == a.ztab[j];
-        for (int j = lane; j < c; j += 32) dup |= S.rfp[j] == hf;
-        dup = __any_sync(kFull, dup);
         if (lane == 0) {
-          S.rfp[c] = hf;
-          if (!dup && !hs_contains(H, a.H_log2, hf, has_empty, &err)) {
+          if (hs_add(H, a.H_log2, hf, has_empty, &err)) {
             const int k = S.n_surv++;
             run[k] = Node{e, link0 | (a.L + c), hf};
             if (kless(e, hf, rE, rf)) {
@@ -415,31 +427,9 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         }
         __syncwarp();
       }
-      err = __reduce_or_sync(kFull, err);
-      const int nu = S.n_surv;
-      // ---- H receives the run: kInsBatch keys per lane, their first compare-and-swap in flight at once
-      for (int i0 = 0; i0 < nu; i0 += 32 * kInsBatch) {
-        bool ins[kInsBatch];
-        uint64_t fk[kInsBatch];
-        unsigned long long old[kInsBatch];
-#pragma unroll
-        for (int r = 0; r < kInsBatch; r++) {
-          const int i = i0 + 32 * r + lane;
-          fk[r] = i < nu ? run[i].fp : kEmpty;
-          if (i < nu && fk[r] == kEmpty) has_empty = true;
-          ins[r] = i < nu && fk[r] != kEmpty;
-        }
-#pragma unroll
-        for (int r = 0; r < kInsBatch; r++)
-          old[r] = ins[r] ? atomicCAS(reinterpret_cast<unsigned long long*>(&H[hs_home(fk[r], a.H_log2)]),
-                                      (unsigned long long)kEmpty, fk[r])
-                          : (unsigned long long)kEmpty;
-#pragma unroll
-        for (int r = 0; r < kInsBatch; r++)
-          if (ins[r] && old[r] != kEmpty && old[r] != fk[r]) hs_insert_from(H, a.H_log2, fk[r], hs_home(fk[r], a.H_log2), &err);
-      }
       has_empty = __any_sync(kFull, has_empty);
       err = __reduce_or_sync(kFull, err);
+      const int nu = S.n_surv;
       // ---- best, statistics, the new run
       int E0 = INT32_MAX, i0 = 0;
       uint64_t fp0 = 0;
