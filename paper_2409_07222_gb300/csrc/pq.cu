@@ -6,8 +6,8 @@
 //   expand   -- one warp per popped node: its correlation table, the all-position dp4a scan and a
 //               visited-set lookup per neighbour, written to a dense [pop][position] survivor array;
 //   compact  -- stable compaction of the survivors (pop order, position);
-//   sort     -- stable LSD radix sort by the fingerprint's high 32 bits then the energy bytes (passes
-//               whose byte is the same in every key are skipped), then runs of equal (E', fp' >> 32)
+//   sort     -- stable LSD radix sort by the fingerprint's top 16 bits then the energy bytes (passes
+//               whose byte is the same in every key are skipped), then runs of equal (E', fp' >> 48)
 //               ordered by (fp', pop, pos) in place: order (E', fp', pop, pos);
 //   dedup    -- stable compaction keeping the first of equal (E', fp');
 //   best     -- strict improvement test on the smallest survivor;
@@ -358,16 +358,17 @@ __device__ __forceinline__ long long compact_n(const PqBufs& b) {
   return MODE == 0 ? b.st->n_dense : b.st->nS;
 }
 
-// Radix passes of the sort: 0..3 the bytes of fp >> 32, 4..7 the bytes of E (least significant first).
+// Radix passes of the sort: 0..1 the bytes of fp >> 48, 2..5 the bytes of E (least significant first).
 // Bit p of the mask is set when pass p runs; pass p reads buffer popc(mask below p) & 1.
 __device__ __forceinline__ unsigned sort_mask(const PqState* st) {
-  const unsigned vf = st->fph_or ^ st->fph_and, ve = st->e_or ^ st->e_and;
+  const unsigned vf = st->fph_or ^ st->fph_and, ve = st->e_or ^ st->e_and;  // fph: fp >> 32
   unsigned m = 0;
 #pragma unroll
-  for (int p = 0; p < 4; p++) {
-    if ((vf >> (8 * p)) & 255u) m |= 1u << p;
-    if ((ve >> (8 * p)) & 255u) m |= 1u << (p + 4);
-  }
+  for (int p = 0; p < 2; p++)
+    if ((vf >> (16 + 8 * p)) & 255u) m |= 1u << p;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+    if ((ve >> (8 * p)) & 255u) m |= 1u << (p + 2);
   return m;
 }
 __device__ __forceinline__ int sort_src(unsigned mask, int pass) { return __popc(mask & ((1u << pass) - 1u)) & 1; }
@@ -513,10 +514,10 @@ __global__ void __launch_bounds__(256) compact_scatter_kernel(PqBufs b) {
   }
 }
 
-// Radix digit of element e of buffer `src` at pass `pass` (0..3: bytes of fp >> 32, 4..7: energy bytes).
+// Radix digit of element e of buffer `src` at pass `pass` (0..1: bytes of fp >> 48, 2..5: energy bytes).
 __device__ __forceinline__ unsigned radix_digit(const PqBufs& b, int src, long long e, int pass) {
-  if (pass < 4) return (unsigned)(b.sfp[src][e] >> (32 + 8 * pass)) & 255u;
-  return ((unsigned)b.sE[src][e] >> (8 * (pass - 4))) & 255u;
+  if (pass < 2) return (unsigned)(b.sfp[src][e] >> (48 + 8 * pass)) & 255u;
+  return ((unsigned)b.sE[src][e] >> (8 * (pass - 2))) & 255u;
 }
 
 __global__ void __launch_bounds__(256) radix_hist_kernel(PqBufs b, int pass) {
@@ -663,8 +664,8 @@ __global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) 
   }
 }
 
-// After the radix passes the keys are ordered by (E, fp >> 32) and, within equal pairs, by input order
-// (pop, pos).  Each run of equal (E, fp >> 32) is put in (fp, pop, pos) order in place by the thread at
+// After the radix passes the keys are ordered by (E, fp >> 48) and, within equal pairs, by input order
+// (pop, pos).  Each run of equal (E, fp >> 48) is put in (fp, pop, pos) order in place by the thread at
 // its start (runs are disjoint; they are short, fingerprints being uniform 64-bit keys).
 __global__ void __launch_bounds__(256) sort_fixup_kernel(PqBufs b) {
   const long long n = b.st->nS;
@@ -674,11 +675,11 @@ __global__ void __launch_bounds__(256) sort_fixup_kernel(PqBufs b) {
   int32_t* ix = b.sidx[f];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < n; i += (long long)gridDim.x * blockDim.x) {
     const int Ei = E[i];
-    const unsigned hi = (unsigned)(fp[i] >> 32);
-    if (E[i + 1] != Ei || (unsigned)(fp[i + 1] >> 32) != hi) continue;
-    if (i > 0 && E[i - 1] == Ei && (unsigned)(fp[i - 1] >> 32) == hi) continue;
+    const unsigned hi = (unsigned)(fp[i] >> 48);
+    if (E[i + 1] != Ei || (unsigned)(fp[i + 1] >> 48) != hi) continue;
+    if (i > 0 && E[i - 1] == Ei && (unsigned)(fp[i - 1] >> 48) == hi) continue;
     long long j = i + 2;
-    while (j < n && E[j] == Ei && (unsigned)(fp[j] >> 32) == hi) j++;
+    while (j < n && E[j] == Ei && (unsigned)(fp[j] >> 48) == hi) j++;
     for (long long a = i + 1; a < j; a++) {  // insertion sort of [i, j) by (fp, index)
       const uint64_t kf = fp[a];
       const int32_t ki = ix[a];
@@ -933,7 +934,7 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
     issue_compact<0>(b, max_n, &dst->nS, s);
     const int nseg = (int)((256ll * nb + kSeg - 1) / kSeg);
-    for (int pass = 0; pass < 8; pass++) {
+    for (int pass = 0; pass < 6; pass++) {
       radix_hist_kernel<<<nb, 256, 0, s>>>(b, pass);
       seg_reduce_kernel<<<nseg, 256, 0, s>>>(b, pass);
       seg_scan_sums_kernel<<<1, 1024, 0, s>>>(b.bsum, nseg, b.st, pass);
