@@ -275,8 +275,9 @@ int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds,
  * (rotations included when T_r > 0).
  *   seeds [n][W] uint64, best_seqs [n][W] uint64, best_E [n] int32, stats [n] labs_pq_stats -- device.
  *   Memory: each resident warp holds max_expansions x (L + 2 T_r) x 16 B of queue records, 24 B per pop
- *   of run heads, 8 W B per pop of pivots and 2^H_log2 x 8 B of visited set; as many warps run as fit in
- *   max_workspace_bytes (0: 64 GiB) and the occupancy limit, the rest of the candidates wait for a warp.
+ *   of run heads, 8 W B per pop of pivots, about 4 L B per pop of pivot tables (C_k and P_m) and
+ *   2^H_log2 x 8 B of visited set; as many warps run as fit in max_workspace_bytes (0: 64 GiB) and the
+ *   occupancy limit, the rest of the candidates wait for a warp.
  * Errors: LABS_ERR_INVALID_ARG on a bad configuration; per candidate, stats.status = LABS_ERR_CAPACITY if
  * its visited set passed 3/4 load (raise H_log2).
  */
