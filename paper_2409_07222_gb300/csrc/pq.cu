@@ -734,8 +734,33 @@ __device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64
   return merge_split_in(RE, Rfp, UE, Ufp, o, max(0ll, o - nU), min(o, nR));
 }
 
-// Merge path in tiles: a block takes kMergeTile consecutive outputs and finds the tile's two ends by
-// full searches (two threads); the tile's keys of both inputs (kMergeTile in all) are then staged in
+// The same split found by the whole block (every thread calls it, gets the answer): each step tests
+// blockDim increasing points of the range at once, and the number that test true (a prefix, the
+// predicate being monotone) narrows the range by a factor of blockDim + 1 -- three steps for 2^22.
+__device__ long long block_merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
+                                       const uint64_t* Ufp, long long nU, long long o) {
+  long long lo = max(0ll, o - nU), hi = min(o, nR);
+  const long long nt = blockDim.x, t = threadIdx.x;
+  while (lo < hi) {  // the same on every thread
+    const long long span = hi - lo;
+    const bool dense = span <= nt;  // then the points are lo .. hi - 1 and one step ends the search
+    auto point = [&](long long k) { return dense ? lo + k : lo + (span * (k + 1)) / (nt + 1); };
+    const long long np = dense ? span : nt;
+    bool pred = false;
+    if (t < np) {
+      const long long mid = point(t), ui = o - mid - 1;
+      pred = key_lt(RE[mid], Rfp[mid], UE[ui], Ufp[ui]);
+    }
+    const long long c = __syncthreads_count(pred);
+    const long long nlo = c > 0 ? point(c - 1) + 1 : lo;
+    hi = c < np ? point(c) : hi;
+    lo = nlo;
+  }
+  return lo;
+}
+
+// Merge path in tiles: a block takes kMergeTile consecutive outputs and finds the tile's two ends
+// (block_merge_split); the tile's keys of both inputs (kMergeTile in all) are then staged in
 // shared memory, and each thread finds its own output's source by a search there.  Warps write 32
 // consecutive outputs at a time and copy their sequences together (lane l moves word l mod W of output
 // l / W, and so on), so every store is coalesced.
@@ -750,17 +775,16 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
   const int32_t* RE = b.PE[cur] + nb;
   const uint64_t* Rfp = b.Pfp[cur] + nb;
   const uint64_t* Rseq = b.Pseq[cur] + nb * b.W;
-  __shared__ long long split[2];
   __shared__ int32_t sE[kMergeTile];   // the tile's open-set keys at [0, nr), survivor keys at [nr, nr + nu)
   __shared__ uint64_t sF[kMergeTile];
   int ins = 0;
   for (long long o0 = (long long)blockIdx.x * kMergeTile; o0 < nOut; o0 += (long long)gridDim.x * kMergeTile) {
     const long long o1 = min(o0 + kMergeTile, nOut);
-    __syncthreads();  // the previous tile's ends and keys are no longer read
-    if (threadIdx.x < 2) split[threadIdx.x] = merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, threadIdx.x ? o1 : o0);
-    __syncthreads();
-    const long long ra = split[0], ua = o0 - ra;
-    const int nr = (int)(split[1] - ra), nu = (int)(o1 - split[1] - ua);
+    __syncthreads();  // the previous tile's keys are no longer read
+    const long long ra = block_merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o0);
+    const long long rb = block_merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o1);
+    const long long ua = o0 - ra;
+    const int nr = (int)(rb - ra), nu = (int)(o1 - rb - ua);
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
       sE[i] = RE[ra + i];
       sF[i] = Rfp[ra + i];
@@ -818,13 +842,16 @@ __global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
   h_count(b, ins);
 }
 
-__global__ void pq_round_end_kernel(PqBufs b) {
+// One block: the split of the merged output at the cap (how many open-set entries stayed) by the block
+// search, then the round's bookkeeping by thread 0.
+__global__ void __launch_bounds__(256) pq_round_end_kernel(PqBufs b) {
   PqState* st = b.st;
   if (st->b == 0) return;
   const int cur = st->cur;
   const long long nb = st->b, nR = st->nP - nb, nU = st->nU;
   const long long nOut = min(b.cap, nR + nU);
-  const long long a = merge_split(b.PE[cur] + nb, b.Pfp[cur] + nb, nR, b.uE, b.ufp, nU, nOut);
+  const long long a = block_merge_split(b.PE[cur] + nb, b.Pfp[cur] + nb, nR, b.uE, b.ufp, nU, nOut);
+  if (threadIdx.x != 0) return;
   st->admitted += nOut - a;
   st->evicted += nR - a;
   st->nP = nOut;
@@ -969,7 +996,7 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     sort_and_dedup((long long)cfg->B * width, cs);
     pq_best_kernel<<<1, 1, 0, cs>>>(b);
     pq_merge_kernel<<<merge_blocks, 256, 0, cs>>>(b);
-    pq_round_end_kernel<<<1, 1, 0, cs>>>(b);
+    pq_round_end_kernel<<<1, 256, 0, cs>>>(b);
   }
   cudaGraph_t round_graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &round_graph);
