@@ -90,3 +90,34 @@ def test_legendre_family_host_enumeration(lib):
         if len(want) > 1:
             short = np.zeros((1, 2), dtype=np.int32)
             assert f(L, r_lo, r_hi, t_max, short.ctypes.data, 1, ctypes.byref(n)) == 2  # LABS_ERR_CAPACITY
+
+
+def test_block_split_search_narrows_to_the_first_false():
+    """The merge's block-wide split search (every thread tests one of blockDim increasing points, the
+    count of true answers narrows the range) returns the first index where a monotone predicate is false,
+    the same answer as a binary search -- checked for ranges of every size up to a few blocks."""
+    import random
+    rng = random.Random(11)
+    nt = 256
+
+    def search(lo, hi, first_false):
+        steps = 0
+        while lo < hi:
+            span = hi - lo
+            dense = span <= nt
+            point = (lambda k: lo + k) if dense else (lambda k: lo + (span * (k + 1)) // (nt + 1))
+            np_ = span if dense else nt
+            c = sum(1 for t in range(np_) if point(t) < first_false)
+            nlo = point(c - 1) + 1 if c > 0 else lo
+            hi = point(c) if c < np_ else hi
+            lo = nlo
+            steps += 1
+        return lo, steps
+
+    for _ in range(300):
+        lo = rng.randrange(0, 1000)
+        hi = lo + rng.choice([0, 1, 2, 255, 256, 257, rng.randrange(0, 5000), rng.randrange(0, 1 << 22)])
+        ans = rng.randint(lo, hi)
+        got, steps = search(lo, hi, ans)
+        assert got == ans
+        assert steps <= 4

@@ -139,3 +139,56 @@ def test_fold_entry_split_without_divide():
                 assert all((e * magic) >> 16 == e // nt for e in range(33)), (L, skew, p, M, H, nt)
                 seen += 1
     assert seen > 1000
+
+
+def _window_bytes(bits, L, p, d, rev):
+    """Mirror of the device construction of one byte-window word: positions p, p+d, p+2d, p+3d."""
+    plast = p + 3 * d
+    if p > L or plast < 1:
+        return 0x01010101
+    b = p - 1
+    x = (bits >> b) if b >= 0 else (bits << (-b))
+    if d == 2:
+        x &= 0x55
+        x = (x | (x >> 1)) & 0x33
+        x = (x | (x >> 2)) & 0x0F
+    else:
+        x &= 0xF
+    lo = (1 - p + d - 1) // d if p < 1 else 0
+    hi = (plast - L + d - 1) // d if plast > L else 0
+    v = ((0xF << lo) & (0xF >> hi)) & 0xF
+    xv, pad = x & v, v ^ 0xF
+    if rev:
+        xv = int('{:04b}'.format(xv)[::-1], 2)
+        pad = int('{:04b}'.format(pad)[::-1], 2)
+    spread = lambda n: (n * 0x204081) & 0x01010101  # bit e -> bit 8e, no carries
+    return 2 * spread(xv) + spread(pad)
+
+
+def test_byte_windows_four_positions_per_word():
+    """Every word of the forward and reversed byte windows, built four positions at a time from the bits
+    (one shift, every other bit for the skew classes, a multiply spreading 4 bits to 4 bytes, the pads),
+    equals the per-byte definition: s + 1 inside 1..L, 1 outside."""
+    import random
+    rng = random.Random(5)
+    checked = 0
+    for L in list(range(3, 100)) + [449, 450, 451, 527, 575, 576]:
+        for skew in (0, 1):
+            if skew and L % 2 == 0:
+                continue
+            ly = layout(L, skew, min(24, (L - 1) // 2) if skew else 0, 16, 2)
+            if not ly["ok"]:
+                continue
+            bits = rng.getrandbits(L)
+            lam = 2 if skew else 1
+            byte = lambda i: (2 if (bits >> (i - 1)) & 1 else 0) if 1 <= i <= L else 1
+            words = (kClassBytes if skew else kDirBytes) // 4
+            for cls in range(2 if skew else 1):
+                first = q_pos(skew, cls, kQOff)
+                for w in range(words):
+                    f = _window_bytes(bits, L, first + lam * (4 * w - kQOff), lam, False)
+                    assert f == sum(byte(q_pos(skew, cls, 4 * w + e)) << (8 * e) for e in range(4)), (L, skew, cls, w)
+                    r = _window_bytes(bits, L, first + lam * (ly["Qr"] - 4 * w - 3 - kQOff), lam, True)
+                    assert r == sum(byte(q_pos(skew, cls, ly["Qr"] - 4 * w - e)) << (8 * e) for e in range(4)), (L, skew, cls, w)
+                    checked += 1
+    assert checked > 10000
