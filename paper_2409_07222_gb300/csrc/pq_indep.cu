@@ -11,13 +11,15 @@
 //             a new run is one sift-up.  Keys (E, fp) are distinct in a queue (the visited set admits a
 //             sequence once), so the pop order is that of the sequential definition;
 //   pivots -- the sequence of every popped node (a node is stored as its pivot and column, and is made
-//             into a sequence only when popped);
+//             into a sequence only when popped), with its correlation table and P_m, so that a flip
+//             child starts from its parent's by one O(L) update;
 //   H      -- the candidate's visited set (open addressing, cleared per candidate).
-// A pop scans all L single flips (the dp4a tiles of labs_core.cuh) and, with T_r > 0, the pivot's 2 T_r
-// rotations (a rotation equal to a flip child or to an earlier rotation is the same sequence and is
-// dropped, as the ordered dedup keeps the smaller column).  Memory per resident warp is about
-// max_expansions x (L + 2 T_r) x 16 B + 2^H_log2 x 8 B: HBM capacity, not bandwidth, is what this design
-// spends.
+// A pop scans all L single flips (the dp4a tiles of labs_core.cuh); each neighbour is one
+// insert-if-absent into H, a survivor being one whose key was absent.  With T_r > 0 the pivot's 2 T_r
+// rotations follow the flips (a rotation equal to a flip child or to an earlier rotation finds its key in
+// H and is dropped, as the ordered dedup keeps the smaller column).  Memory per resident warp is about
+// max_expansions x ((L + 2 T_r) x 16 B + 4 L B) + 2^H_log2 x 8 B: HBM capacity, not bandwidth, is what
+// this design spends.
 #include <algorithm>
 
 #include "labs_core.cuh"
@@ -30,7 +32,7 @@ constexpr int kIWarps = 4;
 constexpr int kIM = 8;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr int kProbeLimit = 1 << 20;
-constexpr int kMaxTr = 64;    // rotations per side (the library's bound on T_r)
+constexpr int kMaxTr = 64;  // rotations per side (the library's bound on T_r)
 
 struct Node {  // one queue record: 16 bytes
   int32_t E;
