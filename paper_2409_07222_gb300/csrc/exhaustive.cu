@@ -13,27 +13,24 @@ struct Seq128 {
   uint64_t lo, hi;
 };
 
-__device__ __forceinline__ int bit128(const Seq128& x, int i) {  // i 0-based
-  return i < 64 ? (int)((x.lo >> i) & 1u) : (int)((x.hi >> (i - 64)) & 1u);
-}
-
+// The sequence of free assignment a, built with word operations: the left half (positions 1..c) is the
+// prefix followed by the free elements (bit j of a set means element p+1+j is -1); the right half follows
+// from Eq. 2, position c + j mirroring c - j with the sign (-1)^j: the bit-reversed left half without the
+// centre, XOR an alternating mask.
 __device__ __forceinline__ Seq128 assignment_seq(int L, int p, uint64_t prefix, uint64_t a) {
-  const int c = (L + 1) / 2;
-  Seq128 x{0, 0};
-  for (int i = 1; i <= L; i++) {
-    int src = i, neg = 0;
-    if (i > c) {
-      src = 2 * c - i;
-      neg = (i - c) & 1;
-    }
-    int b = (src <= p) ? (int)((prefix >> (src - 1)) & 1u) : (int)(((a >> (src - p - 1)) & 1u) ^ 1u);
-    b ^= neg;
-    if (b) {
-      if (i <= 64)
-        x.lo |= 1ull << (i - 1);
-      else
-        x.hi |= 1ull << (i - 65);
-    }
+  const int c = (L + 1) / 2, k = c - 1, nfree = c - p;  // 1 <= k <= 63 for 3 <= L <= 127
+  const uint64_t pmask = p >= 64 ? ~0ull : (1ull << p) - 1ull;
+  const uint64_t fmask = nfree >= 64 ? ~0ull : (1ull << nfree) - 1ull;
+  const uint64_t left = (prefix & pmask) | (p < 64 ? ((~a & fmask) << p) : 0ull);
+  const uint64_t kmask = (1ull << k) - 1ull;
+  const uint64_t right = (__brevll(left & kmask) >> (64 - k)) ^ (0x5555555555555555ull & kmask);
+  Seq128 x;
+  if (c >= 64) {
+    x.lo = left;
+    x.hi = right;
+  } else {
+    x.lo = left | (right << c);
+    x.hi = right >> (64 - c);
   }
   return x;
 }

@@ -125,7 +125,8 @@ def test_threshold(lg, L, skew, p, n, rank):
 # ------------------------------------------------------------------------------------------------
 # labs_skew_exhaustive
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("L,p,prefix", [(5, 0, 0), (13, 0, 0), (21, 0, 0), (21, 3, 0b101), (37, 0, 0), (39, 6, 0b110011)])
+@pytest.mark.parametrize("L,p,prefix", [(5, 0, 0), (13, 0, 0), (21, 0, 0), (21, 3, 0b101), (37, 0, 0), (39, 6, 0b110011),
+                                         (101, 40, 0x9E3779B97F4A & ((1 << 40) - 1)), (127, 55, 0x5DEECE66D1234567 & ((1 << 55) - 1))])
 def test_exhaustive(lg, L, p, prefix):
     minE, cnt, arg, seq = lg.labs_skew_exhaustive(L, p, prefix)
     e_min, e_cnt, e_arg, e_seq = oracle.skew_exhaustive(L, p, prefix)
