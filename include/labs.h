@@ -20,6 +20,7 @@
 #ifndef LABS_H_
 #define LABS_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -402,6 +403,21 @@ int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t
  */
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream);
+
+/*
+ * Hexadecimal coding of sequences, as the paper prints its record sequences (Section 4, the paragraph
+ * on the results' table): each hex digit stands for four bits, most significant first; the first
+ * 4 * ceil(L/4) - L bits are zero pads and are dropped; of the remaining L bits the first is s_1 and a 0
+ * stands for -1.  Host-only (no context, no device work, nothing allocated); all pointers are HOST.
+ * labs_seq_to_hex -- writes the ceil(L/4) upper-case digits and a terminating NUL of the packed sequence
+ *   seq [W] uint64 (the library's layout) to hex.  LABS_ERR_CAPACITY if hex_size < ceil(L/4) + 1,
+ *   LABS_ERR_INVALID_ARG for L outside [1, 576] or a NULL pointer.
+ * labs_hex_to_seq -- parses exactly ceil(L/4) digits (either case) into seq [W] uint64 (bits above L-1
+ *   zero).  LABS_ERR_INVALID_ARG for another length, a character that is not a hex digit, a pad bit that
+ *   is not zero, L outside [1, 576] or a NULL pointer; seq is left unchanged on error.
+ */
+int labs_seq_to_hex(const uint64_t* seq, int L, char* hex, size_t hex_size);
+int labs_hex_to_seq(const char* hex, int L, uint64_t* seq);
 
 #ifdef __cplusplus
 }

@@ -231,6 +231,24 @@ def labs_sequence_operators(L, seqs, device=None):
     return grow, Eg, shrink, Es
 
 
+def labs_seq_to_hex(seq, L):
+    """The paper's hexadecimal coding (Section 4) of one packed sequence (host uint64/int64 array [W], or a
+    tensor, copied to the host): ceil(L/4) upper-case digits."""
+    w = np.ascontiguousarray(seq.cpu().numpy() if torch.is_tensor(seq) else seq).view(np.uint64).reshape(-1)
+    if w.size < words_per_seq(L):
+        raise ValueError("need %d words for L=%d" % (words_per_seq(L), L))
+    buf = ctypes.create_string_buffer((L + 3) // 4 + 1)
+    _lib.check(load().labs_seq_to_hex(w.ctypes.data_as(ctypes.c_void_p), L, buf, len(buf)), "labs_seq_to_hex")
+    return buf.value.decode()
+
+
+def labs_hex_to_seq(hex_digits, L):
+    """Packed host uint64 [W] of a sequence given in the paper's hexadecimal coding (Section 4)."""
+    out = np.zeros(words_per_seq(L), dtype=np.uint64)
+    _lib.check(load().labs_hex_to_seq(hex_digits.encode(), L, out.ctypes.data_as(ctypes.c_void_p)), "labs_hex_to_seq")
+    return out
+
+
 def labs_legendre_family(L, r_lo=0.20, r_hi=0.24, t_max=0.1):
     """Host enumeration of the Legendre seed family: int32 numpy [n, 2] of (prime p, rotation off)."""
     n = ctypes.c_int64()

@@ -104,20 +104,11 @@ int labs_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int 
   return labsg::launch_flip_deltas(ctx, seqs, C, L, n, skew, p, dE_out, (cudaStream_t)stream);
 }
 
-static int check_walk_shape(int L, int skew, int p, int n_prefix, const uint64_t* prefixes) {
-  if (L < 3 || L > LABS_MAX_L || (skew != 0 && skew != 1) || p < 0 || n_prefix < 1) return LABS_ERR_INVALID_ARG;
-  if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
-  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
-  if (p > 64 * LABS_MAX_W) return LABS_ERR_INVALID_ARG;
-  if (!prefixes || !aligned8(prefixes)) return LABS_ERR_INVALID_ARG;
-  return LABS_OK;
-}
-
 int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
                           uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out, int32_t* E_samples,
                           void* stream) {
   if (!ctx) return LABS_ERR_INVALID_ARG;
-  int s = check_walk_shape(L, skew, p, n_prefix, prefixes);
+  int s = labsg::check_walk_shape(L, skew, p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
   if (n_samples < 1 || rank < 0 || rank >= n_samples || !E_thr_out || !aligned4(E_thr_out) ||
       (E_samples && !aligned4(E_samples)))
@@ -132,7 +123,7 @@ int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t*
 int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
                      labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, void* stream) {
   if (!ctx || !cfg) return LABS_ERR_INVALID_ARG;
-  int s = check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
+  int s = labsg::check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
   if (cfg->n_walks < 0 || cfg->walk_begin < 0 || cfg->flip_budget < 0 || cfg->R < 1 || cfg->R > labsg::kMaxR ||
       cfg->bloom_log2 < 5 || cfg->bloom_log2 > 15 || cfg->bloom_k < 1 || cfg->bloom_k > 8)
@@ -190,7 +181,7 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
                         labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
                         void* stream) {
   if (!ctx || !cfg || chunk < 1 || !(lambda == lambda)) return LABS_ERR_INVALID_ARG;
-  int s = check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
+  int s = labsg::check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
   if (cfg->n_walks < 0 || cfg->walk_begin < 0 || cfg->flip_budget < 0 || cfg->R < 1 || cfg->R > labsg::kMaxR ||
       cfg->bloom_log2 < 5 || cfg->bloom_log2 > 15 || cfg->bloom_k < 1 || cfg->bloom_k > 8)
@@ -264,6 +255,52 @@ int labs_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint6
   int s = set_device(ctx);
   if (s != LABS_OK) return s;
   return labsg::launch_pq_independent(ctx, cfg, seeds, n, best_seqs, best_E, stats, (cudaStream_t)stream);
+}
+
+// Hexadecimal coding of a sequence (Section 4, the results' table): the hex digits, most significant
+// first, spell 4 * ceil(L/4) bits whose first 4 * ceil(L/4) - L are zero pads; the remaining bits are
+// s_1 .. s_L in order, a 1 standing for +1 and a 0 for -1.  Host memory only; no device work.
+int labs_seq_to_hex(const uint64_t* seq, int L, char* hex, size_t hex_size) {
+  if (!seq || !hex || L < 1 || L > LABS_MAX_L) return LABS_ERR_INVALID_ARG;
+  const int nd = (L + 3) / 4, pad = 4 * nd - L;
+  if (hex_size < (size_t)nd + 1) return LABS_ERR_CAPACITY;
+  for (int d = 0; d < nd; d++) {
+    int v = 0;
+    for (int b = 0; b < 4; b++) {
+      const int i = 4 * d + b - pad + 1;  // position carried by this bit; i < 1 is a pad
+      const int bit = i >= 1 ? (int)((seq[(i - 1) >> 6] >> ((i - 1) & 63)) & 1u) : 0;
+      v = 2 * v + bit;
+    }
+    hex[d] = "0123456789ABCDEF"[v];
+  }
+  hex[nd] = '\0';
+  return LABS_OK;
+}
+
+int labs_hex_to_seq(const char* hex, int L, uint64_t* seq) {
+  if (!hex || !seq || L < 1 || L > LABS_MAX_L) return LABS_ERR_INVALID_ARG;
+  const int nd = (L + 3) / 4, pad = 4 * nd - L;
+  if (std::strlen(hex) != (size_t)nd) return LABS_ERR_INVALID_ARG;
+  uint64_t w[LABS_MAX_W] = {0};
+  for (int d = 0; d < nd; d++) {
+    const char c = hex[d];
+    int v;
+    if (c >= '0' && c <= '9') v = c - '0';
+    else if (c >= 'A' && c <= 'F') v = c - 'A' + 10;
+    else if (c >= 'a' && c <= 'f') v = c - 'a' + 10;
+    else return LABS_ERR_INVALID_ARG;
+    for (int b = 0; b < 4; b++) {
+      const int bit = (v >> (3 - b)) & 1;
+      const int i = 4 * d + b - pad + 1;
+      if (i < 1) {
+        if (bit) return LABS_ERR_INVALID_ARG;  // a pad bit must be zero
+        continue;
+      }
+      w[(i - 1) >> 6] |= (uint64_t)bit << ((i - 1) & 63);
+    }
+  }
+  for (int t = 0; t < (L + 63) / 64; t++) seq[t] = w[t];
+  return LABS_OK;
 }
 
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,

@@ -45,6 +45,17 @@ int policy_length(const labs_policy* P);
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? LABS_OK : LABS_ERR_CUDA; }
 
+// Shape of a walk or a sieve sample (Algorithm 1): length, mode, prefix length (Eq. 3) and the prefix
+// array.  Shared by every entry point that draws walk starts, so their validation cannot drift apart.
+inline int check_walk_shape(int L, int skew, int p, int n_prefix, const uint64_t* prefixes) {
+  if (L < 3 || L > LABS_MAX_L || (skew != 0 && skew != 1) || p < 0 || n_prefix < 1) return LABS_ERR_INVALID_ARG;
+  if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
+  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
+  if (p > 64 * LABS_MAX_W) return LABS_ERR_INVALID_ARG;
+  if (!prefixes || (reinterpret_cast<uintptr_t>(prefixes) & 7u)) return LABS_ERR_INVALID_ARG;
+  return LABS_OK;
+}
+
 // Host launchers (argument validation happens in the C-ABI layer).
 int launch_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out,
                         cudaStream_t st);

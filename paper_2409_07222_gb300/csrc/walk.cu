@@ -1263,12 +1263,8 @@ extern "C" int labs_sample_threshold_noalloc(int L, int skew, int p, const uint6
                                              uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out,
                                              void* stream) {
   using namespace labsg;
-  if (L < 3 || L > LABS_MAX_L || (skew != 0 && skew != 1) || p < 0 || n_prefix < 1) return LABS_ERR_INVALID_ARG;
-  if (skew && (L % 2 == 0 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
-  if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
-  if (!prefixes || (reinterpret_cast<uintptr_t>(prefixes) & 7u) || !E_thr_out ||
-      (reinterpret_cast<uintptr_t>(E_thr_out) & 3u))
-    return LABS_ERR_INVALID_ARG;
+  if (check_walk_shape(L, skew, p, n_prefix, prefixes) != LABS_OK) return LABS_ERR_INVALID_ARG;
+  if (!E_thr_out || (reinterpret_cast<uintptr_t>(E_thr_out) & 3u)) return LABS_ERR_INVALID_ARG;
   if (n_samples < 1 || rank < 0 || rank >= n_samples) return LABS_ERR_INVALID_ARG;
   if (n_samples > kNoAllocMaxSamples) return LABS_ERR_CAPACITY;  // beyond the fixed scratch
   int device = 0, sms = 0;

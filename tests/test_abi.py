@@ -121,3 +121,58 @@ def test_block_split_search_narrows_to_the_first_false():
         got, steps = search(lo, hi, ans)
         assert got == ans
         assert steps <= 4
+
+
+def _hex_by_definition(s):
+    """The paper's coding (Section 4) written out: +1 -> 1, -1 -> 0, left-padded with zeros to a multiple of
+    four bits, read as one binary number, printed in hexadecimal with one digit per four bits."""
+    bits = "".join("1" if v == 1 else "0" for v in s)
+    nd = -(-len(s) // 4)
+    return format(int(bits, 2), "0%dX" % nd)
+
+
+def test_hex_coding_barker13(lib):
+    """Barker 13 (+ + + + + - - + + - + - +) is 1F35 in this coding: three zero pads, then 1111100110101."""
+    import numpy as np
+
+    import paper_2409_07222_gb300 as lg
+    from oracle import pm1_to_words
+
+    s = [1, 1, 1, 1, 1, -1, -1, 1, 1, -1, 1, -1, 1]
+    w = pm1_to_words(np.array(s, dtype=np.int8))
+    assert lg.labs_seq_to_hex(w, 13) == "1F35"
+    assert np.array_equal(lg.labs_hex_to_seq("1f35", 13), w)
+
+
+@pytest.mark.parametrize("L", [1, 2, 13, 63, 64, 65, 451, 487, 527, 576])
+def test_hex_coding_round_trip(lib, L):
+    """Every length class (pads of 0..3 bits, one to nine words): the library's digits equal the coding
+    written out from its definition, and parsing them returns the same words."""
+    import numpy as np
+
+    import paper_2409_07222_gb300 as lg
+    from oracle import pm1_to_words
+
+    rng = np.random.default_rng(L)
+    for _ in range(4):
+        s = rng.choice(np.array([-1, 1], dtype=np.int8), size=L)
+        w = pm1_to_words(s)
+        h = lg.labs_seq_to_hex(w, L)
+        assert h == _hex_by_definition(s)
+        assert np.array_equal(lg.labs_hex_to_seq(h, L), w)
+
+
+def test_hex_coding_rejects_bad_input(lib):
+    import ctypes
+
+    import numpy as np
+
+    w = np.zeros(1, dtype=np.uint64)
+    p = w.ctypes.data_as(ctypes.c_void_p)
+    assert lib.labs_hex_to_seq(b"1F35", 12, p) == 1      # 12 positions take 3 digits
+    assert lib.labs_hex_to_seq(b"3F35", 13, p) == 1      # a pad bit set (13 positions leave three pads)
+    assert lib.labs_hex_to_seq(b"1G35", 13, p) == 1      # not a hex digit
+    assert lib.labs_hex_to_seq(b"1F35", 0, p) == 1
+    buf = ctypes.create_string_buffer(4)
+    assert lib.labs_seq_to_hex(p, 13, buf, 4) == 2       # 4 digits need 5 bytes with the NUL
+    assert lib.labs_seq_to_hex(p, 13, buf, 5 - 1) == 2

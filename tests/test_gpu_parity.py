@@ -201,6 +201,19 @@ def test_walks_shard_offset_and_ragged_counts(lg):
     compare_walks(cand, ws, L, True, p, pre, 37, 150, 64, 3, 16, walk_begin=1000)
 
 
+def test_walks_l451_full_segments_through_restarts(lg):
+    """The bench's walk parameters in full: T_i = 1808 (Section 3's 8(L+1)/2), a 2^15-bit Bloom filter with
+    4 probes filled to its design load of 1,808 inserts per segment, and walks that run through two
+    restarts (4,000 flips = 1808 + 1808 + 384)."""
+    L, p = 451, 24
+    pre = inp.distinct_prefixes(256, p, seed=2409)
+    n, budget, T_i = 8, 4000, 1808
+    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16)
+    compare_walks(cand, ws, L, True, p, pre, n, budget, T_i, 2409, 16)
+    assert np.all(ws[:, 1] == 3)  # segments: two restarts per walk
+    assert st["flips"] == n * budget
+
+
 # ------------------------------------------------------------------------------------------------
 # labs_batched_search (mixed lengths, one persistent launch, CUDA graph, autotuner)
 # ------------------------------------------------------------------------------------------------
@@ -319,6 +332,39 @@ def test_pq_paper_lengths(lg, L):
     _pq_compare(lg, L, seeds, 4096, 64, 256)
 
 
+@pytest.mark.parametrize("L", [451, 487, 527])
+def test_pq_bench_sizes(lg, L):
+    """The step-2 bench's round shape at the three paper lengths: 4,096 seeds, B = 4,096 pops per round
+    (about 1.8-2.2 million neighbours scored per round), two rounds, and an open set of 2^13 that evicts
+    in the second round.  Best, energy and every statistic equal the oracle's."""
+    seeds = inp.random_words(4096, L, seed=4 * L)
+    if L % 2:
+        seeds = oracle.skew_fill(seeds, L)
+    _pq_compare(lg, L, seeds, 1 << 13, 4096, 2 * 4096, H_log2=20)
+
+
+def test_pq_visited_set_capacity_error(lg):
+    """A visited set too small for the run: the search stops at the first round that leaves H above 3/4
+    load and reports LABS_ERR_CAPACITY in its statistics (bounded probes, no hang).  Everything up to that
+    round equals the oracle's run with the same number of pops."""
+    from paper_2409_07222_gb300 import _lib
+
+    L = 31
+    seeds = inp.random_words(6, L, seed=8)
+    best, bE, st = lg.labs_pq_refine(L, dev_words(seeds), B=4, cap=1 << 12, H_log2=12, max_expansions=100_000)
+    torch.cuda.synchronize()
+    gs = lg.pq_stats_numpy(st)
+    assert int(gs["status"]) == _lib.LABS_ERR_CAPACITY
+    assert 4 * int(gs["h_size"]) > 3 * 4096 and int(gs["h_size"]) < 4096
+    exps = int(gs["expansions"])
+    assert 0 < exps < 100_000
+    ob, oE, ofp, ost = oracle.pq_refine(L, seeds, 1 << 12, 4, exps)
+    assert int(bE.cpu()[0]) == oE and int(gs["best_fp"]) == ofp
+    assert np.array_equal(host_words(best.cpu()), ob)
+    for k in ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements"):
+        assert int(gs[k]) == ost[k], (k, int(gs[k]), ost[k])
+
+
 # ------------------------------------------------------------------------------------------------
 # End-element sequence operators and the loop back into step 2 (Fig. 4)
 # ------------------------------------------------------------------------------------------------
@@ -428,3 +474,26 @@ def test_pq_independent_more_candidates_than_warps(lg):
     for q in (0, 17, 39):
         _, oE, _, _ = oracle.pq_refine(L, seeds[q:q + 1], 1 << 30, 1, 50)
         assert bE[q] == oE
+
+
+def test_pq_independent_visited_set_capacity_error(lg):
+    """Per-candidate visited sets of 2^10 slots: every candidate stops after the pop that takes its set
+    past 3/4 load, with LABS_ERR_CAPACITY in its own statistics, and its result equals the oracle's run with
+    the same number of pops."""
+    from paper_2409_07222_gb300 import _lib
+
+    L, n = 31, 5
+    seeds = inp.random_words(n, L, seed=12)
+    best, bE, st = lg.labs_pq_independent(L, dev_words(seeds), max_expansions=5000, H_log2=10)
+    torch.cuda.synchronize()
+    best = host_words(best.cpu()).reshape(n, -1)
+    bE = bE.cpu().numpy()
+    stn = st.cpu().numpy().view(lg.PQ_STATS_DTYPE).reshape(n)
+    for q in range(n):
+        assert int(stn[q]["status"]) == _lib.LABS_ERR_CAPACITY, q
+        assert 4 * int(stn[q]["h_size"]) > 3 * 1024 and int(stn[q]["h_size"]) < 1024
+        exps = int(stn[q]["expansions"])
+        ob, oE, ofp, ost = oracle.pq_refine(L, seeds[q:q + 1], 1 << 30, 1, exps)
+        assert bE[q] == oE and np.array_equal(best[q], ob) and int(stn[q]["best_fp"]) == ofp, q
+        for k in ("expansions", "survivors", "h_size", "improvements"):
+            assert int(stn[q][k]) == ost[k], (q, k, int(stn[q][k]), ost[k])

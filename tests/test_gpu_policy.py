@@ -60,17 +60,21 @@ def _close(got, exp, tol=1e-3):
 
 @pytest.mark.parametrize("L,n", [(13, 5), (64, 3), (200, 130), (451, 2), (576, 3)])
 def test_forward_matches_oracle(lg, L, n):
-    """The tensor-core inference path against the oracle evaluated with the same BF16 weights and with
-    the convolution outputs rounded to BF16 where the device stores them: what remains is FP32 summation
-    order (and the rare activation that lands on the other side of a BF16 rounding boundary).  Sizes span
-    one to five 128-position tiles per sample, a ragged last tile and two 128-sample dense tiles."""
+    """The tensor-core inference path against the plain fp64 forward of the network at the same
+    BF16-rounded weights, activations unrounded.  The device stores the three convolution outputs as BF16
+    (8-bit significand, relative rounding error at most 2^-9 each), so the bound is the BF16-mode
+    tolerance, 2e-2 of the largest |logit|.  A second, tighter check evaluates the oracle with those three
+    stored activations rounded to BF16 as well: what remains is FP32 summation order, within 2e-3.  Sizes
+    span one to five 128-position tiles per sample, a ragged last tile and two 128-sample dense tiles."""
     flat, q = _params(L, 3)
     w, x = _batch(L, n, 7)
     pol = lg.Policy(L)
     pol.set_params(flat)
     got = pol.forward(torch.from_numpy(w.view(np.int64)).cuda()).cpu().numpy()
-    exp, _ = opol.forward(q, x, act_bf16=True)
-    assert _close(got, exp, tol=2e-3), float(np.max(np.abs(got - exp)) / np.max(np.abs(exp)))
+    exp, _ = opol.forward(q, x)
+    assert _close(got, exp, tol=2e-2), float(np.max(np.abs(got - exp)) / np.max(np.abs(exp)))
+    exp_stored, _ = opol.forward(q, x, act_bf16=True)
+    assert _close(got, exp_stored, tol=2e-3), float(np.max(np.abs(got - exp_stored)) / np.max(np.abs(exp_stored)))
 
 
 def test_forward_chunks_and_batch_independence(lg):

@@ -475,6 +475,118 @@ def test_pq_batch_invariants():
     assert st_big["admitted"] + 8 == st_big["h_size"]
 
 
+_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def _sm64_py(key, i):
+    """Output i of SplitMix64 started at `key` (Steele, Lea & Flood 2014), written out in Python."""
+    z = (key + (i + 1) * _GAMMA) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def _zobrist_py(L):
+    key = _sm64_py(_sm64_py(_sm64_py(0, 0x5A0B), L), 0)
+    return [None] + [_sm64_py(key, i - 1) for i in range(1, L + 1)]
+
+
+def _batch_pq(L, seeds_pm1, cap, B, max_exp, T_u=0, T_r=0):
+    """Algorithm 2 in its batch-synchronous reading, restated with Python lists and sets: every round
+    pops the b smallest (E, fp) keys, scores every flip child (and, with T_r, every rotation) that is not
+    in H from scratch, orders the children by (E, fp, pop, position) keeping the first of each (E, fp),
+    improves the best on a strict E decrease, then keeps the cap smallest of (rest of the queue u children)
+    and puts exactly the admitted children into H.  Energies by numpy, fingerprints as XOR of Zobrist keys
+    computed from the SplitMix64 definition -- nothing shared with the C oracle."""
+    Z = _zobrist_py(L)
+
+    def fp_of(s):
+        f = 0
+        for i, v in enumerate(s, 1):
+            if v == -1:
+                f ^= Z[i]
+        return f
+
+    seen = {}
+    for s in seeds_pm1:
+        s = tuple(int(v) for v in s)
+        seen[(np_energy(list(s)), fp_of(s))] = s
+    P = sorted((k[0], k[1], v) for k, v in seen.items())[:cap]
+    H = {fp for _, fp, _ in P}
+    best = P[0]
+    st = dict(expansions=0, rounds=0, survivors=0, admitted=0, evicted=0, improvements=0)
+    u, stop = 0, 0
+    while True:
+        if st["expansions"] >= max_exp:
+            stop = 1
+            break
+        if not P:
+            stop = 2
+            break
+        if T_u > 0 and u >= T_u:
+            stop = 3
+            break
+        b = min(B, len(P), max_exp - st["expansions"])
+        popped, rest = P[:b], P[b:]
+        children = []
+        for pop, (_, _, s) in enumerate(popped):
+            kids = [(i, s[:i - 1] + (-s[i - 1],) + s[i:]) for i in range(1, L + 1)]
+            kids += [(L + r, s[r:] + s[:r]) for r in range(1, T_r + 1)]               # first r to the end
+            kids += [(L + T_r + r, s[-r:] + s[:-r]) for r in range(1, T_r + 1)]       # last r to the start
+            for pos, c in kids:
+                f = fp_of(c)
+                if f not in H:
+                    children.append((np_energy(list(c)), f, pop, pos, c))
+        children.sort(key=lambda t: t[:4])
+        uniq, keys = [], set()
+        for t in children:
+            if (t[0], t[1]) not in keys:
+                keys.add((t[0], t[1]))
+                uniq.append(t)
+        st["survivors"] += len(uniq)
+        if uniq and uniq[0][0] < best[0]:
+            best = (uniq[0][0], uniq[0][1], uniq[0][4])
+            st["improvements"] += 1
+            u = 0
+        else:
+            u += b
+        merged = sorted([(E, f, s, False) for E, f, s in rest] + [(E, f, c, True) for E, f, _, _, c in uniq],
+                        key=lambda t: (t[0], t[1]))[:cap]
+        new = [t for t in merged if t[3]]
+        H |= {t[1] for t in new}
+        st["admitted"] += len(new)
+        st["evicted"] += len(rest) - (len(merged) - len(new))
+        P = [(E, f, s) for E, f, s, _ in merged]
+        st["expansions"] += b
+        st["rounds"] += 1
+    st["h_size"] = len(H)
+    st["stop_reason"] = stop
+    return best, st
+
+
+@pytest.mark.parametrize("L,n_seeds,cap,B,max_exp,T_u,T_r", [
+    (15, 6, 10, 4, 80, 0, 0),      # a cap that evicts every round
+    (21, 9, 25, 7, 140, 30, 0),    # T_u stop
+    (13, 5, 9, 5, 100, 0, 2),      # rotations with eviction
+    (6, 4, 8, 3, 10_000, 0, 0),    # the queue runs empty (every state of L = 6 visited)
+    (17, 12, 4, 16, 90, 0, 1),     # B above the cap, more seeds than the cap
+])
+def test_pq_batch_path_equals_restatement(L, n_seeds, cap, B, max_exp, T_u, T_r):
+    """The oracle's B > 1 / finite-cap path (eviction, survivors, admitted, evicted, H size) equals the
+    independent restatement of the batch round: best key and sequence and all eight counters."""
+    seeds = inp.random_words(n_seeds, L, seed=500 + L)
+    seeds = np.concatenate([seeds, seeds[:1]])  # a duplicate seed is kept once
+    best_w, best_E, best_fp, st = oracle.pq_refine(L, seeds, cap=cap, B=B, max_expansions=max_exp, T_u=T_u, T_r=T_r)
+    (eE, efp, es), est = _batch_pq(L, oracle.words_to_pm1(seeds, L), cap, B, max_exp, T_u=T_u, T_r=T_r)
+    assert (best_E, best_fp) == (eE, efp)
+    assert tuple(int(v) for v in oracle.words_to_pm1(best_w[None], L)[0]) == es
+    for k in ("expansions", "rounds", "survivors", "admitted", "evicted", "h_size", "improvements", "stop_reason"):
+        assert st[k] == est[k], (k, st[k], est[k])
+    if cap < 20 and max_exp < 1000:
+        assert st["evicted"] > 0
+
+
 # --------------------------------------------------------------------------------------------
 # End-element sequence operators (Fig. 4 loop back into step 2)
 # --------------------------------------------------------------------------------------------

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import labs_inputs as inp
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,6 +38,17 @@ def test_noalloc_matches_threshold_on_two_calls(lg):
         exp = lg.labs_sample_threshold(L, skew, p, pre, seed, n, rank)
         torch.cuda.synchronize()
         assert int(got.cpu()[0]) == int(exp.cpu()[0]), (L, n, rank)
+
+
+def test_noalloc_matches_the_oracle(lg):
+    """The sieve bound of the fixed-scratch entry point equals the oracle's nearest-rank sample bound
+    directly (not only through the allocating entry point), on a sample the oracle finishes in seconds."""
+    for L, skew, p, seed, n, rank in [(451, True, 24, 2409, 20_000, 19), (101, True, 8, 7, 5_000, 4_999),
+                                      (64, False, 5, 3, 3_001, 1_500)]:
+        pre = inp.distinct_prefixes(16, p, seed=seed)
+        got = lg.labs_sample_threshold_noalloc(L, skew, p, pre, seed, n, rank)
+        torch.cuda.synchronize()
+        assert int(got.cpu()[0]) == oracle.threshold(L, skew, p, pre, seed, n, rank), (L, n, rank)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lg):
