@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
     ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre",
-                             "exhaustive", "energy", "deltas"],
+                             "exhaustive", "energy", "deltas", "peaks"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
                          "network: the proposal network's inference alone; operators: the end-element operators; "
@@ -178,8 +178,10 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": walks * flips / value * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": W1["L"], "p": W1["p"], "walks": W1["n_walks"],
-                       "flips_per_walk": W1["flip_budget"]},
+            "config": {"workload": WORKLOAD, "L": W1["L"], "p": W1["p"], "walks_timed": walks,
+                       "flips_per_walk_timed": flips,
+                       "sample": "each step times %d walks x %d flips of the 65,536 x 10^5 workload (walk ids 0..%d)"
+                                 % (walks, flips, walks - 1)},
             "cpu_baseline": res, "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -312,6 +314,31 @@ def run_pq(args, ws, rank, local):
             "roofline": {"bound": "alu", "achieved": terms / t / 1e9, "peak": peak, "unit": "Gop/s",
                          "frac": terms / t / 1e9 / peak, "traffic": None,
                          "work": "per expansion L(L-1) neighbour-lag multiply-adds (whole step timed, host-driven)"}}
+    print(json.dumps(line))
+    return 0
+
+
+def issue_peaks(local):
+    """Measured lane-instructions per SM clock of each instruction class (labs_measure_issue_rates) and the
+    chip peaks they imply at the maximum SM clock (SMS x rate x 2070 MHz)."""
+    import paper_2409_07222_gb300 as lg
+
+    rates = lg.labs_measure_issue_rates(local)
+    return {"lanes_per_clk_per_sm": rates,
+            "peak_Gops_at_max_clock": {k: SMS * v * SM_MAX_MHZ * 1e6 / 1e9 for k, v in rates.items()}}
+
+
+def run_peaks(args, ws, rank, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    clocks = ClockSampler(local)
+    pk = issue_peaks(local)
+    clk = clocks.stop()
+    line = {"metric": "issue rate", "unit": "lane-instructions per SM clock", "n_gpus": 1,
+            "config": {"workload": "issue_rate_probe", "threads_per_sm": 1024, "chains_per_thread": 16,
+                       "sms": SMS},
+            "clocks": clk, **pk}
     print(json.dumps(line))
     return 0
 
@@ -720,6 +747,8 @@ def main():
         return run_network(args, ws, rank, local)
     if args.workload == "learned":
         return run_learned(args, ws, rank, local)
+    if args.workload == "peaks":
+        return run_peaks(args, ws, rank, local)
 
     import torch
 
@@ -735,6 +764,7 @@ def main():
 
     L, p, R = W1["L"], W1["p"], W1["R"]
     n_walks, budget = args.walks, args.flips
+    rates = issue_peaks(local)["lanes_per_clk_per_sm"] if rank == 0 else None  # before any timing
     pre_h = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"])
     pre = torch.from_numpy(pre_h.view(np.int64)).to(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -807,6 +837,15 @@ def main():
                "h2d_bytes_per_step": int(pre_h.nbytes),
                "d2h_bytes_per_step": int(n_walks * R * 96 + 48)}
 
+    # the only exchange of sharded step 1: every rank's sieved candidates reduced to the 4,096 step-2 seeds
+    # (host merge after the timed region; N = 1 does the same reduction locally)
+    from paper_2409_07222_gb300.merge import merge_across_ranks
+
+    t0 = time.perf_counter()
+    cand_h = lg.candidates_numpy(out, n_walks, R)
+    seeds = merge_across_ranks(cand_h, inp.STEP2["n_seeds"])
+    merge_ms = (time.perf_counter() - t0) * 1e3
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -827,12 +866,22 @@ def main():
                    "parallelism": "walks sharded by rank" if ws > 1 else "single GPU"},
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
+        "candidate_merge": {"seeds": int(len(seeds)), "best_E": int(seeds["E"][0]) if len(seeds) else None,
+                            "ms": merge_ms, "ranks": ws,
+                            "what": "K = 4,096 smallest distinct (E, fp) over all ranks' candidates, host merge "
+                                    "after the timed region"},
         "clocks": clk,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
                      "traffic": traffic_per_launch(n_walks),
                      "kernel": "walk_kernel", "walk_kernel_ms": walk_s * 1e3,
                      "work": "%d neighbour-lag terms per flip (202 free x 225 even lags), one int32 multiply-add "
-                             "each; peak = 152 SMs x 128 lanes x 2070 MHz" % terms_per_flip(L, p)},
+                             "each; peak = 152 SMs x 128 lanes x 2070 MHz (issue slots)" % terms_per_flip(L, p),
+                     "measured_lanes_per_clk_per_sm": rates,
+                     "dp4a_pipe": {"peak": SMS * rates["DP4A"] * 4 * SM_MAX_MHZ * 1e6 / 1e9,
+                                   "frac": achieved / (SMS * rates["DP4A"] * 4 * SM_MAX_MHZ * 1e6 / 1e9),
+                                   "unit": "Gop/s",
+                                   "basis": "measured DP4A lane rate x 4 multiply-adds per DP4A x 152 SMs x "
+                                            "2070 MHz: the ceiling of a scan made of DP4A alone"}},
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_walks, args.cpu_flips)

@@ -419,6 +419,17 @@ int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* 
 int labs_seq_to_hex(const uint64_t* seq, int L, char* hex, size_t hex_size);
 int labs_hex_to_seq(const char* hex, int L, uint64_t* seq);
 
+/*
+ * labs_measure_issue_rates -- measurement support for the rooflines (the paper has no counterpart): the
+ * sustained issue rate of nine instruction classes on `device`, in lane-instructions per SM clock,
+ * written to rates[0..8] (HOST doubles) in the order IADD (add.s32), LOP3, SHF (funnel shift), IMAD
+ * (mad.lo.s32), DP4A, POPC, PRMT, FFMA (fma.rn.f32), DP2A.  Each class runs alone: one 1024-thread block
+ * per SM, 16 independent chains per thread, timed in SM clocks with clock64(); the median over the SMs.
+ * Synchronises the device; allocates and frees a few hundred bytes of device memory.
+ * Errors: LABS_ERR_INVALID_ARG for a bad device or n_rates < 9, LABS_ERR_CUDA / LABS_ERR_NOMEM.
+ */
+int labs_measure_issue_rates(int device, double* rates, int n_rates);
+
 #ifdef __cplusplus
 }
 #endif

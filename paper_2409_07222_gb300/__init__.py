@@ -249,6 +249,18 @@ def labs_hex_to_seq(hex_digits, L):
     return out
 
 
+ISSUE_RATE_CLASSES = ("IADD", "LOP3", "SHF", "IMAD", "DP4A", "POPC", "PRMT", "FFMA", "DP2A")
+
+
+def labs_measure_issue_rates(device=None):
+    """Measured lane-instructions per SM clock of each class in ISSUE_RATE_CLASSES (dict)."""
+    dev = _device(device)
+    out = np.zeros(len(ISSUE_RATE_CLASSES), dtype=np.float64)
+    _lib.check(load().labs_measure_issue_rates(dev.index, out.ctypes.data_as(ctypes.c_void_p), len(out)),
+               "labs_measure_issue_rates")
+    return dict(zip(ISSUE_RATE_CLASSES, (float(v) for v in out)))
+
+
 def labs_legendre_family(L, r_lo=0.20, r_hi=0.24, t_max=0.1):
     """Host enumeration of the Legendre seed family: int32 numpy [n, 2] of (prime p, rotation off)."""
     n = ctypes.c_int64()

@@ -51,6 +51,7 @@ SIGNATURES = {
     "labs_policy_train_step": (_ci, [_P, _P, _P, _P, _i64, _ci, _ci, ctypes.c_float, _P, _P, _P]),
     "labs_seq_to_hex": (_ci, [_P, _ci, ctypes.c_char_p, ctypes.c_size_t]),
     "labs_hex_to_seq": (_ci, [ctypes.c_char_p, _ci, _P]),
+    "labs_measure_issue_rates": (_ci, [_ci, _P, _ci]),
 }
 
 

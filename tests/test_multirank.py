@@ -33,6 +33,13 @@ def _rank_main(rank, world, port, out_dir):
     cand, st = oracle.walk_search(L, True, p, pre, count, 400, 60, seed=11, R=4, walk_begin=begin)
     gathered = [None] * world
     dist.all_gather_object(gathered, (begin, cand.tobytes(), st.tobytes()))
+    from paper_2409_07222_gb300.merge import merge_across_ranks
+
+    top = merge_across_ranks(cand, 9)
+    if rank == 0:
+        np.save(os.path.join(out_dir, "top.npy"), top)
+    else:
+        assert top is None
     t, u = bench.reduce_over_ranks(10.0 + rank, 100 * (rank + 1), "cpu")
     np.save(os.path.join(out_dir, "rank%d.npy" % rank), np.array([t, u], dtype=np.float64))
     if rank == 0:
@@ -61,6 +68,29 @@ def test_two_ranks_shard_walks_and_reduce(tmp_path):
     for r in range(2):
         t, u = np.load(tmp_path / ("rank%d.npy" % r))
         assert t == 11.0 and u == 300  # slowest rank's time, all ranks' work
+    # the merged step-2 seeds equal the K best distinct states of the single-process run
+    from paper_2409_07222_gb300.merge import topk_candidates
+
+    top = np.load(tmp_path / "top.npy")
+    want = topk_candidates(cand, 9)
+    assert top.tobytes() == want.tobytes()
+    assert len(np.unique(top["fp"])) == len(top) and np.all(np.diff(top["E"]) >= 0)
+
+
+def test_topk_keeps_first_record_of_each_state():
+    """K smallest distinct (E, fp), first (walk, step) record of each, empty slots dropped -- written out
+    on a hand-made record set."""
+    sys.path.insert(0, ROOT)
+    from paper_2409_07222_gb300 import CANDIDATE_DTYPE
+    from paper_2409_07222_gb300.merge import topk_candidates
+
+    rows = [(5, 3, 9, 11), (5, 1, 4, 11), (2, 7, 1, 20), (5, 0, 8, 10), (2**31 - 1, 0, 0, 2**64 - 1), (9, 2, 2, 1)]
+    c = np.zeros(len(rows), dtype=CANDIDATE_DTYPE)
+    for i, (E, w, st, fp) in enumerate(rows):
+        c[i]["E"], c[i]["walk"], c[i]["step"], c[i]["fp"] = E, w, st, fp
+    got = topk_candidates(c, 3)
+    assert [(int(r["E"]), int(r["fp"]), int(r["walk"]), int(r["step"])) for r in got] == \
+        [(2, 20, 7, 1), (5, 10, 0, 8), (5, 11, 1, 4)]
 
 
 def test_single_process_reduction_is_identity():
