@@ -135,14 +135,16 @@ def labs_sample_threshold_noalloc(L, skew, p, prefixes, seed, n_samples, rank, d
 
 def make_walk_cfg(L, skew=True, p=0, n_walks=1, flip_budget=1000, T_i=0, seed=0, R=16, bloom_log2=15, bloom_k=4,
                   E_thr=INT32_MAX, n_thresh_samples=0, thresh_rank=0, E_target=INT32_MIN, walk_begin=0, tile_m=0,
-                  warps_per_cta=0, E_thr_dev=None):
-    """labs_walk_cfg; E_thr_dev (a device int32 tensor) makes the walk read its sieve bound from it."""
+                  warps_per_cta=0, E_thr_dev=None, lanes_per_walk=0):
+    """labs_walk_cfg; E_thr_dev (a device int32 tensor) makes the walk read its sieve bound from it;
+    lanes_per_walk 32 / 16 fixes one walk per warp / per half-warp (0: the library chooses)."""
     cfg = WalkCfg()
     cfg.L, cfg.skew, cfg.p, cfg.T_i = L, int(bool(skew)), p, T_i
     cfg.n_walks, cfg.walk_begin, cfg.flip_budget, cfg.seed = n_walks, walk_begin, flip_budget, seed
     cfg.R, cfg.bloom_log2, cfg.bloom_k, cfg.E_thr = R, bloom_log2, bloom_k, E_thr
     cfg.n_thresh_samples, cfg.thresh_rank = n_thresh_samples, thresh_rank
     cfg.E_target, cfg.tile_m, cfg.warps_per_cta = E_target, tile_m, warps_per_cta
+    cfg.lanes_per_walk = lanes_per_walk
     cfg.E_thr_dev = E_thr_dev.data_ptr() if E_thr_dev is not None else None
     return cfg
 

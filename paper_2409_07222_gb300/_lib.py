@@ -64,7 +64,7 @@ class WalkCfg(ctypes.Structure):
         ("seed", _u64),
         ("R", _i32), ("bloom_log2", _i32), ("bloom_k", _i32), ("E_thr", _i32),
         ("n_thresh_samples", _i64), ("thresh_rank", _i64),
-        ("E_target", _i32), ("tile_m", _i32), ("warps_per_cta", _i32), ("reserved", _i32),
+        ("E_target", _i32), ("tile_m", _i32), ("warps_per_cta", _i32), ("lanes_per_walk", _i32),
         ("E_thr_dev", _P),
     ]
 

@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(32 * kFdWarps) flip_deltas_kernel(const uint64
     } else {
       build_table(sm, ly);
     }
-    const bool fast = pack_c8(sm);
-    const int SC = table_sum(sm);
+    const bool fast = pack_c8(sm, ly);
+    const int SC = table_sum(sm, ly);
     build_bytes(sm, ly);
     p_all(sm, ly, xb_all[threadIdx.x >> 5], rb_all[threadIdx.x >> 5], Pm);
     int32_t* out = dE + q * L;

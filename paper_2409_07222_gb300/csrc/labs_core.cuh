@@ -86,6 +86,53 @@ __device__ __forceinline__ uint64_t warp_xor_u64(uint64_t v) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// Lane groups: GL consecutive lanes (GL = 32: the whole warp; GL = 16: either half) own one walk or one
+// sequence.  Every synchronising primitive names the group's own lanes only, so the two halves of a
+// warp may hold different walks and diverge safely; shuffles use width GL, so source lanes are
+// group-relative.
+// ------------------------------------------------------------------------------------------------
+template <int GL>
+__device__ __forceinline__ int glane() {
+  return (int)(threadIdx.x & (GL - 1));
+}
+template <int GL>
+__device__ __forceinline__ int gbase() {  // first lane of the group inside the warp
+  return (int)(threadIdx.x & 31 & ~(GL - 1));
+}
+template <int GL>
+__device__ __forceinline__ unsigned gmask() {
+  if (GL == 32) return kFull;
+  return ((1u << (GL & 31)) - 1u) << gbase<GL>();
+}
+template <int GL>
+__device__ __forceinline__ int gsum(int v) { return __reduce_add_sync(gmask<GL>(), v); }
+template <int GL>
+__device__ __forceinline__ int gmin(int v) { return __reduce_min_sync(gmask<GL>(), v); }
+template <int GL>
+__device__ __forceinline__ int gmax(int v) { return __reduce_max_sync(gmask<GL>(), v); }
+template <int GL>
+__device__ __forceinline__ unsigned gminu(unsigned v) { return __reduce_min_sync(gmask<GL>(), v); }
+// group-relative ballot: bit j is group lane j
+template <int GL>
+__device__ __forceinline__ unsigned gballot(bool p) { return __ballot_sync(gmask<GL>(), p) >> gbase<GL>(); }
+template <int GL>
+__device__ __forceinline__ bool gall(bool p) { return __all_sync(gmask<GL>(), p); }
+template <int GL>
+__device__ __forceinline__ bool gany(bool p) { return __any_sync(gmask<GL>(), p); }
+template <int GL>
+__device__ __forceinline__ void gsync() { __syncwarp(gmask<GL>()); }
+template <int GL, class T>
+__device__ __forceinline__ T gshfl(T v, int src) { return __shfl_sync(gmask<GL>(), v, src, GL); }
+template <int GL, class T>
+__device__ __forceinline__ T gshfl_xor(T v, int o) { return __shfl_xor_sync(gmask<GL>(), v, o, GL); }
+template <int GL>
+__device__ __forceinline__ uint64_t gxor_u64(uint64_t v) {
+#pragma unroll
+  for (int o = GL / 2; o > 0; o >>= 1) v ^= gshfl_xor<GL>(v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Layout of one walk for (L, skew, p, M).  Identical on every lane (pure function of its inputs).
 // ------------------------------------------------------------------------------------------------
 struct Layout {
@@ -103,10 +150,12 @@ struct Layout {
   // error n * (magic * tasks - 2^16) stays below 32 * tasks < 2^16), so a lane splits a class's tasks
   // without a divide
   int fold_magic[2];
+  int cw;  // 32-bit words per class in the byte-window arrays (class `cls` starts at word cls * cw)
+  int cl;  // correlation-table entries kept (C16 / C8 lengths): > G, a multiple of 8, zero beyond G
 };
 
 // word offset of class `cls` inside the fwd/bwd arrays (class 1 exists only for skew walks)
-__host__ __device__ __forceinline__ int cls_words(int cls) { return cls * (kClassBytes / 4); }
+__host__ __device__ __forceinline__ int cls_words(const Layout& ly, int cls) { return cls * ly.cw; }
 
 // class and class index of position i (1-based)
 __host__ __device__ __forceinline__ int pos_cls(const Layout& ly, int i) { return ly.skew ? (i & 1) : 0; }
@@ -171,9 +220,34 @@ __host__ __device__ inline bool make_layout(Layout& ly, int L, int skew, int p, 
   int cap = skew ? kClassBytes : kDirBytes;
   int need_f = qmax_end + 4 * ly.NGend + 8;
   int need_b = ly.Qr + 4 * ly.NGend + 8;
+  ly.cw = cap / 4;
+  ly.cl = kCLen;
   // the walk's P bookkeeping reads class index 2q - q_f <= 2 * qmax_end
   return (H == 1 || H == 2) && M % 4 == 0 && need_f < cap && need_b < cap && 2 * qmax_end < cap &&
          4 * ly.NGend <= kCLen && L >= 2 && L <= kMaxL;
+}
+
+// Shrinks a valid layout's arrays to what its length needs (the walk kernels size their shared-memory
+// slabs per launch with it): class arrays of the smallest multiple of 16 bytes above every window, the
+// P bookkeeping's index 2 qmax_end and the class itself, and a table of the smallest multiple of 8
+// entries above G and 4 NGend (its last entry, always zero, stands in for a missing pair term).
+__host__ __device__ inline void compact_layout(Layout& ly) {
+  int qmax_end = 0;
+  for (int cls = 0; cls < ly.ncls; cls++)
+    if (ly.ntiles[cls] > 0) {
+      const int end = ly.tile_first[cls] + ly.ntiles[cls] * ly.M - 1;
+      if (end > qmax_end) qmax_end = end;
+    }
+  int need = qmax_end + 4 * ly.NGend + 8;
+  const int need_b = ly.Qr + 4 * ly.NGend + 8;
+  if (need_b > need) need = need_b;
+  if (2 * qmax_end + 1 > need) need = 2 * qmax_end + 1;
+  const int n_cls = ly.skew ? (ly.L + 1) / 2 : ly.L;  // class indices kQOff .. kQOff + n_cls - 1 hold positions
+  if (kQOff + n_cls + 1 > need) need = kQOff + n_cls + 1;
+  ly.cw = (need + 15) / 16 * 4;
+  int cl = 4 * ly.NGend;
+  if (ly.G + 1 > cl) cl = ly.G + 1;
+  ly.cl = (cl + 7) / 8 * 8;
 }
 
 // Tile tau -> (class, first class index).
@@ -188,7 +262,10 @@ __device__ __forceinline__ void tile_of(const Layout& ly, int tau, int& cls, int
 }
 
 // ------------------------------------------------------------------------------------------------
-// Shared-memory slab of one warp
+// Shared-memory slab of one walk.  ScanSmem is the fixed-size form (every length up to 576); the walk
+// kernels carve slabs sized for their launch's lengths out of dynamic shared memory and address them
+// through a ScanView with the same members.  Class `cls` of fwd/bwd starts at word cls * ly.cw; the
+// tables hold ly.cl entries.
 // ------------------------------------------------------------------------------------------------
 struct __align__(16) ScanSmem {
   uint32_t fwd[kDirBytes / 4];
@@ -198,16 +275,30 @@ struct __align__(16) ScanSmem {
   uint32_t bits[kBitWords];
 };
 
-__device__ __forceinline__ int seq_bit(const ScanSmem& sm, int i) { return (sm.bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1; }
+struct ScanView {
+  uint32_t* fwd;
+  uint32_t* bwd;
+  int16_t* C16;
+  int8_t* C8;
+  uint32_t* bits;
+};
 
-__device__ __forceinline__ int fwd_byte(const ScanSmem& sm, const Layout& ly, int cls, int q) {
-  return reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(cls))[q];
+template <class S>
+__device__ __forceinline__ int seq_bit(const S& sm, int i) {
+  return (sm.bits[(i - 1) >> 5] >> ((i - 1) & 31)) & 1;
 }
-__device__ __forceinline__ int bwd_byte(const ScanSmem& sm, const Layout& ly, int cls, int t) {
-  return reinterpret_cast<const uint8_t*>(sm.bwd + cls_words(cls))[t];
+
+template <class S>
+__device__ __forceinline__ int fwd_byte(const S& sm, const Layout& ly, int cls, int q) {
+  return reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(ly, cls))[q];
+}
+template <class S>
+__device__ __forceinline__ int bwd_byte(const S& sm, const Layout& ly, int cls, int t) {
+  return reinterpret_cast<const uint8_t*>(sm.bwd + cls_words(ly, cls))[t];
 }
 // s_i in {-1, +1} read from the forward byte array
-__device__ __forceinline__ int s_at(const ScanSmem& sm, const Layout& ly, int i) {
+template <class S>
+__device__ __forceinline__ int s_at(const S& sm, const Layout& ly, int i) {
   return fwd_byte(sm, ly, pos_cls(ly, i), pos_q(ly, i)) - 1;
 }
 
@@ -215,7 +306,8 @@ __device__ __forceinline__ int s_at(const ScanSmem& sm, const Layout& ly, int i)
 // Bytes of positions p, p+d, p+2d, p+3d (d = 1 or 2): byte e = s + 1 (0 or 2) for a position inside
 // 1..L, else the pad 1; rev: byte e holds position p + (3 - e) d.  Bits at and above L are zero in
 // sm.bits.  Every other bit of the window is taken for d = 2 (the positions of one parity class).
-__device__ __forceinline__ uint32_t window_bytes(const ScanSmem& sm, int L, int p, int d, bool rev) {
+template <class S>
+__device__ __forceinline__ uint32_t window_bytes(const S& sm, int L, int p, int d, bool rev) {
   const int plast = p + 3 * d;
   if (p > L || plast < 1) return 0x01010101u;  // no position of the window inside 1..L
   const int b = p - 1;  // bit index of position p: -3d <= b <= L - 1
@@ -247,18 +339,19 @@ __device__ __forceinline__ uint32_t window_bytes(const ScanSmem& sm, int L, int 
 
 // The forward and reversed byte windows of every class: class index t is position q_pos(cls, t), i.e.
 // lambda (t - kQOff) + first position of the class, so every word is four positions lambda apart.
-__device__ inline void build_bytes(ScanSmem& sm, const Layout& ly) {
-  const int words_per_cls = (ly.skew ? kClassBytes : kDirBytes) / 4;
+template <int GL = 32, class S>
+__device__ inline void build_bytes(S& sm, const Layout& ly) {
+  const int words_per_cls = ly.cw;
   for (int cls = 0; cls < ly.ncls; cls++) {
-    uint32_t* F = sm.fwd + cls_words(cls);
-    uint32_t* B = sm.bwd + cls_words(cls);
+    uint32_t* F = sm.fwd + cls_words(ly, cls);
+    uint32_t* B = sm.bwd + cls_words(ly, cls);
     const int first = q_pos(ly, cls, kQOff);  // position of class index kQOff
-    for (int w = lane_id(); w < words_per_cls; w += 32) {
+    for (int w = glane<GL>(); w < words_per_cls; w += GL) {
       F[w] = window_bytes(sm, ly.L, first + ly.lam * (4 * w - kQOff), ly.lam, false);
       B[w] = window_bytes(sm, ly.L, first + ly.lam * (ly.Qr - 4 * w - 3 - kQOff), ly.lam, true);
     }
   }
-  __syncwarp();
+  gsync<GL>();
 }
 
 // C_k = (L-k) - 2 popc((x XOR (x >> k)) restricted to the low L-k bits) from the packed bits.
@@ -337,38 +430,39 @@ __device__ inline void p_all(const ScanSmem& sm, const Layout& ly, uint32_t* xb,
   }
 }
 
-// C_{lambda g} for g = 1..G; lanes split the lags.  Writes C16 (zero-padded to kCLen) and returns E on
-// every lane (sum over the tracked lags; for skew inputs the untracked odd lags are zero).
-__device__ inline int build_table(ScanSmem& sm, const Layout& ly) {
-  const int lane = lane_id();
+// C_{lambda g} for g = 1..G; lanes split the lags.  Writes C16 (zero-padded to ly.cl) and returns E on
+// every lane of the group (sum over the tracked lags; for skew inputs the untracked odd lags are zero).
+template <int GL = 32, class S>
+__device__ inline int build_table(S& sm, const Layout& ly) {
   int e_part = 0;
-  for (int h = lane; h < kCLen; h += 32) {
+  for (int h = glane<GL>(); h < ly.cl; h += GL) {
     int g = h + 1;
     int cval = (g <= ly.G) ? corr_lag(sm.bits, ly.L, ly.lam * g) : 0;
     sm.C16[h] = (int16_t)cval;
     e_part += cval * cval;
   }
-  __syncwarp();
-  return warp_sum_i32(e_part);
+  gsync<GL>();
+  return gsum<GL>(e_part);
 }
 
 // int8 copy of the table; returns true on every lane if all |C| <= 127 (fast path allowed).
-__device__ inline bool pack_c8(ScanSmem& sm) {
-  const int lane = lane_id();
+template <int GL = 32, class S>
+__device__ inline bool pack_c8(S& sm, const Layout& ly) {
   bool ok = true;
-  for (int h = lane; h < kCLen; h += 32) {
+  for (int h = glane<GL>(); h < ly.cl; h += GL) {
     int v = sm.C16[h];
     ok &= (v >= -127 && v <= 127);
     sm.C8[h] = (int8_t)max(-127, min(127, v));
   }
-  __syncwarp();
-  return __all_sync(kFull, ok);
+  gsync<GL>();
+  return gall<GL>(ok);
 }
 
-__device__ inline int table_sum(const ScanSmem& sm) {
+template <int GL = 32, class S>
+__device__ inline int table_sum(const S& sm, const Layout& ly) {
   int s = 0;
-  for (int h = lane_id(); h < kCLen; h += 32) s += sm.C16[h];
-  return warp_sum_i32(s);
+  for (int h = glane<GL>(); h < ly.cl; h += GL) s += sm.C16[h];
+  return gsum<GL>(s);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -376,16 +470,16 @@ __device__ inline int table_sum(const ScanSmem& sm) {
 // neighbours of one tile (class `cls`, class indices q0 .. q0+M-1; q0 = 3 mod 4 so every window has a
 // static alignment).  u_end - u_begin must be a multiple of R = M/4 + 1.
 // ------------------------------------------------------------------------------------------------
-template <int M, bool WIDE>
-__device__ __forceinline__ void scan_range(const ScanSmem& sm, const Layout& ly, int cls, int q0, int u_begin,
-                                           int u_end, int (&acc)[M]) {
+template <int M, bool WIDE, class S>
+__device__ __forceinline__ void scan_range(const S& sm, const Layout& ly, int cls, int q0, int u_begin, int u_end,
+                                           int (&acc)[M]) {
   // Word streams: plain words P[t] (ring of R) and, for byte offsets r = 1..3, the realigned words
   // S_r[t] = bytes 4t+r .. 4t+r+3 (rings of R).  Each new word costs one load and three funnel
   // shifts per direction, shared by every neighbour of the tile.
   constexpr int K4 = M / 4;
   constexpr int R = K4 + 1;
-  const uint32_t* Fw = sm.fwd + cls_words(cls);
-  const uint32_t* Bw = sm.bwd + cls_words(cls);
+  const uint32_t* Fw = sm.fwd + cls_words(ly, cls);
+  const uint32_t* Bw = sm.bwd + cls_words(ly, cls);
   const int tf0 = ((q0 + 1) >> 2) + u_begin;
   const int tb0 = ((ly.Qr - q0 + 1) >> 2) - K4 + u_begin;
   uint32_t pf[R], pb[R], sf[3][R], sb[3][R];
@@ -445,8 +539,8 @@ __device__ __forceinline__ void scan_range(const ScanSmem& sm, const Layout& ly,
 }
 
 // The whole lag range of one tile (single lane per tile).
-template <int M, bool WIDE>
-__device__ __forceinline__ void scan_tile(const ScanSmem& sm, const Layout& ly, int cls, int q0, int (&acc)[M]) {
+template <int M, bool WIDE, class S>
+__device__ __forceinline__ void scan_tile(const S& sm, const Layout& ly, int cls, int q0, int (&acc)[M]) {
 #pragma unroll
   for (int j = 0; j < M; j++) acc[j] = 0;
   scan_range<M, WIDE>(sm, ly, cls, q0, 0, ly.NGh, acc);
@@ -473,7 +567,8 @@ __device__ __forceinline__ SlotInfo slot_info(const Layout& ly, int cls, int q) 
 }
 
 // P_m from scratch: sum over g <= min(nf, nb), g != gd, of s_{m - lambda g} s_{m + lambda g}.
-__device__ __forceinline__ int p_from_scratch(const ScanSmem& sm, const Layout& ly, int cls, int q, const SlotInfo& si) {
+template <class S>
+__device__ __forceinline__ int p_from_scratch(const S& sm, const Layout& ly, int cls, int q, const SlotInfo& si) {
   if (!si.active) return 0;
   int gmax = min(si.nf, si.nb);
   int P = 0;
@@ -485,8 +580,9 @@ __device__ __forceinline__ int p_from_scratch(const ScanSmem& sm, const Layout& 
 }
 
 // Delta E of slot (cls, q) from its accumulator, the table sum SC and P.
-__device__ __forceinline__ int finish_delta(const ScanSmem& sm, const Layout& ly, int cls, int q, const SlotInfo& si,
-                                            int acc, int SC, int P) {
+template <class S>
+__device__ __forceinline__ int finish_delta(const S& sm, const Layout& ly, int cls, int q, const SlotInfo& si, int acc,
+                                            int SC, int P) {
   int s_m = fwd_byte(sm, ly, cls, q) - 1;
   int T = acc - 2 * SC;
   int alpha = si.pair ? 4 : 2;
@@ -505,22 +601,23 @@ __device__ __forceinline__ int finish_delta(const ScanSmem& sm, const Layout& ly
 // bytewise (as in the scan).  Lags beyond G have pads at both ends, so their y is 0 and C stays 0.
 // Returns the change of the table sum; *fast receives whether every |C| <= 127 (the int8 copy is only
 // read while that holds, and every step rewrites all of it).
-__device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bool* fast) {
+template <int GL = 32, class S>
+__device__ inline int table_update(S& sm, const Layout& ly, int mstar, bool* fast) {
   const int cls = pos_cls(ly, mstar), q = pos_q(ly, mstar);
   const int pair = (ly.skew && mstar != ly.c) ? 1 : 0;
   const int s_m = fwd_byte(sm, ly, cls, q) - 1;
   const int as = -(pair ? 4 : 2) * s_m;  // C_g += as * y_g
   const int gd = pair ? (ly.L + 1 - 2 * mstar) >> 1 : 0;
   const int s_mp = pair ? (((ly.c - mstar) & 1) ? -s_m : s_m) : 0;
-  const uint32_t* Fw = sm.fwd + cls_words(cls);
-  const uint32_t* Bw = sm.bwd + cls_words(cls);
+  const uint32_t* Fw = sm.fwd + cls_words(ly, cls);
+  const uint32_t* Bw = sm.bwd + cls_words(ly, cls);
   const int of = q + 1, ob = ly.Qr - q + 1;  // byte offsets of lag 1 in the two windows
   const int wf = of >> 2, sf = 8 * (of & 3), wb = ob >> 2, sb = 8 * (ob & 3);
   uint32_t* C16w = reinterpret_cast<uint32_t*>(sm.C16);
   uint32_t* C8w = reinterpret_cast<uint32_t*>(sm.C8);
   int dsum = 0;
   bool ok = true;
-  for (int u = lane_id(); u < ly.NG; u += 32) {
+  for (int u = glane<GL>(); u < ly.NG; u += GL) {
     uint32_t y4 = __funnelshift_r(Fw[wf + u], Fw[wf + u + 1], sf) + __funnelshift_r(Bw[wb + u], Bw[wb + u + 1], sb);
     // the pair's own product is not part of C: lag gd drops s_m' from its byte, which holds
     // (s_m' + 1) + (the other end + 1 or a pad 1), so the byte stays in 0..4 and no borrow crosses bytes
@@ -540,24 +637,26 @@ __device__ inline int table_update(ScanSmem& sm, const Layout& ly, int mstar, bo
     C16w[2 * u + 1] = ((uint32_t)c[2] & 0xffffu) | ((uint32_t)c[3] << 16);
     C8w[u] = c8;
   }
-  __syncwarp();
-  *fast = __all_sync(kFull, ok);
-  return warp_sum_i32(dsum);
+  gsync<GL>();
+  *fast = gall<GL>(ok);
+  return gsum<GL>(dsum);
 }
 
 // Negates s_i in the bits and both byte arrays (one lane per position, distinct positions may run
-// on different lanes at once; then __syncwarp).
-__device__ __forceinline__ void flip_position(ScanSmem& sm, const Layout& ly, int i) {
+// on different lanes at once; then a group sync).
+template <class S>
+__device__ __forceinline__ void flip_position(S& sm, const Layout& ly, int i) {
   const int cls = pos_cls(ly, i), q = pos_q(ly, i);
-  uint8_t* F = reinterpret_cast<uint8_t*>(sm.fwd + cls_words(cls));
-  uint8_t* B = reinterpret_cast<uint8_t*>(sm.bwd + cls_words(cls));
+  uint8_t* F = reinterpret_cast<uint8_t*>(sm.fwd + cls_words(ly, cls));
+  uint8_t* B = reinterpret_cast<uint8_t*>(sm.bwd + cls_words(ly, cls));
   F[q] = (uint8_t)(2 - F[q]);
   B[ly.Qr - q] = (uint8_t)(2 - B[ly.Qr - q]);
   atomicXor(&sm.bits[(i - 1) >> 5], 1u << ((i - 1) & 31));
 }
 
 // Copies packed 64-bit words from global memory into the slab bits (zero-padded).
-__device__ inline void load_bits(ScanSmem& sm, const uint64_t* src, int L) {
+template <class S>
+__device__ inline void load_bits(S& sm, const uint64_t* src, int L) {
   const int W32 = (L + 31) >> 5;
   for (int w = lane_id(); w < kBitWords; w += 32) {
     uint32_t v = 0;
@@ -573,41 +672,49 @@ __device__ inline void load_bits(ScanSmem& sm, const uint64_t* src, int L) {
 }
 
 // Builds a walk start into the bits: s_1..s_p from the prefix, free element j (position p+1+j) is +1
-// iff bit j%64 of output j/64 of stream `key`; skew walks fill the last k by Eq. (2).
-__device__ inline void build_start(ScanSmem& sm, const Layout& ly, const uint64_t* prefix, uint64_t key) {
-  const int lane = lane_id();
+// iff bit j%64 of output j/64 of stream `key`; skew walks fill the last k by Eq. (2).  Each 32-bit word
+// is assembled from 32 / GL group ballots.
+template <int GL = 32, class S>
+__device__ inline void build_start(S& sm, const Layout& ly, const uint64_t* prefix, uint64_t key) {
+  const int lane = glane<GL>();
   const int W32 = (ly.L + 31) >> 5;
   for (int w = 0; w < kBitWords; w++) {
-    int i = 32 * w + lane + 1;
-    int bit = 0;
-    if (i <= ly.L) {
-      int src = i;
-      int neg = 0;
-      if (ly.skew && i > ly.c) {
-        src = 2 * ly.c - i;
-        neg = (i - ly.c) & 1;
+    unsigned word = 0;
+#pragma unroll
+    for (int part = 0; part < 32 / GL; part++) {
+      int i = 32 * w + GL * part + lane + 1;
+      int bit = 0;
+      if (i <= ly.L) {
+        int src = i;
+        int neg = 0;
+        if (ly.skew && i > ly.c) {
+          src = 2 * ly.c - i;
+          neg = (i - ly.c) & 1;
+        }
+        int b;
+        if (src <= ly.p) {
+          b = (int)((prefix[(src - 1) >> 6] >> ((src - 1) & 63)) & 1u);
+        } else {
+          int j = src - ly.p - 1;
+          b = (int)((sm64_at(key, (uint64_t)(j >> 6)) >> (j & 63)) & 1u);
+        }
+        bit = b ^ neg;
       }
-      int b;
-      if (src <= ly.p) {
-        b = (int)((prefix[(src - 1) >> 6] >> ((src - 1) & 63)) & 1u);
-      } else {
-        int j = src - ly.p - 1;
-        b = (int)((sm64_at(key, (uint64_t)(j >> 6)) >> (j & 63)) & 1u);
-      }
-      bit = b ^ neg;
+      const unsigned bal = gballot<GL>(bit != 0);
+      word |= GL == 32 ? bal : (bal & ((1u << (GL & 31)) - 1u)) << (GL * part);
     }
-    unsigned word = __ballot_sync(kFull, bit);
     if (lane == 0) sm.bits[w] = (w < W32) ? word : 0u;
   }
-  __syncwarp();
+  gsync<GL>();
 }
 
 // Zobrist fingerprint of the sequence in the bits.
-__device__ inline uint64_t fingerprint(const ScanSmem& sm, int L, uint64_t zkey) {
+template <int GL = 32, class S>
+__device__ inline uint64_t fingerprint(const S& sm, int L, uint64_t zkey) {
   uint64_t h = 0;
-  for (int i = lane_id() + 1; i <= L; i += 32)
+  for (int i = glane<GL>() + 1; i <= L; i += GL)
     if (!seq_bit(sm, i)) h ^= zobrist(zkey, i);
-  return warp_xor_u64(h);
+  return gxor_u64<GL>(h);
 }
 
 }  // namespace labsg

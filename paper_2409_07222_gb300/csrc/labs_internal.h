@@ -15,10 +15,10 @@ struct labs_ctx {
   // growable device workspace, one region per purpose
   void* ws[8];
   size_t ws_bytes[8];
-  // autotuner cache: (length-set key) -> tile M, lag ranges H, walks per CTA
+  // autotuner cache: (length-set key) -> tile M, lag ranges H, lanes per walk, warps per CTA
   int n_tuned;
   uint64_t tuned_key[kMaxTuned];
-  int tuned[kMaxTuned][3];
+  int tuned[kMaxTuned][4];
   // captured batched step (one at a time) and the stream it was captured on
   cudaGraphExec_t graph_exec;
   uint64_t graph_key;

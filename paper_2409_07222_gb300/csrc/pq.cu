@@ -2,20 +2,25 @@
 // space, in batch-synchronous form (labs_pq_refine).
 //
 // GB300 mapping.  The paper runs one priority queue per candidate in Rust on CPU cores; here one open
-// set of the cap smallest (E, fp) keys lives in HBM as a sorted array (double-buffered), and a round
-//   expand   -- one warp per popped node: its correlation table, the all-position dp4a scan and a
-//               visited-set lookup per neighbour, written to a dense [pop][position] survivor array;
-//   compact  -- stable compaction of the survivors (pop order, position);
-//   sort     -- stable LSD radix sort by the fingerprint's top 16 bits then the energy bytes (passes
-//               whose byte is the same in every key are skipped), then runs of equal (E', fp' >> 48)
-//               ordered by (fp', pop, pos) in place: order (E', fp', pop, pos);
-//   dedup    -- stable compaction keeping the first of equal (E', fp');
-//   best     -- strict improvement test on the smallest survivor;
-//   merge    -- merge path of (open set minus the pops) with the survivors into the other buffer, cut at
-//               cap; admitted survivors enter the visited set (open addressing, atomicCAS);
-// keeps every result identical to the sequential definition whatever order threads run in.
-// With T_r > 0 every popped pivot also offers its 2 T_r rotations (MAKE_ROTATIONS) as survivor columns
-// L .. L + 2 T_r - 1, after its L flips.
+// set of the cap smallest (E, fp) keys lives in HBM as an UNORDERED pool of entries (energy,
+// fingerprint, sequence) with a free-slot stack, and beside it a histogram of the entries' energies
+// (one bin per energy, clamped at both ends of a 2^17-bin window, and a coarse level of 256 bins per
+// entry).  The B smallest keys, or the cap smallest, are then found without ordering the pool: the
+// histogram's prefix sums give the bin where the count is reached, every entry below it is taken, and
+// only the entries of that one boundary bin are ranked (a radix select on their full (E, fp) key, so a
+// clamped bin holding several energies is still exact).  A round
+//   pop      -- the b = min(B, open, budget left) smallest keys leave the pool (one pass over it), are
+//               put in key order (one block) and become the round's pivots;
+//   expand   -- one warp per pivot: its correlation table, the all-position dp4a scan and a visited-set
+//               lookup per neighbour, written to a dense [pivot][column] survivor array;
+//   dedup    -- survivors with equal (E', fp') (the same sequence) are kept once, through a hash table;
+//               the one kept is the smallest (pivot, column), as in the sequential definition;
+//   best     -- strict improvement test on the smallest survivor key;
+//   cut      -- the cap smallest of (pool u survivors): entries of the pool above the cut are evicted,
+//               survivors below it are admitted into free slots and into the visited set H;
+// keeps every result identical to the sequential definition whatever order threads run in.  The seeds
+// enter through the same survivor path.  With T_r > 0 every pivot also offers its 2 T_r rotations
+// (MAKE_ROTATIONS) as survivor columns L .. L + 2 T_r - 1, after its L flips.
 #include <algorithm>
 #include <new>
 
@@ -28,37 +33,65 @@ namespace {
 constexpr uint64_t kEmptyKey = ~0ull;  // free slot of the visited set (fp == ~0 is tracked by a flag)
 constexpr int kPqWarps = 4;
 constexpr int kPqM = 8;
-constexpr int kTile = 1024;  // elements per block in the compaction and sort kernels (256 threads x 4)
 constexpr int kMaxProbe = 1 << 20;
+constexpr int kNB = 1 << 17;        // fine energy bins: bin = clamp(E - E_base, 0, kNB - 1)
+constexpr int kCoarse = 256;        // fine bins per coarse bin
+constexpr int kNC = kNB / kCoarse;  // coarse bins
+constexpr int kColBits = 11;        // survivor column inside a representative: width <= 576 + 128 < 2^11
+constexpr int kSortMax = 8192;      // pops per round (B <= 8192), put in key order by one block
+constexpr int kSelThreads = 1024;   // threads of the single-block select, boundary and sort kernels
 
+// Device-side state of one refinement (every round reads and writes it; the host only polls `stop`).
 struct PqState {
-  long long nP, nS, nU, n_dense;
+  long long nP;  // open-set entries
   long long expansions, rounds, survivors, admitted, evicted, h_size, improvements, u;
   unsigned long long best_fp;
-  int b, cur, stop, best_E, error, h_has_empty, pad0, pad1;
-  // OR and AND of the sort keys' 32-bit halves (fingerprint high half, energy) over this sort's input:
-  // a radix byte that is equal in every key orders nothing and its pass is skipped
-  unsigned fph_or, fph_and, e_or, e_and;
+  long long free_top;   // free pool slots (the stack holds their ids)
+  long long pop_cnt;    // entries gathered for popping this round
+  long long cand_cnt;   // boundary-bin candidates gathered
+  long long nU;         // unique survivors of the round
+  long long sel_lt;     // entries below the boundary bin
+  long long sel_need;   // entries taken from the boundary bin; 0: none; -1: no cut (everything kept)
+  long long ev_round;   // evicted this round
+  long long adm_round;  // admitted this round
+  int b, stop, best_E, error, h_has_empty, E_base;
+  int sel_bin;     // boundary fine bin
+  int minE_round;  // smallest survivor energy of the round
+  int sel_E, pad0;
+  unsigned long long sel_fp;  // boundary key: a boundary-bin entry is taken iff (E, fp) <= (sel_E, sel_fp)
+  unsigned long long minfp_round;
+  unsigned best_rep_round, pad1;
 };
 
 struct PqBufs {
   int L, W, B, H_log2;
-  int Tr, width;  // rotations per side (MAKE_ROTATIONS) and survivor columns per pop: L flips + 2 Tr rotations
+  int Tr, width;  // rotations per side (MAKE_ROTATIONS) and survivor columns per pivot: L flips + 2 Tr rotations
   long long cap, max_exp, T_u;
-  int32_t* PE[2];
-  uint64_t* Pfp[2];
-  uint64_t* Pseq[2];
-  int32_t* dE;  // dense survivors [B * L] (or seeds)
-  uint64_t* dfp;
-  int32_t* sE[2];  // sort ping-pong
-  uint64_t* sfp[2];
-  int32_t* sidx[2];
-  int32_t* uE;  // unique survivors
-  uint64_t* ufp;
-  int32_t* uidx;
-  unsigned* counts;  // 256 * blocks
-  unsigned* bsum;    // per-block counts (+ total)
-  uint64_t* H;
+  int hs_log2;        // dedup hash table: 2^hs_log2 slots, at least twice the dense survivors
+  long long cand_cap; // boundary candidate capacity (cap + dense survivors)
+  int n_seeds;
+  int32_t* pE;        // pool [cap]: energy, INT32_MAX for a free slot
+  uint64_t* pFp;      // pool [cap]: fingerprint
+  uint64_t* pSeq;     // pool [cap][W]
+  int32_t* freeIds;   // free-slot stack [cap]
+  unsigned* hP;       // histogram of the pool's energies: fine [kNB], coarse [kNC]
+  unsigned* hP2;
+  unsigned* hU;       // histogram of the round's unique survivors
+  unsigned* hU2;
+  int32_t* popId;     // pool ids gathered for popping [B]
+  int32_t* pivE;      // pivots in key order [B]
+  uint64_t* pivFp;
+  uint64_t* pivSeq;   // [B][W]
+  int32_t* candId;    // boundary candidates: pool id >= 0, or -(u + 1) for survivor u
+  int32_t* dE;        // dense survivors [pivot][column]: energy, or INT32_MAX (visited)
+  uint64_t* dFp;
+  uint64_t* hkey;     // dedup hash table: mixed (E, fp) key, 0 = empty
+  int32_t* hval;      // the unique survivor of a slot
+  int32_t* uE;        // unique survivors
+  uint64_t* uFp;
+  unsigned* uRep;     // representative (pivot << kColBits | column): the smallest of equal keys
+  int32_t* uSlot;     // dedup slot of the survivor
+  uint64_t* H;        // visited set (open addressing)
   uint64_t* ztab;
   PqState* st;
   uint64_t* best_seq;
@@ -133,6 +166,53 @@ __device__ __forceinline__ int h_insert(const PqBufs& b, uint64_t fp) {
 __device__ __forceinline__ bool key_lt(int Ea, uint64_t fa, int Eb, uint64_t fb) {
   return Ea < Eb || (Ea == Eb && fa < fb);
 }
+__device__ __forceinline__ bool key_le(int Ea, uint64_t fa, int Eb, uint64_t fb) {
+  return Ea < Eb || (Ea == Eb && fa <= fb);
+}
+
+__device__ __forceinline__ int e_bin(int E, int E_base) {
+  const int d = E - E_base;
+  return d < 0 ? 0 : (d >= kNB ? kNB - 1 : d);
+}
+
+// Adds v to *ctr once per warp (every lane of the warp calls it with its own v).
+__device__ __forceinline__ void warp_add(long long* ctr, int v) {
+  const int s = __reduce_add_sync(kFull, v);
+  if (lane_id() == 0 && s) atomicAdd(reinterpret_cast<unsigned long long*>(ctr), (unsigned long long)(long long)s);
+}
+
+// Reserves one output index per lane with pred, one atomic per warp (every lane calls it); returns the
+// lane's index, or -1.
+__device__ __forceinline__ long long warp_append(long long* ctr, bool pred) {
+  const unsigned m = __ballot_sync(kFull, pred);
+  if (!m) return -1;
+  const int leader = __ffs(m) - 1;
+  long long base = 0;
+  if (lane_id() == leader)
+    base = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(ctr), (unsigned long long)__popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
+}
+
+// Adds the insertions of a warp to h_size (every lane calls it).
+__device__ __forceinline__ void h_count(const PqBufs& b, int inserted) { warp_add(&b.st->h_size, inserted); }
+
+// Mixed key of (E, fp) for the dedup table; 0 marks an empty slot, so a mixed key of 0 becomes 1.
+__device__ __forceinline__ uint64_t dedup_key(int E, uint64_t fp) {
+  const uint64_t k = fp ^ ((uint64_t)(uint32_t)E * 0xD6E8FEB86659FD93ull);
+  return k ? k : 1ull;
+}
+
+// Key of a boundary candidate (pool entry or survivor).
+__device__ __forceinline__ void cand_key(const PqBufs& b, int32_t c, int& E, uint64_t& fp) {
+  if (c >= 0) {
+    E = b.pE[c];
+    fp = b.pFp[c];
+  } else {
+    E = b.uE[-c - 1];
+    fp = b.uFp[-c - 1];
+  }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Set-up kernels
@@ -142,15 +222,25 @@ __global__ void pq_ztab_kernel(uint64_t* ztab, int L) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) ztab[i] = zobrist(zk, i + 1);
 }
 
-__global__ void pq_state_init_kernel(PqState* st, long long n_seeds) {
-  PqState z{};
-  z.n_dense = n_seeds;
-  z.best_E = INT32_MAX;
-  z.best_fp = ~0ull;
-  *st = z;
+// Every pool slot free (the stack holds them all), the state zeroed.
+__global__ void pq_init_kernel(PqBufs b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.cap; i += (long long)gridDim.x * blockDim.x) {
+    b.pE[i] = INT32_MAX;
+    b.freeIds[i] = (int32_t)(b.cap - 1 - i);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    PqState z{};
+    z.free_top = b.cap;
+    z.best_E = INT32_MAX;
+    z.best_fp = ~0ull;
+    z.minE_round = INT32_MAX;
+    z.minfp_round = ~0ull;
+    z.best_rep_round = ~0u;
+    *b.st = z;
+  }
 }
 
-// One warp per seed: energy over all lags and the fingerprint, into the dense arrays.
+// One warp per seed: energy over all lags and the fingerprint, into the dense arrays (one column).
 __global__ void __launch_bounds__(32 * kPqWarps) pq_seed_kernel(PqBufs b, int n_seeds) {
   __shared__ uint32_t bits_all[kPqWarps][kBitWords];
   uint32_t* bits = bits_all[threadIdx.x >> 5];
@@ -181,47 +271,15 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_seed_kernel(PqBufs b, int n_
     h = warp_xor_u64(h);
     if (lane == 0) {
       b.dE[q] = e;
-      b.dfp[q] = h;
+      b.dFp[q] = h;
     }
     __syncwarp();
   }
 }
 
-// Adds a block's insertion counts to h_size with one atomic per warp (every thread of the block calls it).
-__device__ __forceinline__ void h_count(const PqBufs& b, int inserted) {
-  const int w = __reduce_add_sync(kFull, inserted);
-  if (lane_id() == 0 && w) atomicAdd(reinterpret_cast<unsigned long long*>(&b.st->h_size), (unsigned long long)w);
-}
-
-// Admits the sorted, de-duplicated seeds: the cap smallest become the open set and enter H.
-__global__ void pq_seed_admit_kernel(PqBufs b) {
-  PqState* st = b.st;
-  const long long n = min((long long)st->nU, b.cap);
-  int ins = 0;
-  for (long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
-    const int q = b.uidx[o];
-    b.PE[0][o] = b.uE[o];
-    b.Pfp[0][o] = b.ufp[o];
-    for (int t = 0; t < b.W; t++) b.Pseq[0][o * b.W + t] = b.seeds[(size_t)q * b.W + t];
-    ins += h_insert(b, b.ufp[o]);
-  }
-  h_count(b, ins);
-}
-
-__global__ void pq_seed_finish_kernel(PqBufs b) {
-  PqState* st = b.st;
-  st->nP = min((long long)st->nU, b.cap);
-  st->cur = 0;
-  if (st->nU > 0) {
-    st->best_E = b.uE[0];
-    st->best_fp = b.ufp[0];
-    const int q = b.uidx[0];
-    for (int t = 0; t < b.W; t++) b.best_seq[t] = b.seeds[(size_t)q * b.W + t];
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
-// Round kernels
+// Round kernels.  SEED = true runs the survivor path on the seeds (dense = the seeds, one column each,
+// representatives are seed indices; nothing is counted as a survivor or an admission).
 // ---------------------------------------------------------------------------------------------
 __global__ void pq_round_begin_kernel(PqBufs b) {
   PqState* st = b.st;
@@ -235,18 +293,276 @@ __global__ void pq_round_begin_kernel(PqBufs b) {
     else if (b.T_u > 0 && st->u >= b.T_u)
       st->stop = 3;
   }
+  st->pop_cnt = 0;
+  st->cand_cnt = 0;
+  st->nU = 0;
+  st->ev_round = 0;
+  st->adm_round = 0;
+  st->minE_round = INT32_MAX;
+  st->minfp_round = ~0ull;
+  st->best_rep_round = ~0u;
   if (st->stop) {
     st->b = 0;
-    st->n_dense = 0;
     return;
   }
   long long bb = min((long long)b.B, st->nP);
   bb = min(bb, b.max_exp - st->expansions);
   st->b = (int)bb;
-  st->n_dense = bb * b.width;
 }
 
-// One warp per popped node: Delta E of all L single flips, visited-set test, dense survivor output.
+// One block: the fine bin where the count of entries reaches the target (POP: b over the pool; else
+// cap over the pool's rest and the survivors, or no cut when everything fits).  sel_lt = entries below
+// that bin, sel_need = entries to take from it.
+template <bool POP>
+__global__ void __launch_bounds__(kSelThreads) pq_select_kernel(PqBufs b) {
+  PqState* st = b.st;
+  __shared__ unsigned long long part[kSelThreads];
+  __shared__ long long s_target;
+  __shared__ int s_cb;
+  __shared__ unsigned long long s_before;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    long long target;
+    if (POP) {
+      target = st->b;
+    } else {
+      st->cand_cnt = 0;  // the pop's candidates are done with
+      const long long total = st->nP - st->b + st->nU;
+      target = total > b.cap ? b.cap : -1;
+    }
+    s_target = target;
+    if (target <= 0) {
+      st->sel_need = target < 0 ? -1 : 0;
+      st->sel_bin = kNB;
+      st->sel_lt = 0;
+    }
+  }
+  __syncthreads();
+  const long long target = s_target;
+  if (target <= 0) return;
+  // coarse level
+  unsigned long long c = 0;
+  if (t < kNC) c = (unsigned long long)b.hP2[t] + (POP ? 0u : b.hU2[t]);
+  part[t] = c;
+  __syncthreads();
+  for (int off = 1; off < kSelThreads; off <<= 1) {  // inclusive scan
+    const unsigned long long v = t >= off ? part[t - off] : 0ull;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  if (t < kNC) {
+    const unsigned long long before = t ? part[t - 1] : 0ull;
+    if (before < (unsigned long long)target && part[t] >= (unsigned long long)target) {
+      s_cb = t;
+      s_before = before;
+    }
+  }
+  __syncthreads();
+  const int cb = s_cb;
+  const unsigned long long cbefore = s_before;
+  // fine level: the coarse bin's 256 bins
+  unsigned long long f = 0;
+  if (t < kCoarse) f = (unsigned long long)b.hP[cb * kCoarse + t] + (POP ? 0u : b.hU[cb * kCoarse + t]);
+  __syncthreads();
+  part[t] = f;
+  __syncthreads();
+  for (int off = 1; off < kCoarse; off <<= 1) {
+    const unsigned long long v = (t < kCoarse && t >= off) ? part[t - off] : 0ull;
+    __syncthreads();
+    if (t < kCoarse) part[t] += v;
+    __syncthreads();
+  }
+  if (t < kCoarse) {
+    const unsigned long long before = cbefore + (t ? part[t - 1] : 0ull);
+    if (before < (unsigned long long)target && cbefore + part[t] >= (unsigned long long)target) {
+      st->sel_bin = cb * kCoarse + t;
+      st->sel_lt = (long long)before;
+      st->sel_need = target - (long long)before;
+    }
+  }
+}
+
+// Pass over the pool (U = false) or the survivors (U = true): POP gathers the pool entries below the
+// boundary bin (popped) and those in it (candidates); the cut gathers the boundary bin's entries.
+template <bool POP, bool U>
+__global__ void __launch_bounds__(256) pq_gather_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (POP ? st->b == 0 : st->sel_need <= 0) return;
+  const int sel = st->sel_bin, Eb = st->E_base;
+  const long long n = U ? st->nU : b.cap;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int bin = kNB;
+    if (i < n) {
+      const int E = U ? b.uE[i] : b.pE[i];
+      if (E != INT32_MAX) bin = e_bin(E, Eb);
+    }
+    // the histogram bounds both counts (b entries below the boundary bin at most); a count beyond a
+    // buffer can only come from an inconsistent state, which is reported instead of written
+    if (POP) {
+      const long long o = warp_append(&st->pop_cnt, bin < sel);
+      if (o >= b.B) st->error = 1;
+      else if (o >= 0) b.popId[o] = (int32_t)i;
+    }
+    const long long o2 = warp_append(&st->cand_cnt, bin == sel);
+    if (o2 >= b.cand_cap) st->error = 1;
+    else if (o2 >= 0) b.candId[o2] = U ? -(int32_t)i - 1 : (int32_t)i;
+  }
+}
+
+// One block: the sel_need smallest (E, fp) keys among the boundary candidates, by a most-significant-
+// digit-first radix select over the 96-bit key (four energy bytes, then eight fingerprint bytes); keys
+// are distinct, so exactly sel_need candidates are <= the selected key.  POP appends them to the pops.
+template <bool POP>
+__global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (POP ? st->b == 0 : st->sel_need <= 0) return;
+  const long long n = min(st->cand_cnt, b.cand_cap);
+  __shared__ unsigned hist[256];
+  __shared__ unsigned long long s_pre_e, s_pre_f;  // the digits fixed so far
+  __shared__ long long s_k;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_pre_e = 0;
+    s_pre_f = 0;
+    s_k = st->sel_need;
+  }
+  __syncthreads();
+  for (int d = 0; d < 12; d++) {
+    if (t < 256) hist[t] = 0;
+    __syncthreads();
+    const unsigned long long pe = s_pre_e, pf = s_pre_f;
+    for (long long i = t; i < n; i += kSelThreads) {
+      int E;
+      uint64_t fp;
+      cand_key(b, b.candId[i], E, fp);
+      const uint64_t ue = (uint32_t)E;
+      bool match;
+      unsigned digit;
+      if (d < 4) {
+        const int sh = 24 - 8 * d;
+        match = d == 0 || (ue >> (sh + 8)) == (pe >> (sh + 8));
+        digit = (unsigned)(ue >> sh) & 255u;
+      } else {
+        const int sh = 56 - 8 * (d - 4);
+        match = ue == pe && (d == 4 || (fp >> (sh + 8)) == (pf >> (sh + 8)));
+        digit = (unsigned)(fp >> sh) & 255u;
+      }
+      if (match) atomicAdd(&hist[digit], 1u);
+    }
+    __syncthreads();
+    if (t == 0) {
+      const long long k = s_k;
+      long long acc = 0;
+      int dg = 0;
+      while (dg < 255 && acc + hist[dg] < k) acc += hist[dg++];
+      s_k = k - acc;
+      if (d < 4)
+        s_pre_e = pe | ((unsigned long long)dg << (24 - 8 * d));
+      else
+        s_pre_f = pf | ((unsigned long long)dg << (56 - 8 * (d - 4)));
+    }
+    __syncthreads();
+  }
+  const int selE = (int)(uint32_t)s_pre_e;
+  const uint64_t selF = s_pre_f;
+  if (t == 0) {
+    st->sel_E = selE;
+    st->sel_fp = selF;
+  }
+  if (POP) {
+    for (long long i = t; i < n; i += kSelThreads) {
+      int E;
+      uint64_t fp;
+      const int32_t c = b.candId[i];
+      cand_key(b, c, E, fp);
+      if (key_le(E, fp, selE, selF)) {
+        const long long o = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&st->pop_cnt), 1ull);
+        if (o < b.B)
+          b.popId[o] = c;
+        else
+          st->error = 1;
+      }
+    }
+  }
+}
+
+// One block: the popped entries in key order (bitonic sort of (E, fp, id), padded to a power of two)
+// become pivots 0..b-1; their pool slots are freed and leave the histogram.
+__global__ void __launch_bounds__(kSelThreads) pq_pop_sort_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const int nb = st->b;
+  if (nb == 0) return;
+  if (st->pop_cnt != nb || st->error) {  // an inconsistent pop: stop the search (capacity status)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st->error = 1;
+      st->b = 0;
+    }
+    return;
+  }
+  extern __shared__ unsigned long long sm_pop[];
+  unsigned long long* kf = sm_pop;                      // fingerprints
+  int* ke = reinterpret_cast<int*>(sm_pop + kSortMax);  // energies
+  int* ki = ke + kSortMax;                              // pool ids
+  int n2 = 1;
+  while (n2 < nb) n2 <<= 1;
+  const int t = threadIdx.x;
+  for (int i = t; i < n2; i += kSelThreads) {
+    if (i < nb) {
+      const int id = b.popId[i];
+      kf[i] = b.pFp[id];
+      ke[i] = b.pE[id];
+      ki[i] = id;
+    } else {
+      kf[i] = ~0ull;
+      ke[i] = INT32_MAX;
+      ki[i] = -1;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = t; i < n2; i += kSelThreads) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const bool gt = key_lt(ke[j], kf[j], ke[i], kf[i]);  // a[i] > a[j]
+          if (gt == up) {
+            const unsigned long long f = kf[i];
+            kf[i] = kf[j];
+            kf[j] = f;
+            const int e = ke[i];
+            ke[i] = ke[j];
+            ke[j] = e;
+            const int d = ki[i];
+            ki[i] = ki[j];
+            ki[j] = d;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  const int Eb = st->E_base;
+  const long long top = st->free_top;
+  for (int q = t; q < nb; q += kSelThreads) {
+    const int id = ki[q];
+    b.pivE[q] = ke[q];
+    b.pivFp[q] = kf[q];
+    for (int w = 0; w < b.W; w++) b.pivSeq[(size_t)q * b.W + w] = b.pSeq[(size_t)id * b.W + w];
+    b.pE[id] = INT32_MAX;
+    b.freeIds[top + q] = id;
+    const int bin = e_bin(ke[q], Eb);
+    atomicSub(&b.hP[bin], 1u);
+    atomicSub(&b.hP2[bin / kCoarse], 1u);
+  }
+  __syncthreads();
+  if (t == 0) st->free_top = top + nb;
+}
+
+// One warp per pivot: Delta E of all L single flips, visited-set test, dense survivor output.
 __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layout ly) {
   __shared__ ScanSmem slabs[kPqWarps];
   __shared__ uint32_t rbits_all[kPqWarps][kBitWords];
@@ -259,19 +575,15 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
   const int lane = lane_id();
   const PqState* st = b.st;
   const int nb = st->b;
-  const int cur = st->cur;
-  const int32_t* PE = b.PE[cur];
-  const uint64_t* Pfp = b.Pfp[cur];
-  const uint64_t* Pseq = b.Pseq[cur];
   for (int q = blockIdx.x * kPqWarps + (threadIdx.x >> 5); q < nb; q += gridDim.x * kPqWarps) {
-    load_bits(sm, Pseq + (size_t)q * b.W, b.L);
+    load_bits(sm, b.pivSeq + (size_t)q * b.W, b.L);
     build_table(sm, ly);
-    const bool fast = pack_c8(sm);
-    const int SC = table_sum(sm);
+    const bool fast = pack_c8(sm, ly);
+    const int SC = table_sum(sm, ly);
     build_bytes(sm, ly);
     p_all(sm, ly, xbits, rbits, Pm);
-    const int E = PE[q];
-    const uint64_t fp = Pfp[q];
+    const int E = b.pivE[q];
+    const uint64_t fp = b.pivFp[q];
     for (int base = 0; base < ly.n_tiles; base += 32) {
       const int tau = base + lane;
       if (tau < ly.n_tiles) {
@@ -307,7 +619,7 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
             seen = h_contains_after(b, fv[j], h_slot(fv[j], b.H_log2));
           const size_t di = (size_t)q * b.width + (mv[j] - 1);
           b.dE[di] = seen ? INT32_MAX : E + dv[j];
-          b.dfp[di] = fv[j];
+          b.dFp[di] = fv[j];
         }
       }
     }
@@ -339,7 +651,7 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
       if (lane == 0) {
         const size_t di = (size_t)q * b.width + b.L + c;
         b.dE[di] = h_contains(b, h) ? INT32_MAX : e;
-        b.dfp[di] = h;
+        b.dFp[di] = h;
       }
       __syncwarp();
     }
@@ -347,366 +659,142 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// Stable compaction (MODE 0: dense survivors -> sort input; MODE 1: sorted -> first of equal keys)
-// and stable LSD radix sort.  Element e of block k is k*1024 + w*128 + r*32 + lane (warp w, round r):
-// increasing e is increasing (w, r, lane), so block-local ranks built warp by warp, round by round,
-// are stable.
-// ---------------------------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ long long compact_n(const PqBufs& b) {
-  return MODE == 0 ? b.st->n_dense : b.st->nS;
+// Dense survivors of the round: b pivots x width columns, or the seeds (one column each).
+template <bool SEED>
+__device__ __forceinline__ long long dense_n(const PqBufs& b, int n_seeds) {
+  return SEED ? (long long)n_seeds : (long long)b.st->b * b.width;
 }
 
-// Radix passes of the sort: 0..1 the bytes of fp >> 48, 2..5 the bytes of E (least significant first).
-// Bit p of the mask is set when pass p runs; pass p reads buffer popc(mask below p) & 1.
-__device__ __forceinline__ unsigned sort_mask(const PqState* st) {
-  const unsigned vf = st->fph_or ^ st->fph_and, ve = st->e_or ^ st->e_and;  // fph: fp >> 32
-  unsigned m = 0;
-#pragma unroll
-  for (int p = 0; p < 2; p++)
-    if ((vf >> (16 + 8 * p)) & 255u) m |= 1u << p;
-#pragma unroll
-  for (int p = 0; p < 4; p++)
-    if ((ve >> (8 * p)) & 255u) m |= 1u << (p + 2);
-  return m;
-}
-__device__ __forceinline__ int sort_src(unsigned mask, int pass) { return __popc(mask & ((1u << pass) - 1u)) & 1; }
-__device__ __forceinline__ int sort_final(const PqState* st) { return __popc(sort_mask(st)) & 1; }
-
-template <int MODE>
-__device__ __forceinline__ bool compact_flag(const PqBufs& b, long long e, int fin) {
-  if (MODE == 0) return b.dE[e] != INT32_MAX;
-  return e == 0 || b.sE[fin][e] != b.sE[fin][e - 1] || b.sfp[fin][e] != b.sfp[fin][e - 1];
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(256) compact_count_kernel(PqBufs b) {
-  const long long n = compact_n<MODE>(b);
-  const long long base = (long long)blockIdx.x * kTile;
-  if (MODE == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // the sort that follows starts its key summary
-    b.st->fph_or = 0u;
-    b.st->fph_and = ~0u;
-    b.st->e_or = 0u;
-    b.st->e_and = ~0u;
-  }
-  if (base >= n) {  // blocks past this round's count still publish a zero for the scan
-    if (threadIdx.x == 0) b.bsum[blockIdx.x] = 0;
-    return;
-  }
-  const int fin = MODE == 1 ? sort_final(b.st) : 0;
-  int c = 0;
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
-    if (e < n && compact_flag<MODE>(b, e, fin)) c++;
-  }
-  c = __reduce_add_sync(kFull, c);
-  __shared__ int ws[8];
-  if (lane_id() == 0) ws[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int w = 0; w < 8; w++) t += ws[w];
-    b.bsum[blockIdx.x] = t;
-  }
-}
-
-// Single block: exclusive scan of a[0..n) in place; *total receives the sum.
-__global__ void __launch_bounds__(1024) scan_kernel(unsigned* a, long long n, long long* total) {
-  __shared__ unsigned long long part[1024];
-  const int t = threadIdx.x;
-  const long long chunk = (n + 1023) / 1024;
-  const long long lo = t * chunk, hi = min(n, lo + chunk);
-  unsigned long long s = 0;
-  for (long long i = lo; i < hi; i++) s += a[i];
-  part[t] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
-    unsigned long long v = t >= off ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  unsigned long long run = t ? part[t - 1] : 0;
-  for (long long i = lo; i < hi; i++) {
-    const unsigned v = a[i];
-    a[i] = (unsigned)run;
-    run += v;
-  }
-  if (t == 1023 && total) *total = (long long)part[1023];
-}
-
-// Number of blocks a compaction or sort over n elements uses.
-__device__ __forceinline__ long long tiles_of(long long n) { return (n + kTile - 1) / kTile; }
-
-template <int MODE>
-__global__ void __launch_bounds__(256) compact_scatter_kernel(PqBufs b) {
-  const long long n = compact_n<MODE>(b);
-  const long long base = (long long)blockIdx.x * kTile;
-  if (base >= n) return;
-  __shared__ int wcount[8][4];
-  __shared__ unsigned wkey[8][4];
-  const int w = threadIdx.x >> 5, lane = lane_id();
-  const int fin = MODE == 1 ? sort_final(b.st) : 0;
-  bool fl[4];
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + w * 128 + r * 32 + lane;
-    fl[r] = e < n && compact_flag<MODE>(b, e, fin);
-    const unsigned m = __ballot_sync(kFull, fl[r]);
-    if (lane == 0) wcount[w][r] = __popc(m);
-  }
-  __syncthreads();
-  int off = b.bsum[blockIdx.x];
-  for (int ww = 0; ww < w; ww++)
-    for (int r = 0; r < 4; r++) off += wcount[ww][r];
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + w * 128 + r * 32 + lane;
-    const unsigned m = __ballot_sync(kFull, fl[r]);
-    if (fl[r]) {
-      const long long o = off + __popc(m & ((1u << lane) - 1u));
-      if (MODE == 0) {
-        b.sE[0][o] = b.dE[e];
-        b.sfp[0][o] = b.dfp[e];
-        b.sidx[0][o] = (int32_t)e;
-      } else {
-        b.uE[o] = b.sE[fin][e];
-        b.ufp[o] = b.sfp[fin][e];
-        b.uidx[o] = b.sidx[fin][e];
+// Dedup, first pass: every survivor inserts its (E, fp) key; the first inserter of a key creates the
+// unique survivor (its representative is settled by the second pass).
+template <bool SEED>
+__global__ void __launch_bounds__(256) pq_dedup_insert_kernel(PqBufs b, int n_seeds) {
+  const long long n = dense_n<SEED>(b, n_seeds);
+  const uint64_t mask = (1ull << b.hs_log2) - 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    bool fresh = false;
+    uint64_t slot = 0;
+    int E = INT32_MAX;
+    uint64_t fp = 0;
+    if (i < n) {
+      E = b.dE[i];
+      fp = b.dFp[i];
+    }
+    if (E != INT32_MAX) {
+      const uint64_t k = dedup_key(E, fp);
+      uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
+      for (uint64_t it = 0; it <= mask; it++) {  // the table holds at most half its slots
+        const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&b.hkey[s]), 0ull, k);
+        if (old == 0ull) {
+          fresh = true;
+          slot = s;
+          break;
+        }
+        if (old == k) break;
+        s = (s + 1) & mask;
       }
     }
-    off += __popc(m);
-  }
-  if (MODE == 0) {  // the block's share of the key summary
-    unsigned fo = 0u, fa = ~0u, eo = 0u, ea = ~0u;
-    for (int r = 0; r < 4; r++) {
-      const long long e = base + w * 128 + r * 32 + lane;
-      if (fl[r]) {
-        const unsigned fh = (unsigned)(b.dfp[e] >> 32), ev = (unsigned)b.dE[e];
-        fo |= fh;
-        fa &= fh;
-        eo |= ev;
-        ea &= ev;
-      }
-    }
-    fo = __reduce_or_sync(kFull, fo);
-    fa = __reduce_and_sync(kFull, fa);
-    eo = __reduce_or_sync(kFull, eo);
-    ea = __reduce_and_sync(kFull, ea);
-    if (lane == 0) {
-      wkey[w][0] = fo;
-      wkey[w][1] = fa;
-      wkey[w][2] = eo;
-      wkey[w][3] = ea;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int ww = 1; ww < 8; ww++) {
-        fo |= wkey[ww][0];
-        fa &= wkey[ww][1];
-        eo |= wkey[ww][2];
-        ea &= wkey[ww][3];
-      }
-      atomicOr(&b.st->fph_or, fo);
-      atomicAnd(&b.st->fph_and, fa);
-      atomicOr(&b.st->e_or, eo);
-      atomicAnd(&b.st->e_and, ea);
+    const long long u = warp_append(&b.st->nU, fresh);
+    if (fresh) {
+      b.uE[u] = E;
+      b.uFp[u] = fp;
+      b.uRep[u] = ~0u;
+      b.uSlot[u] = (int32_t)slot;
+      b.hval[slot] = (int32_t)u;
     }
   }
 }
 
-// Radix digit of element e of buffer `src` at pass `pass` (0..1: bytes of fp >> 48, 2..5: energy bytes).
-__device__ __forceinline__ unsigned radix_digit(const PqBufs& b, int src, long long e, int pass) {
-  if (pass < 2) return (unsigned)(b.sfp[src][e] >> (48 + 8 * pass)) & 255u;
-  return ((unsigned)b.sE[src][e] >> (8 * (pass - 2))) & 255u;
-}
-
-__global__ void __launch_bounds__(256) radix_hist_kernel(PqBufs b, int pass) {
-  const long long n = b.st->nS;
-  const long long nblk = tiles_of(n);
-  const long long base = (long long)blockIdx.x * kTile;
-  const unsigned mask = sort_mask(b.st);
-  if (base >= n || !((mask >> pass) & 1u)) return;
-  __shared__ unsigned h[256];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int src = sort_src(mask, pass);
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + (threadIdx.x >> 5) * 128 + r * 32 + lane_id();
-    if (e < n) atomicAdd(&h[radix_digit(b, src, e, pass)], 1u);
-  }
-  __syncthreads();
-  b.counts[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
-}
-
-// Exclusive scan of the digit-major radix counts (256 x blocks of this round), in three phases over
-// segments of kSeg entries: segment sums, a scan of the sums, then each segment with its offset.
-constexpr int kSeg = 4096;
-
-__device__ __forceinline__ long long radix_count_len(const PqBufs& b) { return 256 * tiles_of(b.st->nS); }
-
-__global__ void __launch_bounds__(256) seg_reduce_kernel(PqBufs b, int pass) {
-  if (!((sort_mask(b.st) >> pass) & 1u)) return;
-  const long long n = radix_count_len(b);
-  const long long lo = (long long)blockIdx.x * kSeg;
-  unsigned s = 0;
-  if (lo < n)
-    for (long long i = lo + threadIdx.x; i < min(n, lo + kSeg); i += 256) s += b.counts[i];
-  s = __reduce_add_sync(kFull, s);
-  __shared__ unsigned w[8];
-  if (lane_id() == 0) w[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned t = 0;
-    for (int i = 0; i < 8; i++) t += w[i];
-    b.bsum[blockIdx.x] = t;  // zero for segments past this round's length
-  }
-}
-
-__global__ void __launch_bounds__(1024) seg_scan_sums_kernel(unsigned* a, int n, const PqState* st, int pass) {
-  if (!((sort_mask(st) >> pass) & 1u)) return;
-  __shared__ unsigned part[1024];
-  const int t = threadIdx.x;
-  const int chunk = (n + 1023) / 1024;
-  const int lo = t * chunk, hi = min(n, lo + chunk);
-  unsigned s = 0;
-  for (int i = lo; i < hi; i++) s += a[i];
-  part[t] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    unsigned v = t >= off ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  unsigned run = t ? part[t - 1] : 0;
-  for (int i = lo; i < hi; i++) {
-    const unsigned v = a[i];
-    a[i] = run;
-    run += v;
-  }
-}
-
-__global__ void __launch_bounds__(256) seg_down_kernel(PqBufs b, int pass) {
-  const long long n = radix_count_len(b);
-  const long long lo = (long long)blockIdx.x * kSeg;
-  if (lo >= n || !((sort_mask(b.st) >> pass) & 1u)) return;
-  // thread t owns entries lo + 16t .. lo + 16t + 15
-  const long long first = lo + 16 * threadIdx.x;
-  unsigned v[16], s = 0;
-#pragma unroll
-  for (int i = 0; i < 16; i++) {
-    v[i] = first + i < n ? b.counts[first + i] : 0u;
-    s += v[i];
-  }
-  // block exclusive scan of the thread sums
-  unsigned incl = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned x = __shfl_up_sync(kFull, incl, o);
-    if (lane_id() >= o) incl += x;
-  }
-  __shared__ unsigned wsum[8];
-  if (lane_id() == 31) wsum[threadIdx.x >> 5] = incl;
-  __syncthreads();
-  unsigned wofs = 0;
-  for (int w = 0; w < (int)(threadIdx.x >> 5); w++) wofs += wsum[w];
-  unsigned run = b.bsum[blockIdx.x] + wofs + incl - s;
-#pragma unroll
-  for (int i = 0; i < 16; i++)
-    if (first + i < n) {
-      b.counts[first + i] = run;
-      run += v[i];
+// Dedup, second pass: each survivor finds its key's slot and lowers the representative to the smallest
+// (pivot, column) -- the pivots are in key order, so this is the sequential definition's first occurrence.
+template <bool SEED>
+__global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b, int n_seeds) {
+  const long long n = dense_n<SEED>(b, n_seeds);
+  const uint64_t mask = (1ull << b.hs_log2) - 1;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int E = b.dE[i];
+    if (E == INT32_MAX) continue;
+    const uint64_t k = dedup_key(E, b.dFp[i]);
+    uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
+    for (uint64_t it = 0; it <= mask; it++) {
+      if (b.hkey[s] == k) break;
+      s = (s + 1) & mask;
     }
-}
-
-__global__ void __launch_bounds__(256) radix_scatter_kernel(PqBufs b, int pass) {
-  const long long n = b.st->nS;
-  const long long nblk = tiles_of(n);
-  const long long base = (long long)blockIdx.x * kTile;
-  const unsigned mask = sort_mask(b.st);
-  if (base >= n || !((mask >> pass) & 1u)) return;
-  __shared__ unsigned cnt[8][256];
-  const int w = threadIdx.x >> 5, lane = lane_id();
-  const int src = sort_src(mask, pass), dst = src ^ 1;
-  for (int d = threadIdx.x; d < 8 * 256; d += 256) (&cnt[0][0])[d] = 0;
-  __syncthreads();
-  unsigned dig[4];
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + w * 128 + r * 32 + lane;
-    dig[r] = e < n ? radix_digit(b, src, e, pass) : 256u;
-    const unsigned peers = __match_any_sync(kFull, dig[r]);
-    if (dig[r] < 256u && lane == __ffs(peers) - 1) cnt[w][dig[r]] += __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  {  // per digit: exclusive prefix over warps, plus the block's global offset
-    const int d = threadIdx.x;
-    unsigned run = b.counts[(long long)d * nblk + blockIdx.x];
-    for (int ww = 0; ww < 8; ww++) {
-      const unsigned v = cnt[ww][d];
-      cnt[ww][d] = run;
-      run += v;
-    }
-  }
-  __syncthreads();
-  for (int r = 0; r < 4; r++) {
-    const long long e = base + w * 128 + r * 32 + lane;
-    const unsigned peers = __match_any_sync(kFull, dig[r]);
-    if (dig[r] < 256u) {
-      const unsigned o = cnt[w][dig[r]] + __popc(peers & ((1u << lane) - 1u));
-      b.sE[dst][o] = b.sE[src][e];
-      b.sfp[dst][o] = b.sfp[src][e];
-      b.sidx[dst][o] = b.sidx[src][e];
-    }
-    __syncwarp();
-    if (dig[r] < 256u && lane == __ffs(peers) - 1) cnt[w][dig[r]] += __popc(peers);
-    __syncwarp();
+    const unsigned rep = SEED ? (unsigned)i << kColBits
+                              : ((unsigned)(i / b.width) << kColBits) | (unsigned)(i % b.width);
+    atomicMin(&b.uRep[b.hval[s]], rep);
   }
 }
 
-// After the radix passes the keys are ordered by (E, fp >> 48) and, within equal pairs, by input order
-// (pop, pos).  Each run of equal (E, fp >> 48) is put in (fp, pop, pos) order in place by the thread at
-// its start (runs are disjoint; they are short, fingerprints being uniform 64-bit keys).
-__global__ void __launch_bounds__(256) sort_fixup_kernel(PqBufs b) {
-  const long long n = b.st->nS;
-  const int f = sort_final(b.st);
-  int32_t* E = b.sE[f];
-  uint64_t* fp = b.sfp[f];
-  int32_t* ix = b.sidx[f];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < n; i += (long long)gridDim.x * blockDim.x) {
-    const int Ei = E[i];
-    const unsigned hi = (unsigned)(fp[i] >> 48);
-    if (E[i + 1] != Ei || (unsigned)(fp[i + 1] >> 48) != hi) continue;
-    if (i > 0 && E[i - 1] == Ei && (unsigned)(fp[i - 1] >> 48) == hi) continue;
-    long long j = i + 2;
-    while (j < n && E[j] == Ei && (unsigned)(fp[j] >> 48) == hi) j++;
-    for (long long a = i + 1; a < j; a++) {  // insertion sort of [i, j) by (fp, index)
-      const uint64_t kf = fp[a];
-      const int32_t ki = ix[a];
-      long long c = a;
-      while (c > i && (fp[c - 1] > kf || (fp[c - 1] == kf && ix[c - 1] > ki))) {
-        fp[c] = fp[c - 1];
-        ix[c] = ix[c - 1];
-        c--;
-      }
-      fp[c] = kf;
-      ix[c] = ki;
-    }
-  }
+// The round's smallest survivor energy.
+__global__ void __launch_bounds__(256) pq_u_min_kernel(PqBufs b) {
+  const long long n = b.st->nU;
+  int m = INT32_MAX;
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+    m = min(m, b.uE[u]);
+  m = __reduce_min_sync(kFull, m);
+  if (lane_id() == 0 && m != INT32_MAX) atomicMin(&b.st->minE_round, m);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Best, merge, round end
-// ---------------------------------------------------------------------------------------------
+// The histogram's energy window, from the smallest seed energy (improvements stay far inside it).
+__global__ void pq_set_window_kernel(PqBufs b) {
+  PqState* st = b.st;
+  st->E_base = st->minE_round == INT32_MAX ? 0 : max(0, st->minE_round - kNB / 2);
+}
+
+// Survivor histogram, and the smallest fingerprint among the smallest-energy survivors.
+__global__ void __launch_bounds__(256) pq_u_hist_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = st->nU;
+  const int Eb = st->E_base, mE = st->minE_round;
+  uint64_t mf = ~0ull;
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    const int E = b.uE[u];
+    const int bin = e_bin(E, Eb);
+    atomicAdd(&b.hU[bin], 1u);
+    atomicAdd(&b.hU2[bin / kCoarse], 1u);
+    if (E == mE) mf = min(mf, b.uFp[u]);
+  }
+  if (mf != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(&st->minfp_round), (unsigned long long)mf);
+}
+
+// The representative of the smallest survivor key (unique).
+__global__ void __launch_bounds__(256) pq_u_best_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = st->nU;
+  const int mE = st->minE_round;
+  const uint64_t mf = st->minfp_round;
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
+    if (b.uE[u] == mE && b.uFp[u] == mf) st->best_rep_round = b.uRep[u];
+}
+
+// One thread: the best (a strict improvement, as in Algorithm 2; for the seeds, the smallest seed) and
+// the round's counters.
+template <bool SEED>
 __global__ void pq_best_kernel(PqBufs b) {
   PqState* st = b.st;
-  if (st->b == 0) return;
+  if (!SEED && st->b == 0) return;
+  const unsigned rep = st->best_rep_round;
+  if (SEED) {
+    if (st->nU > 0 && (rep >> kColBits) < (unsigned)b.n_seeds) {
+      st->best_E = st->minE_round;
+      st->best_fp = st->minfp_round;
+      const int q = (int)(rep >> kColBits);
+      for (int t = 0; t < b.W; t++) b.best_seq[t] = b.seeds[(size_t)q * b.W + t];
+    }
+    return;
+  }
   st->survivors += st->nU;
-  if (st->nU > 0 && b.uE[0] < st->best_E) {
-    st->best_E = b.uE[0];
-    st->best_fp = b.ufp[0];
-    const int q = b.uidx[0] / b.width, col = b.uidx[0] % b.width;
-    pq_child(b.Pseq[st->cur] + (size_t)q * b.W, b, col, b.best_seq);
+  if (st->nU > 0 && (rep >> kColBits) >= (unsigned)st->b) {  // every survivor has a representative
+    st->error = 1;
+    return;
+  }
+  if (st->nU > 0 && st->minE_round < st->best_E) {
+    st->best_E = st->minE_round;
+    st->best_fp = st->minfp_round;
+    pq_child(b.pivSeq + (size_t)(rep >> kColBits) * b.W, b, (int)(rep & ((1u << kColBits) - 1u)), b.best_seq);
     st->improvements++;
     st->u = 0;
   } else {
@@ -714,150 +802,113 @@ __global__ void pq_best_kernel(PqBufs b) {
   }
 }
 
-// Number of open-set (rest) entries among the first o merged outputs.
-// The search may start from any [lo, hi] that contains the answer (the predicate is monotone in mid).
-__device__ __forceinline__ long long merge_split_in(const int32_t* RE, const uint64_t* Rfp, const int32_t* UE,
-                                                    const uint64_t* Ufp, long long o, long long lo, long long hi) {
-  while (lo < hi) {
-    const long long mid = (lo + hi) >> 1;
-    const long long ui = o - mid - 1;
-    if (key_lt(RE[mid], Rfp[mid], UE[ui], Ufp[ui]))
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  return lo;
+// Whether a key of bin `bin` is inside the cut.
+__device__ __forceinline__ bool below_cut(const PqState* st, int bin, int E, uint64_t fp) {
+  if (st->sel_need < 0) return true;  // no cut
+  return bin < st->sel_bin || (bin == st->sel_bin && key_le(E, fp, st->sel_E, st->sel_fp));
 }
 
-__device__ __forceinline__ long long merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
-                                                 const uint64_t* Ufp, long long nU, long long o) {
-  return merge_split_in(RE, Rfp, UE, Ufp, o, max(0ll, o - nU), min(o, nR));
-}
-
-// The same split found by the whole block (every thread calls it, gets the answer): each step tests
-// blockDim increasing points of the range at once, and the number that test true (a prefix, the
-// predicate being monotone) narrows the range by a factor of blockDim + 1 -- three steps for 2^22.
-__device__ long long block_merge_split(const int32_t* RE, const uint64_t* Rfp, long long nR, const int32_t* UE,
-                                       const uint64_t* Ufp, long long nU, long long o) {
-  long long lo = max(0ll, o - nU), hi = min(o, nR);
-  const long long nt = blockDim.x, t = threadIdx.x;
-  while (lo < hi) {  // the same on every thread
-    const long long span = hi - lo;
-    const bool dense = span <= nt;  // then the points are lo .. hi - 1 and one step ends the search
-    auto point = [&](long long k) { return dense ? lo + k : lo + (span * (k + 1)) / (nt + 1); };
-    const long long np = dense ? span : nt;
-    bool pred = false;
-    if (t < np) {
-      const long long mid = point(t), ui = o - mid - 1;
-      pred = key_lt(RE[mid], Rfp[mid], UE[ui], Ufp[ui]);
-    }
-    const long long c = __syncthreads_count(pred);
-    const long long nlo = c > 0 ? point(c - 1) + 1 : lo;
-    hi = c < np ? point(c) : hi;
-    lo = nlo;
-  }
-  return lo;
-}
-
-// Merge path in tiles: a block takes kMergeTile consecutive outputs and finds the tile's two ends
-// (block_merge_split); the tile's keys of both inputs (kMergeTile in all) are then staged in
-// shared memory, and each thread finds its own output's source by a search there.  Warps write 32
-// consecutive outputs at a time and copy their sequences together (lane l moves word l mod W of output
-// l / W, and so on), so every store is coalesced.
-constexpr int kMergeTile = 2048;
-
-__global__ void __launch_bounds__(256) pq_merge_kernel(PqBufs b) {
-  const PqState* st = b.st;
-  if (st->b == 0) return;
-  const int cur = st->cur, nxt = cur ^ 1;
-  const long long nb = st->b, nR = st->nP - nb, nU = st->nU;
-  const long long nOut = min(b.cap, nR + nU);
-  const int32_t* RE = b.PE[cur] + nb;
-  const uint64_t* Rfp = b.Pfp[cur] + nb;
-  const uint64_t* Rseq = b.Pseq[cur] + nb * b.W;
-  __shared__ int32_t sE[kMergeTile];   // the tile's open-set keys at [0, nr), survivor keys at [nr, nr + nu)
-  __shared__ uint64_t sF[kMergeTile];
-  int ins = 0;
-  for (long long o0 = (long long)blockIdx.x * kMergeTile; o0 < nOut; o0 += (long long)gridDim.x * kMergeTile) {
-    const long long o1 = min(o0 + kMergeTile, nOut);
-    __syncthreads();  // the previous tile's keys are no longer read
-    const long long ra = block_merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o0);
-    const long long rb = block_merge_split(RE, Rfp, nR, b.uE, b.ufp, nU, o1);
-    const long long ua = o0 - ra;
-    const int nr = (int)(rb - ra), nu = (int)(o1 - rb - ua);
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      sE[i] = RE[ra + i];
-      sF[i] = Rfp[ra + i];
-    }
-    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
-      sE[nr + i] = b.uE[ua + i];
-      sF[nr + i] = b.ufp[ua + i];
-    }
-    __syncthreads();
-    for (long long ob = o0 + (threadIdx.x & ~31); ob < o1; ob += blockDim.x) {
-      const long long o = ob + lane_id();
-      int kind = 0, src = 0, col = 0;  // kind: 0 none, 1 open set entry src, 2 flip col of pivot src, 3 rotation
-      if (o < o1) {
-        const int ol = (int)(o - o0);
-        int lo = max(0, ol - nu), hi = min(ol, nr);  // open-set entries among the tile's first ol outputs
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          const int uj = nr + ol - mid - 1;
-          if (key_lt(sE[mid], sF[mid], sE[uj], sF[uj]))
-            lo = mid + 1;
-          else
-            hi = mid;
-        }
-        const int al = lo, ul = ol - lo;
-        const bool from_rest = al < nr && (ul >= nu || key_lt(sE[al], sF[al], sE[nr + ul], sF[nr + ul]));
-        if (from_rest) {
-          b.PE[nxt][o] = sE[al];
-          b.Pfp[nxt][o] = sF[al];
-          kind = 1;
-          src = (int)(ra + al);
-        } else {
-          const long long ui = ua + ul;
-          const int q = b.uidx[ui] / b.width;
-          col = b.uidx[ui] % b.width;
-          b.PE[nxt][o] = sE[nr + ul];
-          b.Pfp[nxt][o] = sF[nr + ul];
-          kind = col < b.L ? 2 : 3;
-          src = q;
-          if (kind == 3) pq_child(b.Pseq[cur] + (size_t)q * b.W, b, col, b.Pseq[nxt] + o * b.W);
-          ins += h_insert(b, sF[nr + ul]);
-        }
-      }
-      for (int t = lane_id(); t < 32 * b.W; t += 32) {
-        const int oo = t / b.W, word = t - oo * b.W;
-        const int k2 = __shfl_sync(kFull, kind, oo), s2 = __shfl_sync(kFull, src, oo), c2 = __shfl_sync(kFull, col, oo);
-        if (k2 == 1) {
-          b.Pseq[nxt][(ob + oo) * b.W + word] = Rseq[(long long)s2 * b.W + word];
-        } else if (k2 == 2) {
-          const uint64_t wv = b.Pseq[cur][(size_t)s2 * b.W + word];
-          b.Pseq[nxt][(ob + oo) * b.W + word] = wv ^ (word == (c2 >> 6) ? 1ull << (c2 & 63) : 0ull);
-        }
-      }
-    }
-  }
-  h_count(b, ins);
-}
-
-// One block: the split of the merged output at the cap (how many open-set entries stayed) by the block
-// search, then the round's bookkeeping by thread 0.
-__global__ void __launch_bounds__(256) pq_round_end_kernel(PqBufs b) {
+// Pool pass: the entries beyond the cut are evicted (slot freed, histogram updated).
+__global__ void __launch_bounds__(256) pq_evict_kernel(PqBufs b) {
   PqState* st = b.st;
-  if (st->b == 0) return;
-  const int cur = st->cur;
-  const long long nb = st->b, nR = st->nP - nb, nU = st->nU;
-  const long long nOut = min(b.cap, nR + nU);
-  const long long a = block_merge_split(b.PE[cur] + nb, b.Pfp[cur] + nb, nR, b.uE, b.ufp, nU, nOut);
-  if (threadIdx.x != 0) return;
-  st->admitted += nOut - a;
-  st->evicted += nR - a;
-  st->nP = nOut;
-  st->expansions += nb;
-  st->rounds++;
-  st->cur = cur ^ 1;
+  if (st->sel_need < 0) return;
+  const int Eb = st->E_base;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.cap; base += stride) {
+    const long long i = base + threadIdx.x;
+    bool out = false;
+    int bin = 0;
+    if (i < b.cap) {
+      const int E = b.pE[i];
+      if (E != INT32_MAX) {
+        bin = e_bin(E, Eb);
+        out = !below_cut(st, bin, E, b.pFp[i]);
+      }
+    }
+    const long long o = warp_append(&st->free_top, out);
+    if (out) {
+      b.freeIds[o] = (int32_t)i;
+      b.pE[i] = INT32_MAX;
+      atomicSub(&b.hP[bin], 1u);
+      atomicSub(&b.hP2[bin / kCoarse], 1u);
+    }
+    warp_add(&st->ev_round, out ? 1 : 0);
+  }
+}
+
+// Survivor pass: the survivors inside the cut take a free slot (the sequence built from the pivot, or
+// copied from the seed) and enter the visited set; every survivor clears its dedup slot.
+template <bool SEED>
+__global__ void __launch_bounds__(256) pq_admit_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = st->nU;
+  const int Eb = st->E_base;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long u = base + threadIdx.x;
+    bool in = false;
+    int E = 0, bin = 0;
+    uint64_t fp = 0;
+    if (u < n) {
+      E = b.uE[u];
+      fp = b.uFp[u];
+      bin = e_bin(E, Eb);
+      in = below_cut(st, bin, E, fp);
+      b.hkey[b.uSlot[u]] = 0ull;
+    }
+    // free slots come off the top of the stack, one atomic per warp
+    const unsigned m = __ballot_sync(kFull, in);
+    long long top = 0;
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      if (lane_id() == leader)
+        top = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&st->free_top),
+                                   (unsigned long long)(-(long long)__popc(m)));
+      top = __shfl_sync(kFull, top, leader);
+    }
+    int ins = 0;
+    const long long o = top - 1 - __popc(m & ((1u << lane_id()) - 1u));
+    if (in && o < 0) {  // more admissions than free slots: only an inconsistent state gets here
+      st->error = 1;
+      in = false;
+    }
+    const unsigned rep = in ? b.uRep[u] : 0u;
+    if (in && (rep >> kColBits) >= (unsigned)(SEED ? b.n_seeds : st->b)) {  // every survivor has one (pass 2)
+      st->error = 1;
+      in = false;
+    }
+    if (in) {
+      const int id = b.freeIds[o];
+      b.pE[id] = E;
+      b.pFp[id] = fp;
+      if (SEED) {
+        for (int t = 0; t < b.W; t++) b.pSeq[(size_t)id * b.W + t] = b.seeds[(size_t)(rep >> kColBits) * b.W + t];
+      } else {
+        pq_child(b.pivSeq + (size_t)(rep >> kColBits) * b.W, b, (int)(rep & ((1u << kColBits) - 1u)),
+                 b.pSeq + (size_t)id * b.W);
+      }
+      atomicAdd(&b.hP[bin], 1u);
+      atomicAdd(&b.hP2[bin / kCoarse], 1u);
+      ins = h_insert(b, fp);
+    }
+    h_count(b, ins);
+    warp_add(&st->adm_round, in ? 1 : 0);
+  }
+}
+
+template <bool SEED>
+__global__ void pq_round_end_kernel(PqBufs b) {
+  PqState* st = b.st;
+  if (SEED) {
+    st->nP = st->adm_round;
+  } else {
+    if (st->b == 0) return;
+    st->nP = st->nP - st->b - st->ev_round + st->adm_round;
+    st->admitted += st->adm_round;
+    st->evicted += st->ev_round;
+    st->expansions += st->b;
+    st->rounds++;
+  }
   const long long slots = 1ll << b.H_log2;
   if (st->h_size * 4 > slots * 3) st->error = 1;
 }
@@ -877,25 +928,19 @@ __global__ void pq_write_stats_kernel(PqBufs b, int32_t* best_E, labs_pq_stats* 
   out->status = st->error ? LABS_ERR_CAPACITY : LABS_OK;
 }
 
-// Issues compaction (MODE) over at most `max_n` elements.
-template <int MODE>
-void issue_compact(const PqBufs& b, long long max_n, long long* total, cudaStream_t st) {
-  const long long nblk = std::max(1ll, (max_n + kTile - 1) / kTile);
-  compact_count_kernel<MODE><<<(unsigned)nblk, 256, 0, st>>>(b);
-  scan_kernel<<<1, 1024, 0, st>>>(b.bsum, nblk, total);
-  compact_scatter_kernel<MODE><<<(unsigned)nblk, 256, 0, st>>>(b);
-}
-
 }  // namespace
 
 int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                      int32_t* best_E, labs_pq_stats* stats, cudaStream_t st) {
   const int L = cfg->L, W = (L + 63) / 64;
+  if (cfg->B > kSortMax) return LABS_ERR_INVALID_ARG;
   Layout ly;
   if (!make_layout(ly, L, 0, 0, kPqM)) return LABS_ERR_INVALID_ARG;
   const int width = L + 2 * cfg->T_r;
-  const long long nmax = std::max<long long>((long long)cfg->B * width, n_seeds);
-  const long long nblk = (nmax + kTile - 1) / kTile;
+  const long long n_dense = std::max<long long>((long long)cfg->B * width, n_seeds);
+  int hs_log2 = 10;
+  while ((1ll << hs_log2) < 2 * n_dense) hs_log2++;
+  const long long cap = cfg->cap;
   // workspace layout (one region, 256-byte aligned pieces)
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -903,14 +948,14 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t oPE0 = take(4 * cfg->cap), oPE1 = take(4 * cfg->cap);
-  const size_t oPf0 = take(8 * cfg->cap), oPf1 = take(8 * cfg->cap);
-  const size_t oPs0 = take(8 * cfg->cap * W), oPs1 = take(8 * cfg->cap * W);
-  const size_t odE = take(4 * nmax), odf = take(8 * nmax);
-  const size_t osE0 = take(4 * nmax), osE1 = take(4 * nmax), osf0 = take(8 * nmax), osf1 = take(8 * nmax);
-  const size_t osi0 = take(4 * nmax), osi1 = take(4 * nmax);
-  const size_t ouE = take(4 * nmax), ouf = take(8 * nmax), oui = take(4 * nmax);
-  const size_t ocnt = take(4 * 256 * nblk), obs = take(4 * (nblk + 1));
+  const size_t opE = take(4 * cap), opF = take(8 * cap), opS = take(8 * cap * W), ofree = take(4 * cap);
+  const size_t ohP = take(4 * kNB), ohP2 = take(4 * kNC), ohU = take(4 * kNB), ohU2 = take(4 * kNC);
+  const size_t opop = take(4 * (size_t)cfg->B), opivE = take(4 * (size_t)cfg->B), opivF = take(8 * (size_t)cfg->B);
+  const size_t opivS = take(8 * (size_t)cfg->B * W);
+  const size_t ocand = take(4 * (size_t)(cap + n_dense));
+  const size_t odE = take(4 * n_dense), odF = take(8 * n_dense);
+  const size_t ohk = take(8ull << hs_log2), ohv = take(4ull << hs_log2);
+  const size_t ouE = take(4 * n_dense), ouF = take(8 * n_dense), ouR = take(4 * n_dense), ouS = take(4 * n_dense);
   const size_t ozt = take(8 * L), ost = take(sizeof(PqState)), obest = take(8 * W);
   const size_t oH = take(8ull << cfg->H_log2);
   char* base = static_cast<char*>(ws_get(ctx, kWsPq0, off));
@@ -922,81 +967,112 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   b.Tr = cfg->T_r;
   b.width = width;
   b.H_log2 = cfg->H_log2;
-  b.cap = cfg->cap;
+  b.cap = cap;
   b.max_exp = cfg->max_expansions;
   b.T_u = cfg->T_u;
-  b.PE[0] = reinterpret_cast<int32_t*>(base + oPE0);
-  b.PE[1] = reinterpret_cast<int32_t*>(base + oPE1);
-  b.Pfp[0] = reinterpret_cast<uint64_t*>(base + oPf0);
-  b.Pfp[1] = reinterpret_cast<uint64_t*>(base + oPf1);
-  b.Pseq[0] = reinterpret_cast<uint64_t*>(base + oPs0);
-  b.Pseq[1] = reinterpret_cast<uint64_t*>(base + oPs1);
+  b.hs_log2 = hs_log2;
+  b.cand_cap = cap + n_dense;
+  b.n_seeds = n_seeds;
+  b.pE = reinterpret_cast<int32_t*>(base + opE);
+  b.pFp = reinterpret_cast<uint64_t*>(base + opF);
+  b.pSeq = reinterpret_cast<uint64_t*>(base + opS);
+  b.freeIds = reinterpret_cast<int32_t*>(base + ofree);
+  b.hP = reinterpret_cast<unsigned*>(base + ohP);
+  b.hP2 = reinterpret_cast<unsigned*>(base + ohP2);
+  b.hU = reinterpret_cast<unsigned*>(base + ohU);
+  b.hU2 = reinterpret_cast<unsigned*>(base + ohU2);
+  b.popId = reinterpret_cast<int32_t*>(base + opop);
+  b.pivE = reinterpret_cast<int32_t*>(base + opivE);
+  b.pivFp = reinterpret_cast<uint64_t*>(base + opivF);
+  b.pivSeq = reinterpret_cast<uint64_t*>(base + opivS);
+  b.candId = reinterpret_cast<int32_t*>(base + ocand);
   b.dE = reinterpret_cast<int32_t*>(base + odE);
-  b.dfp = reinterpret_cast<uint64_t*>(base + odf);
-  b.sE[0] = reinterpret_cast<int32_t*>(base + osE0);
-  b.sE[1] = reinterpret_cast<int32_t*>(base + osE1);
-  b.sfp[0] = reinterpret_cast<uint64_t*>(base + osf0);
-  b.sfp[1] = reinterpret_cast<uint64_t*>(base + osf1);
-  b.sidx[0] = reinterpret_cast<int32_t*>(base + osi0);
-  b.sidx[1] = reinterpret_cast<int32_t*>(base + osi1);
+  b.dFp = reinterpret_cast<uint64_t*>(base + odF);
+  b.hkey = reinterpret_cast<uint64_t*>(base + ohk);
+  b.hval = reinterpret_cast<int32_t*>(base + ohv);
   b.uE = reinterpret_cast<int32_t*>(base + ouE);
-  b.ufp = reinterpret_cast<uint64_t*>(base + ouf);
-  b.uidx = reinterpret_cast<int32_t*>(base + oui);
-  b.counts = reinterpret_cast<unsigned*>(base + ocnt);
-  b.bsum = reinterpret_cast<unsigned*>(base + obs);
+  b.uFp = reinterpret_cast<uint64_t*>(base + ouF);
+  b.uRep = reinterpret_cast<unsigned*>(base + ouR);
+  b.uSlot = reinterpret_cast<int32_t*>(base + ouS);
   b.ztab = reinterpret_cast<uint64_t*>(base + ozt);
   b.st = reinterpret_cast<PqState*>(base + ost);
   b.best_seq = reinterpret_cast<uint64_t*>(base + obest);
   b.H = reinterpret_cast<uint64_t*>(base + oH);
   b.seeds = seeds;
-  PqState* dst = b.st;
 
-  // ---- set-up: visited set, Zobrist keys, seeds sorted by (E, fp, index), de-duplicated, admitted
+  const unsigned g_pool = (unsigned)std::max(1ll, std::min<long long>((cap + 255) / 256, (long long)ctx->num_sms * 16));
+  const unsigned g_dense =
+      (unsigned)std::max(1ll, std::min<long long>((n_dense + 255) / 256, (long long)ctx->num_sms * 16));
+  const size_t sort_smem = (size_t)kSortMax * 16;
+  if (cudaFuncSetAttribute(pq_pop_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem) !=
+      cudaSuccess)
+    return LABS_ERR_CUDA;
+
+  // The survivor path, shared by the seeds and every round: dedup, best, cut, eviction, admission.
+  auto survivor_path = [&](bool seed, cudaStream_t s) {
+    if (seed) {
+      pq_dedup_insert_kernel<true><<<g_dense, 256, 0, s>>>(b, n_seeds);
+      pq_dedup_rep_kernel<true><<<g_dense, 256, 0, s>>>(b, n_seeds);
+    } else {
+      pq_dedup_insert_kernel<false><<<g_dense, 256, 0, s>>>(b, n_seeds);
+      pq_dedup_rep_kernel<false><<<g_dense, 256, 0, s>>>(b, n_seeds);
+    }
+    pq_u_min_kernel<<<g_dense, 256, 0, s>>>(b);
+    if (seed) pq_set_window_kernel<<<1, 1, 0, s>>>(b);
+    pq_u_hist_kernel<<<g_dense, 256, 0, s>>>(b);
+    pq_u_best_kernel<<<g_dense, 256, 0, s>>>(b);
+    if (seed)
+      pq_best_kernel<true><<<1, 1, 0, s>>>(b);
+    else
+      pq_best_kernel<false><<<1, 1, 0, s>>>(b);
+    pq_select_kernel<false><<<1, kSelThreads, 0, s>>>(b);
+    pq_gather_kernel<false, false><<<g_pool, 256, 0, s>>>(b);
+    pq_gather_kernel<false, true><<<g_dense, 256, 0, s>>>(b);
+    pq_boundary_kernel<false><<<1, kSelThreads, 0, s>>>(b);
+    pq_evict_kernel<<<g_pool, 256, 0, s>>>(b);
+    if (seed) {
+      pq_admit_kernel<true><<<g_dense, 256, 0, s>>>(b);
+      pq_round_end_kernel<true><<<1, 1, 0, s>>>(b);
+    } else {
+      pq_admit_kernel<false><<<g_dense, 256, 0, s>>>(b);
+      pq_round_end_kernel<false><<<1, 1, 0, s>>>(b);
+    }
+    cudaMemsetAsync(b.hU, 0, 4 * kNB, s);
+    cudaMemsetAsync(b.hU2, 0, 4 * kNC, s);
+  };
+
+  // ---- set-up: visited set, pool, histograms, dedup table, Zobrist keys; the seeds go through the
+  // survivor path into the empty pool (equal seeds kept once, the cap smallest admitted)
   if (cudaMemsetAsync(b.H, 0xff, 8ull << cfg->H_log2, st) != cudaSuccess) return LABS_ERR_CUDA;
+  if (cudaMemsetAsync(b.hP, 0, 4 * kNB, st) != cudaSuccess || cudaMemsetAsync(b.hP2, 0, 4 * kNC, st) != cudaSuccess ||
+      cudaMemsetAsync(b.hU, 0, 4 * kNB, st) != cudaSuccess || cudaMemsetAsync(b.hU2, 0, 4 * kNC, st) != cudaSuccess ||
+      cudaMemsetAsync(b.hkey, 0, 8ull << hs_log2, st) != cudaSuccess)
+    return LABS_ERR_CUDA;
   pq_ztab_kernel<<<(L + 255) / 256, 256, 0, st>>>(b.ztab, L);
-  pq_state_init_kernel<<<1, 1, 0, st>>>(dst, n_seeds);
+  pq_init_kernel<<<g_pool, 256, 0, st>>>(b);
   pq_seed_kernel<<<(unsigned)std::min<long long>((n_seeds + kPqWarps - 1) / kPqWarps, ctx->num_sms * 16), 32 * kPqWarps,
                    0, st>>>(b, n_seeds);
-  auto sort_and_dedup = [&](long long max_n, cudaStream_t s) {
-    const unsigned nb = (unsigned)std::max(1ll, (max_n + kTile - 1) / kTile);
-    issue_compact<0>(b, max_n, &dst->nS, s);
-    const int nseg = (int)((256ll * nb + kSeg - 1) / kSeg);
-    for (int pass = 0; pass < 6; pass++) {
-      radix_hist_kernel<<<nb, 256, 0, s>>>(b, pass);
-      seg_reduce_kernel<<<nseg, 256, 0, s>>>(b, pass);
-      seg_scan_sums_kernel<<<1, 1024, 0, s>>>(b.bsum, nseg, b.st, pass);
-      seg_down_kernel<<<nseg, 256, 0, s>>>(b, pass);
-      radix_scatter_kernel<<<nb, 256, 0, s>>>(b, pass);
-    }
-    sort_fixup_kernel<<<(unsigned)std::min<long long>((max_n + 255) / 256, (long long)ctx->num_sms * 8), 256, 0, s>>>(b);
-    issue_compact<1>(b, max_n, &dst->nU, s);
-  };
-  sort_and_dedup(n_seeds, st);
-  pq_seed_admit_kernel<<<(unsigned)std::min<long long>((std::min<long long>(n_seeds, cfg->cap) + 255) / 256, 4096), 256, 0,
-                         st>>>(b);
-  pq_seed_finish_kernel<<<1, 1, 0, st>>>(b);
+  survivor_path(true, st);
+  if (cudaGetLastError() != cudaSuccess) return LABS_ERR_CUDA;
 
   // ---- rounds
   const long long max_rounds = (cfg->max_expansions + cfg->B - 1) / cfg->B + 1;
   const unsigned exp_blocks = (unsigned)std::max(1ll, std::min<long long>((cfg->B + kPqWarps - 1) / kPqWarps,
                                                                         (long long)ctx->num_sms * 8));
-  const unsigned merge_blocks =
-      (unsigned)std::max(1ll, std::min<long long>((cfg->cap + kMergeTile - 1) / kMergeTile, (long long)ctx->num_sms * 16));
   // Every round issues the same launches with the same arguments (a round's sizes and stop state live
-  // in device memory), so one round is captured as a CUDA graph and replayed: about 50 launches per
-  // round become one.
-  if (cudaGetLastError() != cudaSuccess) return LABS_ERR_CUDA;
+  // in device memory), so one round is captured as a CUDA graph and replayed.
   if (!ctx->capture_stream && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
     return LABS_ERR_CUDA;
   if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LABS_ERR_CUDA;
   {
     cudaStream_t cs = ctx->capture_stream;
     pq_round_begin_kernel<<<1, 1, 0, cs>>>(b);
+    pq_select_kernel<true><<<1, kSelThreads, 0, cs>>>(b);
+    pq_gather_kernel<true, false><<<g_pool, 256, 0, cs>>>(b);
+    pq_boundary_kernel<true><<<1, kSelThreads, 0, cs>>>(b);
+    pq_pop_sort_kernel<<<1, kSelThreads, sort_smem, cs>>>(b);
     pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, cs>>>(b, ly);
-    sort_and_dedup((long long)cfg->B * width, cs);
-    pq_best_kernel<<<1, 1, 0, cs>>>(b);
-    pq_merge_kernel<<<merge_blocks, 256, 0, cs>>>(b);
-    pq_round_end_kernel<<<1, 256, 0, cs>>>(b);
+    survivor_path(false, cs);
   }
   cudaGraph_t round_graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(ctx->capture_stream, &round_graph);
@@ -1019,7 +1095,7 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
       break;
     }
     if ((r & 31) == 31 || r + 1 == max_rounds) {  // poll the stop flag
-      if (cudaMemcpyAsync(hstop, &dst->stop, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      if (cudaMemcpyAsync(hstop, &b.st->stop, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess) {
         status = LABS_ERR_CUDA;
         break;

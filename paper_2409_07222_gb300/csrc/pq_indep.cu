@@ -339,11 +339,11 @@ __global__ void __launch_bounds__(32 * kIWarps) pq_indep_kernel(IndepArgs a, Lay
         for (int w = lane; w < kBitWords; w += 32) sm.bits[w] = S.pbits[w];
         __syncwarp();
         build_table(sm, ly);
-        fast = pack_c8(sm);
+        fast = pack_c8(sm, ly);
         build_bytes(sm, ly);
         p_all(sm, ly, S.xb, S.cbits, S.P);
       }
-      const int SC = table_sum(sm);
+      const int SC = table_sum(sm, ly);
       {
         const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16);
         const uint32_t* Pw = reinterpret_cast<const uint32_t*>(S.P);

@@ -27,10 +27,17 @@ constexpr int kMaxLens = 96;    // lengths in one launch (kernel parameter table
 constexpr int kMaxPasses = 3;   // lane passes over the tasks of one walk
 // per slot and lane: slot word and choice key (int32 each), plus Delta E when the choice is biased
 __host__ __device__ constexpr int slot_bytes(bool biased) { return biased ? 12 : 8; }
+// threads per block the kernels are compiled for: whole-warp walks run two 8-warp blocks per SM (128
+// registers a thread); half-warp walks run one block of up to 12 warps (24 walks), whose register budget,
+// 65536 / 384 threads, holds the whole step without spills
+__host__ __device__ constexpr int walk_block_threads(int GL) { return GL == 32 ? 256 : 384; }
+__host__ __device__ constexpr int walk_min_blocks(int GL) { return GL == 32 ? 2 : 1; }
 
-struct WalkSmem {
-  ScanSmem s;
-  uint32_t bloom[1024];  // up to 2^15 bits
+// Shared-memory slab of one walk, sized per launch for its lengths (byte offsets, 16-byte aligned):
+// the sequence bits at 0, the tables, the byte-window arrays, the Bloom filter and the per-slot words
+// ([slot][lane of the group]).
+struct SlabPlan {
+  int off_C16, off_C8, off_fwd, off_bwd, off_bloom, off_slots, bytes;
 };
 
 // Per-length entry of a launch: the layout (tiles, windows) and where its walks sit among the items.
@@ -61,6 +68,7 @@ struct WalkParams {
   float lambda;
   uint64_t* seq_out;     // [n_items][W]: the walk's sequence when the launch leaves it
   int32_t* move_log;     // [n_items][2]: first move of the launch (position, Delta E), (-1, 0) if none
+  SlabPlan slab;
   LenEntry len[kMaxLens];
 };
 
@@ -86,24 +94,26 @@ __device__ __forceinline__ uint32_t bloom_idx(uint64_t fp, int j, uint32_t mask)
   return (lo + (uint32_t)j * (hi | 1u)) & mask;
 }
 
-// Every lane returns whether all K probes of fp are set.
+// Every lane of the group returns whether all K probes of fp are set.
+template <int GL>
 __device__ __forceinline__ bool bloom_test(const uint32_t* bloom, uint64_t fp, int K, uint32_t mask) {
-  const int lane = lane_id();
+  const int lane = glane<GL>();
   bool hit = true;
   if (lane < K) {
     uint32_t b = bloom_idx(fp, lane, mask);
     hit = (bloom[b >> 5] >> (b & 31)) & 1u;
   }
-  return __all_sync(kFull, hit);
+  return gall<GL>(hit);
 }
 
+template <int GL>
 __device__ __forceinline__ void bloom_add(uint32_t* bloom, uint64_t fp, int K, uint32_t mask) {
-  const int lane = lane_id();
+  const int lane = glane<GL>();
   if (lane < K) {
     uint32_t b = bloom_idx(fp, lane, mask);
     atomicOr(&bloom[b >> 5], 1u << (b & 31));
   }
-  __syncwarp();
+  gsync<GL>();
 }
 
 __device__ __forceinline__ bool key_less(int Ea, uint64_t fa, int Eb, uint64_t fb) {
@@ -138,11 +148,11 @@ struct PendingFlip {
 };
 
 // Folds the pending move into the slot words of its class.  The class's (task, k) slots are spread over
-// all lanes, task fastest, so that neighbouring lanes touch different banks.
-template <int M, int H>
-__device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, const PendingFlip& pf, int* sl_w) {
+// the group's lanes, task fastest, so that neighbouring lanes touch different banks.
+template <int M, int H, int GL, class S>
+__device__ __forceinline__ void fold_flip(const S& sm, const Layout& ly, const PendingFlip& pf, int* sl_w) {
   constexpr int MH = M / H;
-  const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(pf.cls));
+  const uint8_t* Fc = reinterpret_cast<const uint8_t*>(sm.fwd + cls_words(ly, pf.cls));
   const int pmul = ly.skew ? -64 : -16;  // -4 alpha^2 for the neighbours that change
   const int qc = (pf.pair && pos_cls(ly, ly.c) == pf.cls) ? pos_q(ly, ly.c) : -1;  // the centre
   const int m3 = ly.skew ? pf.qmir + pf.q0f : -1;                                  // 3 q of the pair-product
@@ -152,12 +162,13 @@ __device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, 
   const int task0 = (pf.cls ? ly.ntiles[0] : 0) * H;
   const int qt = ly.tile_first[pf.cls];
   const int mg = ly.fold_magic[pf.cls];
-  int k = (lane_id() * mg) >> 16, tl = lane_id() - k * nt;
-  const int step_k = (32 * mg) >> 16, step_t = 32 - step_k * nt;
+  const int lane = glane<GL>();
+  int k = (lane * mg) >> 16, tl = lane - k * nt;
+  const int step_k = (GL * mg) >> 16, step_t = GL - step_k * nt;
   for (; k < MH;) {
     const int task = task0 + tl;
     const int q = qt + (tl / H) * M + (tl % H) * MH + k;
-    const int idx = ((task >> 5) * MH + k) * 32 + (task & 31);
+    const int idx = ((task / GL) * MH + k) * GL + (task % GL);
     int wv = sl_w[idx];
     const int ms = slot_pos(wv);
     int v = ((int)Fc[max(2 * q - pf.q0f, 0)] - 1) * pf.s0;
@@ -173,7 +184,7 @@ __device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, 
       k++;
     }
   }
-  __syncwarp();
+  gsync<GL>();
 }
 
 // Finish code of a slot, formed by prep: base * 32 + code, where base is the constant part of the
@@ -181,11 +192,12 @@ __device__ __forceinline__ void fold_flip(const ScanSmem& sm, const Layout& ly, 
 // the last move flipped (the state just left), or 31 for no neighbour.  Branch-free: a slot without a
 // pair term reads the table's last entry, which is always zero (lags beyond G).
 constexpr int kNoSlot = 31;
-__device__ __forceinline__ int prep_code(const ScanSmem& sm, const Layout& ly, int word, bool back) {
+template <class S>
+__device__ __forceinline__ int prep_code(const S& sm, const Layout& ly, int word, bool back) {
   const int ms = slot_pos(word);
   const int m = ms < 0 ? -ms : ms;
   const bool pair = ly.skew && m != ly.c && m != 0;
-  const int gd = pair ? ly.c - m : kCLen;
+  const int gd = pair ? ly.c - m : ly.cl;
   const int cg = 8 * (int)sm.C16[gd - 1];
   const int base = slot_Pt(word) + ((gd & 1) ? -cg : cg);
   const int a2 = pair ? 8 : 4;
@@ -193,9 +205,10 @@ __device__ __forceinline__ int prep_code(const ScanSmem& sm, const Layout& ly, i
   return ms == 0 ? kNoSlot : base * 32 + code;
 }
 
-// Task of `lane` in pass `ps`: tile (class, q0), lag range h, whether it exists.
+// Task of group lane `lane` in pass `ps`: tile (class, q0), lag range h, whether it exists.
+template <int GL>
 __device__ __forceinline__ bool lane_task(const Layout& ly, int H, int ps, int lane, int& cls, int& q0, int& h) {
-  const int task = ps * 32 + lane;
+  const int task = ps * GL + lane;
   h = H == 2 ? (task & 1) : 0;
   cls = 0;
   q0 = 0;
@@ -205,34 +218,40 @@ __device__ __forceinline__ bool lane_task(const Layout& ly, int H, int ps, int l
 }
 
 // One walk-step kernel for every length of the launch.  Template: tile size M and lag ranges per tile H
-// (the autotuned "words per thread"); the number of lane passes is per length (<= kMaxPasses).
-// Per-slot state sits in shared memory, lane-major ([slot][lane], conflict-free): the slot word, the
-// step's choice key and, for biased walks, its Delta E.  With `state` the walk runs in chunks of
-// accepted flips and is saved between launches (bits, table, Bloom filter, counters); the sieve slots
-// stay in the output records meanwhile.
+// (the autotuned "words per thread"), lanes per walk GL (32: one walk per warp; 16: one per half-warp,
+// two walks sharing every instruction of the step's serial phases); the number of lane passes is per
+// length (<= kMaxPasses).  Per-slot state sits in the walk's slab, lane-major ([slot][lane], conflict
+// free): the slot word, the step's choice key and, for biased walks, its Delta E.  With `state` the walk
+// runs in chunks of accepted flips and is saved between launches (bits, table, Bloom filter, counters);
+// the sieve slots stay in the output records meanwhile.
 // ONE: a single-length launch -- the length's entry is read at a fixed parameter offset and its
 // Zobrist keys are tabulated once per block in shared memory.  BIASED: the choice key is the proposal
 // score of WalkParams::bias (single-length launches only).
-template <int M, int H, bool ONE, bool BIASED>
-__global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ WalkParams P) {
+template <int M, int H, bool ONE, bool BIASED, int GL>
+__global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
+    walk_kernel(const __grid_constant__ WalkParams P) {
   constexpr int MH = M / H;  // slots owned by a lane per pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int wid = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  WalkSmem& ws = reinterpret_cast<WalkSmem*>(smem_raw)[wid];
-  ScanSmem& sm = ws.s;
-  constexpr int kSlotBytes = slot_bytes(BIASED);
-  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * kSlotBytes) * nwarps);
+  const int gid = threadIdx.x / GL;  // walk slot of this group in the block
+  const int ngroups = blockDim.x / GL;
+  unsigned char* slab = smem_raw + (size_t)gid * P.slab.bytes;
+  ScanView sm;
+  sm.bits = reinterpret_cast<uint32_t*>(slab);
+  sm.C16 = reinterpret_cast<int16_t*>(slab + P.slab.off_C16);
+  sm.C8 = reinterpret_cast<int8_t*>(slab + P.slab.off_C8);
+  sm.fwd = reinterpret_cast<uint32_t*>(slab + P.slab.off_fwd);
+  sm.bwd = reinterpret_cast<uint32_t*>(slab + P.slab.off_bwd);
+  uint32_t* bloom = reinterpret_cast<uint32_t*>(slab + P.slab.off_bloom);
+  uint64_t* ztab = reinterpret_cast<uint64_t*>(smem_raw + (size_t)P.slab.bytes * ngroups);
   if (ONE) {
     const uint64_t zk = stream_key(0, kPurposeZobrist, (uint64_t)P.len[0].ly.L, 0);
     for (int i = threadIdx.x; i < P.len[0].ly.L; i += blockDim.x) ztab[i] = zobrist(zk, i + 1);
     __syncthreads();
   }
-  unsigned char* slot_base = smem_raw + sizeof(WalkSmem) * nwarps + (size_t)wid * P.slot_stride * 32 * kSlotBytes;
-  int* sl_w = reinterpret_cast<int*>(slot_base);  // slot words
-  int* sl_k = sl_w + P.slot_stride * 32;            // choice keys of the step
-  int* sl_d = sl_k + P.slot_stride * 32;            // Delta E of the step (BIASED only; else = key)
-  const int lane = lane_id();
+  int* sl_w = reinterpret_cast<int*>(slab + P.slab.off_slots);  // slot words
+  int* sl_k = sl_w + P.slot_stride * GL;                         // choice keys of the step
+  int* sl_d = sl_k + P.slot_stride * GL;                         // Delta E of the step (BIASED only; else = key)
+  const int lane = glane<GL>();
   const uint32_t bmask = (1u << P.bloom_log2) - 1u;
   const int bwords = 1 << (P.bloom_log2 - 5);
   const int R = P.R;
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
   while (true) {
     unsigned long long item = 0;
     if (lane == 0) item = atomicAdd(P.counter, 1ull);
-    item = __shfl_sync(kFull, item, 0);
+    item = gshfl<GL>(item, 0);
     if ((long long)item >= P.n_items) break;
     int li = 0;
     if (!ONE)
@@ -256,7 +275,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     const uint64_t zkey = stream_key(0, kPurposeZobrist, (uint64_t)ly.L, 0);
     const int32_t E_thr = P.E_thr_dev ? P.E_thr_dev[li] : le.E_thr_value;
     const int W = (ly.L + 63) >> 6;
-    const int NP = (ly.n_tasks + 31) >> 5;
+    const int NP = (ly.n_tasks + GL - 1) / GL;
     const int S = NP * MH;
     labs_candidate* rec = P.out + (int64_t)item * R;
     const float* bias = BIASED ? P.bias + (long long)item * ly.L : nullptr;
@@ -267,11 +286,11 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     // slot positions of this length
     for (int ps = 0; ps < NP; ps++) {
       int cls, q0, h;
-      const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+      const bool has = lane_task<GL>(ly, H, ps, lane, cls, q0, h);
 #pragma unroll
       for (int k = 0; k < MH; k++) {
         const int m = q_pos(ly, cls, q0 + h * MH + k);
-        sl_w[(ps * MH + k) * 32 + lane] = slot_pack((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0, 0);
+        sl_w[(ps * MH + k) * GL + lane] = slot_pack((has && m >= ly.p + 1 && m <= ly.mlast) ? m : 0, 0);
       }
     }
     int cE = INT32_MAX;
@@ -292,11 +311,11 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
 
     // rebuilds everything derived from the bits and the table: windows, int8 table, slot P and signs
     auto derive = [&]() {
-      SC = table_sum(sm);
-      fast = pack_c8(sm);
-      build_bytes(sm, ly);
+      SC = table_sum<GL>(sm, ly);
+      fast = pack_c8<GL>(sm, ly);
+      build_bytes<GL>(sm, ly);
       for (int t = 0; t < S; t++) {
-        int m = slot_pos(sl_w[t * 32 + lane]);
+        int m = slot_pos(sl_w[t * GL + lane]);
         m = m < 0 ? -m : m;
         int word = 0;
         if (m) {
@@ -305,18 +324,18 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           const int a2 = si.pair ? 16 : 4;
           word = slot_pack(s_at(sm, ly, m) * m, a2 * (si.nf + si.nb - si.pair + 2 * Pm));
         }
-        sl_w[t * 32 + lane] = word;
+        sl_w[t * GL + lane] = word;
       }
       pend.on = false;
     };
     // INIT_PARTITIONED_SEQUENCE of a new segment (Algorithm 1)
     auto start_segment = [&]() {
-      for (int t = lane; t < bwords; t += 32) ws.bloom[t] = 0u;
-      build_start(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
+      for (int t = lane; t < bwords; t += GL) bloom[t] = 0u;
+      build_start<GL>(sm, ly, prefix, stream_key(P.seed, kPurposeWalk, (uint64_t)w, (uint64_t)segs));
       segs++;
-      fp = fingerprint(sm, ly.L, zkey);
-      bloom_add(ws.bloom, fp, P.bloom_k, bmask);
-      E = build_table(sm, ly);
+      fp = fingerprint<GL>(sm, ly.L, zkey);
+      bloom_add<GL>(bloom, fp, P.bloom_k, bmask);
+      E = build_table<GL>(sm, ly);
       derive();
       it = 0;
       mprev = 0;
@@ -324,21 +343,21 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
     };
     // new worst sieve slot: largest (E, fp), lowest lane among equals
     auto find_worst = [&]() {
-      int mE = warp_max_i32(lane < R ? cE : INT32_MIN);
+      int mE = gmax<GL>(lane < R ? cE : INT32_MIN);
       uint64_t mf = (lane < R && cE == mE) ? cfp : 0ull;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        uint64_t other = __shfl_xor_sync(kFull, mf, o);
+      for (int o = GL / 2; o > 0; o >>= 1) {
+        uint64_t other = gshfl_xor<GL>(mf, o);
         mf = other > mf ? other : mf;
       }
-      unsigned who = __ballot_sync(kFull, lane < R && cE == mE && cfp == mf);
+      unsigned who = gballot<GL>(lane < R && cE == mE && cfp == mf);
       wE = mE;
       wfp = mf;
       wlane = __ffs(who) - 1;
     };
 
     if (!resumed) {
-      for (int r = lane; r < R; r += 32) {  // empty sieve slots
+      for (int r = lane; r < R; r += GL) {  // empty sieve slots
         rec[r].E = INT32_MAX;
         rec[r].walk = 0;
         rec[r].step = 0;
@@ -366,11 +385,11 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       find_worst();
       if (!need_start) {
         const unsigned char* gb = reinterpret_cast<const unsigned char*>(gh);
-        for (int t = lane; t < kBitWords; t += 32) sm.bits[t] = reinterpret_cast<const uint32_t*>(gb + kStateBits)[t];
-        for (int t = lane; t < kCLen / 2; t += 32)
+        for (int t = lane; t < kBitWords; t += GL) sm.bits[t] = reinterpret_cast<const uint32_t*>(gb + kStateBits)[t];
+        for (int t = lane; t < ly.cl / 2; t += GL)
           reinterpret_cast<uint32_t*>(sm.C16)[t] = reinterpret_cast<const uint32_t*>(gb + kStateC)[t];
-        for (int t = lane; t < bwords; t += 32) ws.bloom[t] = reinterpret_cast<const uint32_t*>(gb + kStateBloom)[t];
-        __syncwarp();
+        for (int t = lane; t < bwords; t += GL) bloom[t] = reinterpret_cast<const uint32_t*>(gb + kStateBloom)[t];
+        gsync<GL>();
         derive();
       }
     }
@@ -384,7 +403,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       if (need_start) start_segment();
       it++;
       if (pend.on) {  // the last move's P bookkeeping
-        fold_flip<M, H>(sm, ly, pend, sl_w);
+        fold_flip<M, H, GL>(sm, ly, pend, sl_w);
         pend.on = false;
       }
       // ---- scan; each lane keeps its best (key, m) where key orders the choice: Delta E, or the
@@ -393,19 +412,19 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       int kprev = INT32_MAX;  // this lane's key of the move back (only its owner sets it)
       for (int ps = 0; ps < NP; ps++) {
         int cls, q0, h;
-        const bool has = lane_task(ly, H, ps, lane, cls, q0, h);
+        const bool has = lane_task<GL>(ly, H, ps, lane, cls, q0, h);
         const int q_first = q0 + h * MH;
         {
           // prep, while no accumulator is live: park each neighbour's Delta E base with its finish code
           // in the key array
           int wv[MH];
 #pragma unroll
-          for (int k = 0; k < MH; k++) wv[k] = sl_w[(ps * MH + k) * 32 + lane];
+          for (int k = 0; k < MH; k++) wv[k] = sl_w[(ps * MH + k) * GL + lane];
           // the move back: the neighbour flipped by the previous move of this segment
           const int kback = (mprev && pos_cls(ly, mprev) == cls) ? pos_q(ly, mprev) - q_first : -1;
 #pragma unroll
           for (int k = 0; k < MH; k++)
-            sl_k[(ps * MH + k) * 32 + lane] = prep_code(sm, ly, wv[k], k == kback);
+            sl_k[(ps * MH + k) * GL + lane] = prep_code(sm, ly, wv[k], k == kback);
         }
         int acc[M];
 #pragma unroll
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           for (int k = 0; k < MH; k++) {
             const int send = h ? acc[k] : acc[MH + k];
             const int keep = h ? acc[MH + k] : acc[k];
-            acc[k] = keep + __shfl_xor_sync(kFull, send, 1);
+            acc[k] = keep + gshfl_xor<GL>(send, 1);
           }
         }
         // finish: keys of this pass's neighbours, then their minimum by a tree of strict comparisons
@@ -435,7 +454,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
 #pragma unroll
         for (int k = 0; k < MH; k++) {
           const int t = ps * MH + k;
-          const int pk = sl_k[t * 32 + lane];
+          const int pk = sl_k[t * GL + lane];
           const int code = pk & 31;
           const int m = m_first + ly.lam * k;
           const int a = acc[k];
@@ -452,8 +471,8 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
             kprev = key;  // the state just left: certainly in the Bloom filter
             key = INT32_MAX;
           }
-          sl_k[t * 32 + lane] = key;
-          if (BIASED) sl_d[t * 32 + lane] = d;
+          sl_k[t * GL + lane] = key;
+          if (BIASED) sl_d[t * GL + lane] = d;
           kv[k] = key;
           mv[k] = m;
           dv[k] = d;
@@ -476,7 +495,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       // ---- select: smallest (key, m) whose neighbour is not in the Bloom filter
       int mstar = -1, kstar = 0, dstar = 0;
       uint64_t nfp = 0;
-      for (int guard = 0; guard <= S * 32; guard++) {
+      for (int guard = 0; guard <= S * GL; guard++) {
         int kmin, mm;
         if (!BIASED) {
           // one reduction on (key, m) while the minimum key is inside the 22-bit window: a key clamped to
@@ -484,24 +503,25 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           constexpr int kHalf = 1 << 21;
           const unsigned comp = bk == INT32_MAX ? 0xffffffffu
                                                 : ((unsigned)(min(max(bk, -kHalf), kHalf - 1) + kHalf) << 10) | (unsigned)bm;
-          const unsigned cmin = warp_min_u32(comp);
+          const unsigned cmin = gminu<GL>(comp);
           if (cmin == 0xffffffffu) break;
           kmin = (int)(cmin >> 10) - kHalf;
           mm = (int)(cmin & 1023u);
           if (kmin == -kHalf || kmin == kHalf - 1) {
-            kmin = warp_min_i32(bk);
-            mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+            kmin = gmin<GL>(bk);
+            mm = (int)gminu<GL>(bk == kmin ? (unsigned)bm : 0xffffffffu);
           }
         } else {
-          kmin = warp_min_i32(bk);
+          kmin = gmin<GL>(bk);
           if (kmin == INT32_MAX) break;
-          mm = (int)warp_min_u32(bk == kmin ? (unsigned)bm : 0xffffffffu);
+          mm = (int)gminu<GL>(bk == kmin ? (unsigned)bm : 0xffffffffu);
         }
-        const unsigned owner = __ballot_sync(kFull, bk == kmin && bm == mm);
-        const int dmm = __shfl_sync(kFull, bdE, __ffs(owner) - 1);
+        const bool mine = bk == kmin && bm == mm;
+        int dmm = kmin;  // the plain choice key is Delta E itself
+        if (BIASED) dmm = gshfl<GL>(bdE, __ffs(gballot<GL>(mine)) - 1);
         uint64_t cand = fp ^ (ONE ? ztab[mm - 1] : zobrist(zkey, mm));
         if (ly.skew && mm != ly.c) cand ^= ONE ? ztab[ly.L - mm] : zobrist(zkey, ly.L + 1 - mm);
-        if (!bloom_test(ws.bloom, cand, P.bloom_k, bmask)) {
+        if (!bloom_test<GL>(bloom, cand, P.bloom_k, bmask)) {
           mstar = mm;
           kstar = kmin;
           dstar = dmm;
@@ -509,21 +529,21 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
           break;
         }
         skips++;
-        if (bk == kmin && bm == mm) {
+        if (mine) {
           // the owner lane's next best: smallest key ranked after (kmin, mm); keys ranked ahead were
           // dropped earlier in this step
           bk = INT32_MAX;
           int nbm = INT32_MAX, nbd = 0;
           for (int t = 0; t < S; t++) {
-            const int key = sl_k[t * 32 + lane];
-            const int ms = slot_pos(sl_w[t * 32 + lane]);
+            const int key = sl_k[t * GL + lane];
+            const int ms = slot_pos(sl_w[t * GL + lane]);
             const int m = ms < 0 ? -ms : ms;
             if (key == INT32_MAX) continue;
             if (key < kmin || (key == kmin && m <= mm)) continue;
             if (key < bk || (key == bk && m < nbm)) {
               bk = key;
               nbm = m;
-              nbd = BIASED ? sl_d[t * 32 + lane] : key;
+              nbd = BIASED ? sl_d[t * GL + lane] : key;
             }
           }
           bm = nbm;
@@ -531,14 +551,13 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         }
       }
       // the move back ranked ahead of the chosen move: count it as a Bloom skip
-      if (__any_sync(kFull, kprev != INT32_MAX && (mstar < 0 || kprev < kstar || (kprev == kstar && mprev < mstar))))
+      if (gany<GL>(kprev != INT32_MAX && (mstar < 0 || kprev < kstar || (kprev == kstar && mprev < mstar))))
         skips++;
       if (mstar < 0) {
         dead++;
         need_start = true;
         continue;
       }
-      // ---- apply
       // ---- apply; the slot words take the move at the next scan (fold_flip)
       pend.on = true;
       pend.pair = ly.skew && mstar != ly.c;
@@ -549,13 +568,13 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       pend.s1 = pend.pair ? s_at(sm, ly, ly.L + 1 - mstar) : 0;
       pend.qmir = ly.c + 6 - (pend.cls ? 1 : 2);
       mprev = mstar;
-      SC += table_update(sm, ly, mstar, &fast);
+      SC += table_update<GL>(sm, ly, mstar, &fast);
       if (lane == 0) flip_position(sm, ly, mstar);
       if (lane == 1 && pend.pair) flip_position(sm, ly, ly.L + 1 - mstar);
-      __syncwarp();
+      gsync<GL>();
       E += dstar;
       fp = nfp;
-      bloom_add(ws.bloom, fp, P.bloom_k, bmask);
+      bloom_add<GL>(bloom, fp, P.bloom_k, bmask);
       flips++;
       taken++;
       if (taken == 1 && P.move_log && lane == 0) {
@@ -566,7 +585,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       if (first_hit < 0 && E <= P.E_target) first_hit = (int)flips;
       // ---- sieve
       if (E <= E_thr && key_less(E, fp, wE, wfp)) {
-        bool dup = __any_sync(kFull, lane < R && cE != INT32_MAX && cfp == fp);
+        bool dup = gany<GL>(lane < R && cE != INT32_MAX && cfp == fp);
         if (!dup) {
           if (lane == wlane) {
             cE = E;
@@ -596,10 +615,10 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       // ---- leave the walk for the next launch
       if (gh) {
         unsigned char* gb = reinterpret_cast<unsigned char*>(gh);
-        for (int t = lane; t < kBitWords; t += 32) reinterpret_cast<uint32_t*>(gb + kStateBits)[t] = sm.bits[t];
-        for (int t = lane; t < kCLen / 2; t += 32)
+        for (int t = lane; t < kBitWords; t += GL) reinterpret_cast<uint32_t*>(gb + kStateBits)[t] = sm.bits[t];
+        for (int t = lane; t < ly.cl / 2; t += GL)
           reinterpret_cast<uint32_t*>(gb + kStateC)[t] = reinterpret_cast<const uint32_t*>(sm.C16)[t];
-        for (int t = lane; t < bwords; t += 32) reinterpret_cast<uint32_t*>(gb + kStateBloom)[t] = ws.bloom[t];
+        for (int t = lane; t < bwords; t += GL) reinterpret_cast<uint32_t*>(gb + kStateBloom)[t] = bloom[t];
         if (lane == 0) {
           gh->fp = fp;
           gh->skips = skips;
@@ -620,16 +639,16 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
       // ---- final: sort the R slots by (E, fp) (ties between empty slots by lane) and rewrite in place
       int rank = 0;
       for (int r = 0; r < R; r++) {
-        int oE = __shfl_sync(kFull, cE, r);
-        uint64_t of = __shfl_sync(kFull, cfp, r);
+        int oE = gshfl<GL>(cE, r);
+        uint64_t of = gshfl<GL>(cfp, r);
         if (key_less(oE, of, cE, cfp) || (oE == cE && of == cfp && r < lane)) rank++;
       }
-      __syncwarp();
+      gsync<GL>();
       labs_candidate mine;
       if (lane < R) mine = rec[lane];
-      __syncwarp();
+      gsync<GL>();
       if (lane < R) rec[rank] = mine;
-      __syncwarp();
+      gsync<GL>();
       if (P.walk_stats && lane == 0) {
         int64_t* st = P.walk_stats + (int64_t)item * 6;
         st[0] = (int64_t)flips;
@@ -644,7 +663,7 @@ __global__ void __launch_bounds__(256, 2) walk_kernel(const __grid_constant__ Wa
         gh->started = 1;
       }
     }
-    __syncwarp();
+    gsync<GL>();
     agg_flips += flips - flips0;
     agg_segs += segs - segs0;
     agg_skips += skips - skips0;
@@ -757,33 +776,43 @@ __global__ void finish_select_kernel(const unsigned* __restrict__ hist2, long lo
 }
 
 struct Variant {
-  int M, H;
+  int M, H, GL;  // tile, lag ranges per tile, lanes per walk
 };
-static const Variant kVariants[] = {{8, 1}, {12, 1}, {16, 1}, {16, 2}};
+static const Variant kVariants[] = {{8, 1, 32}, {12, 1, 32}, {16, 1, 32}, {16, 2, 32},
+                                    {8, 1, 16}, {12, 1, 16}, {16, 1, 16}, {16, 2, 16}};
 
 // Passes a length needs with variant v (0 if the layout does not fit).
 static int passes_for(int L, int skew, int p, const Variant& v) {
   Layout ly;
   if (!make_layout(ly, L, skew, p, v.M, v.H)) return 0;
-  int np = (ly.n_tasks + 31) / 32;
+  int np = (ly.n_tasks + v.GL - 1) / v.GL;
   return np < 1 ? 1 : np;
 }
 
-template <int M, int H>
+// Bytes of a launch's dynamic shared memory: the walks' slabs and, for single-length launches, the
+// Zobrist table.
+static size_t walk_smem(const WalkParams& P, int walks_per_block) {
+  return (size_t)P.slab.bytes * (size_t)walks_per_block + (P.n_len == 1 ? sizeof(uint64_t) * (size_t)P.len[0].ly.L : 0);
+}
+
+template <int M, int H, int GL>
 int walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st, bool configure, long long* blocks) {
   const bool one = P.n_len == 1, biased = P.bias != nullptr;
   if (biased && !one) return LABS_ERR_INVALID_ARG;
-  const size_t smem = (sizeof(WalkSmem) + (size_t)P.slot_stride * 32 * slot_bytes(biased)) * (size_t)warps +
-                      (one ? sizeof(uint64_t) * LABS_MAX_L : 0);
-  auto kern = !one ? walk_kernel<M, H, false, false> : biased ? walk_kernel<M, H, true, true> : walk_kernel<M, H, true, false>;
+  if (32 * warps > walk_block_threads(GL)) return LABS_ERR_INVALID_ARG;
+  const size_t smem = walk_smem(P, warps * (32 / GL));
+  auto kern = !one ? walk_kernel<M, H, false, false, GL>
+                   : biased ? walk_kernel<M, H, true, true, GL> : walk_kernel<M, H, true, false, GL>;
   if (configure) {
+    if (smem > ctx->smem_optin) return LABS_ERR_INVALID_ARG;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return LABS_ERR_CUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * warps, smem) != cudaSuccess || per_sm < 1)
       return LABS_ERR_CUDA;
     long long b = (long long)per_sm * ctx->num_sms;
-    const long long need = (P.n_items + warps - 1) / warps;
+    const long long walks_per_block = (long long)warps * (32 / GL);
+    const long long need = (P.n_items + walks_per_block - 1) / walks_per_block;
     if (b > need) b = need;
     *blocks = b < 1 ? 1 : b;
     return LABS_OK;
@@ -796,13 +825,27 @@ int walk_t(labs_ctx* ctx, const WalkParams& P, int warps, cudaStream_t st, bool 
 // configure = false: launches with that grid (no runtime call besides the launch itself).
 static int walk_variant(labs_ctx* ctx, const WalkParams& P, const Variant& v, int warps, cudaStream_t st,
                         bool configure, long long* blocks) {
-  switch (v.M * 10 + v.H) {
-    case 81: return walk_t<8, 1>(ctx, P, warps, st, configure, blocks);
-    case 121: return walk_t<12, 1>(ctx, P, warps, st, configure, blocks);
-    case 161: return walk_t<16, 1>(ctx, P, warps, st, configure, blocks);
-    case 162: return walk_t<16, 2>(ctx, P, warps, st, configure, blocks);
+  switch (v.M * 1000 + v.H * 100 + v.GL) {
+    case 8132: return walk_t<8, 1, 32>(ctx, P, warps, st, configure, blocks);
+    case 12132: return walk_t<12, 1, 32>(ctx, P, warps, st, configure, blocks);
+    case 16132: return walk_t<16, 1, 32>(ctx, P, warps, st, configure, blocks);
+    case 16232: return walk_t<16, 2, 32>(ctx, P, warps, st, configure, blocks);
+    case 8116: return walk_t<8, 1, 16>(ctx, P, warps, st, configure, blocks);
+    case 12116: return walk_t<12, 1, 16>(ctx, P, warps, st, configure, blocks);
+    case 16116: return walk_t<16, 1, 16>(ctx, P, warps, st, configure, blocks);
+    case 16216: return walk_t<16, 2, 16>(ctx, P, warps, st, configure, blocks);
     default: return LABS_ERR_INVALID_ARG;
   }
+}
+
+// Warps per block of a launch: the requested count, else 8 for whole-warp walks and, for half-warp
+// walks, as many (up to the block limit) as fit one block's slabs in the shared memory of an SM.
+static int warps_for(const labs_ctx* ctx, const WalkParams& P, const Variant& v, int requested) {
+  if (requested > 0) return requested;
+  if (v.GL == 32) return 8;
+  int w = walk_block_threads(16) / 32;
+  while (w > 1 && walk_smem(P, 2 * w) > ctx->smem_optin) w--;
+  return w;
 }
 
 static int launch_walk(labs_ctx* ctx, const WalkParams& P, const Variant& v, int warps, cudaStream_t st) {
@@ -817,37 +860,69 @@ struct LenSpec {
   int64_t walks, walk_begin;
 };
 
-// Fills the per-length table and slot stride for variant v; false if some length does not fit.
-static bool fill_params(WalkParams& P, const std::vector<LenSpec>& lens, const Variant& v) {
+// Fills the per-length table, the slot stride and the slab plan for variant v; false if some length does
+// not fit.  Every length's arrays are shrunk to what it needs (compact_layout) and the slab takes the
+// largest of each piece over the launch's lengths.
+static bool fill_params(WalkParams& P, const std::vector<LenSpec>& lens, const Variant& v, int R, bool biased,
+                        int bloom_log2) {
   P.n_len = (int)lens.size();
   int64_t item = 0;
-  int maxnp = 1;
+  int maxnp = 1, fwd_bytes = 16, cl = 8;
   for (size_t i = 0; i < lens.size(); i++) {
     LenEntry& e = P.len[i];
     if (!make_layout(e.ly, lens[i].L, lens[i].skew, lens[i].p, v.M, v.H)) return false;
-    int np = (e.ly.n_tasks + 31) / 32;
+    compact_layout(e.ly);
+    int np = (e.ly.n_tasks + v.GL - 1) / v.GL;
     if (np > kMaxPasses) return false;
     maxnp = std::max(maxnp, np);
+    fwd_bytes = std::max(fwd_bytes, 4 * e.ly.cw * e.ly.ncls);
+    cl = std::max(cl, e.ly.cl);
     e.T_i = lens[i].T_i > 0 ? lens[i].T_i : 4 * (lens[i].L + 1);
     e.E_thr_value = INT32_MAX;
     e.item_begin = item;
     e.walk_begin = lens[i].walk_begin;
     item += lens[i].walks;
   }
+  if (R > v.GL) return false;  // one sieve slot per lane
   P.n_items = item;
   P.slot_stride = maxnp * (v.M / v.H);
+  auto up16 = [](int b) { return (b + 15) & ~15; };
+  SlabPlan& sp = P.slab;
+  int off = up16(4 * kBitWords);
+  sp.off_C16 = off;
+  off += up16(2 * cl);
+  sp.off_C8 = off;
+  off += up16(cl);
+  sp.off_fwd = off;
+  off += up16(fwd_bytes);
+  sp.off_bwd = off;
+  off += up16(fwd_bytes);
+  sp.off_bloom = off;
+  off += up16(std::max(4, (1 << bloom_log2) / 8));
+  sp.off_slots = off;
+  off += up16(P.slot_stride * v.GL * slot_bytes(biased));
+  // slab stride = 8 (mod 128) bytes: the two walks of a half-warp launch then sit two banks apart, so
+  // their lanes' window loads (tiles four words apart, all multiples of four banks) do not collide
+  // (every slab access is at most 4 bytes wide, so 8-byte alignment of a slab suffices)
+  sp.bytes = off + (136 - off % 128) % 128;
   return true;
 }
 
-// Heuristic choice: least total per-lane scan work sum(walks * NP * M / H); ties to more lanes per tile,
-// then the larger tile.
-static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, Variant* out) {
+// Heuristic choice: least total per-warp scan work, sum(walks * NP * M / H * GL / 32) (a half-warp walk
+// shares its warp's instructions with another walk); ties to fewer lane passes (each pass repeats the
+// per-slot phases), then to more lanes per tile, then the larger tile.
+// req_m / req_gl: 0 or the tile size / lanes per walk the caller fixed; R: sieve slots per walk.
+static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, int req_gl, int R, Variant* out) {
   bool found = false;
   long double best_cost = 0;
-  Variant best{0, 0};
+  int best_np = 0;
+  Variant best{0, 0, 0};
   for (const Variant& v : kVariants) {
     if (req_m && v.M != req_m) continue;
+    if (req_gl && v.GL != req_gl) continue;
+    if (R > v.GL) continue;
     long double cost = 0;
+    int max_np = 0;
     bool ok = true;
     for (const LenSpec& s : lens) {
       int np = passes_for(s.L, s.skew, s.p, v);
@@ -855,12 +930,17 @@ static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, Variant*
         ok = false;
         break;
       }
-      cost += (long double)std::max<int64_t>(s.walks, 1) * np * v.M / v.H;
+      max_np = std::max(max_np, np);
+      cost += (long double)std::max<int64_t>(s.walks, 1) * np * v.M / v.H * v.GL / 32;
     }
     if (!ok) continue;
-    if (!found || cost < best_cost || (cost == best_cost && (v.H > best.H || (v.H == best.H && v.M > best.M)))) {
+    const bool better = !found || cost < best_cost ||
+                        (cost == best_cost && (max_np < best_np || (max_np == best_np && (v.H > best.H ||
+                                                                    (v.H == best.H && v.M > best.M)))));
+    if (better) {
       best = v;
       best_cost = cost;
+      best_np = max_np;
       found = true;
     }
   }
@@ -915,7 +995,7 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
                        labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, cudaStream_t st) {
   std::vector<LenSpec> lens{{cfg->L, cfg->skew, cfg->p, cfg->T_i, cfg->n_walks, cfg->walk_begin}};
   Variant v;
-  if (!choose_variant(lens, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
+  if (!choose_variant(lens, cfg->tile_m, cfg->lanes_per_walk, cfg->R, &v)) return LABS_ERR_INVALID_ARG;
   WalkParams* P = new (std::nothrow) WalkParams();
   if (!P) return LABS_ERR_NOMEM;
   char* w = static_cast<char*>(ws_get(ctx, kWsWalkCounters, 256));
@@ -925,7 +1005,10 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
   }
   base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, cfg->flip_budget, cfg->seed,
               cfg->E_target, prefixes, out, walk_stats, stats, reinterpret_cast<unsigned long long*>(w));
-  fill_params(*P, lens, v);
+  if (!fill_params(*P, lens, v, cfg->R, false, cfg->bloom_log2)) {
+    delete P;
+    return LABS_ERR_INVALID_ARG;
+  }
   int32_t* thr = reinterpret_cast<int32_t*>(w + 64);
   int s = LABS_OK;
   if (cfg->E_thr_dev) {
@@ -941,7 +1024,7 @@ int launch_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* 
     walk_init_kernel<<<1, 1, 0, st>>>(stats, P->E_thr_dev, P->len[0].E_thr_value, P->counter);
     s = cuda_status(cudaGetLastError());
   }
-  if (s == LABS_OK && P->n_items > 0) s = launch_walk(ctx, *P, v, cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8, st);
+  if (s == LABS_OK && P->n_items > 0) s = launch_walk(ctx, *P, v, warps_for(ctx, *P, v, cfg->warps_per_cta), st);
   delete P;
   return s;
 }
@@ -957,7 +1040,7 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
                           cudaStream_t st) {
   std::vector<LenSpec> lens{{cfg->L, cfg->skew, cfg->p, cfg->T_i, cfg->n_walks, cfg->walk_begin}};
   Variant v;
-  if (!choose_variant(lens, cfg->tile_m, &v)) return LABS_ERR_INVALID_ARG;
+  if (!choose_variant(lens, cfg->tile_m, cfg->lanes_per_walk, cfg->R, &v)) return LABS_ERR_INVALID_ARG;
   const long long n = cfg->n_walks;
   const int L = cfg->L, W = (L + 63) / 64;
   const long long n_chunks = (cfg->flip_budget + chunk - 1) / chunk;
@@ -972,7 +1055,10 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(w);
   base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, cfg->flip_budget, cfg->seed, cfg->E_target,
               prefixes, out, walk_stats, stats, counter);
-  fill_params(*P, lens, v);
+  if (!fill_params(*P, lens, v, cfg->R, policy != nullptr, cfg->bloom_log2)) {  // one slab plan for the plain and biased launches
+    delete P;
+    return LABS_ERR_INVALID_ARG;
+  }
   int32_t* thr = reinterpret_cast<int32_t*>(w + 64);
   int s = LABS_OK;
   if (cfg->E_thr_dev) {
@@ -984,7 +1070,7 @@ int launch_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* 
   } else {
     P->len[0].E_thr_value = cfg->E_thr;
   }
-  const int warps = cfg->warps_per_cta > 0 ? cfg->warps_per_cta : 8;
+  const int warps = warps_for(ctx, *P, v, cfg->warps_per_cta);
   long long blocks = 0, blocks_biased = 0;
   if (s == LABS_OK) s = walk_variant(ctx, *P, v, warps, st, true, &blocks);
   if (s == LABS_OK && policy) {  // the chunks run the biased instantiation: configure it as well
@@ -1055,7 +1141,7 @@ int issue_batch(labs_ctx* ctx, const labs_batch_cfg* cfg, const std::vector<LenS
   if (!P) return LABS_ERR_NOMEM;
   base_params(*P, cfg->R, cfg->bloom_log2, cfg->bloom_k, cfg->p, n_prefix, flip_budget, cfg->seed, cfg->E_target,
               prefixes, out, walk_stats, stats, counter);
-  if (!fill_params(*P, lens, v)) {
+  if (!fill_params(*P, lens, v, cfg->R, false, cfg->bloom_log2)) {
     delete P;
     return LABS_ERR_INVALID_ARG;
   }
@@ -1103,34 +1189,44 @@ int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_
   unsigned long long* counter = reinterpret_cast<unsigned long long*>(w);
 
   // ---- variant and walks per CTA: given, or timed
-  Variant v{0, 0};
+  Variant v{0, 0, 0};
   int warps = cfg->warps_per_cta;
   uint64_t tkey = (uint64_t)ctx->num_sms;
   for (const LenSpec& s : lens) tkey = mix_key(tkey, ((uint64_t)s.L << 40) ^ (uint64_t)s.walks);
-  tkey = mix_key(tkey, ((uint64_t)cfg->tile_m << 8) ^ (uint64_t)warps);
+  tkey = mix_key(tkey, ((uint64_t)cfg->tile_m << 8) ^ (uint64_t)warps ^ ((uint64_t)cfg->R << 16) ^
+                           ((uint64_t)cfg->bloom_log2 << 24));
   bool cached = false;
   for (int i = 0; i < ctx->n_tuned; i++)
     if (ctx->tuned_key[i] == tkey) {
-      v = {ctx->tuned[i][0], ctx->tuned[i][1]};
-      warps = ctx->tuned[i][2];
+      v = {ctx->tuned[i][0], ctx->tuned[i][1], ctx->tuned[i][2]};
+      warps = ctx->tuned[i][3];
       cached = true;
     }
+  // the (variant, warps per CTA) candidates: whole-warp walks try 4 and 8 warps, half-warp walks the
+  // largest block whose slabs fit an SM
+  WalkParams* Q = new (std::nothrow) WalkParams();
+  if (!Q) return LABS_ERR_NOMEM;
   if (!cached) {
-    std::vector<Variant> vs;
+    std::vector<std::pair<Variant, int>> cands;
     for (const Variant& c : kVariants) {
       if (cfg->tile_m && c.M != cfg->tile_m) continue;
-      bool ok = true;
-      for (const LenSpec& s : lens) {
-        int np = passes_for(s.L, s.skew, s.p, c);
-        ok &= np >= 1 && np <= kMaxPasses;
+      if (!fill_params(*Q, lens, c, cfg->R, false, cfg->bloom_log2)) continue;
+      if (warps > 0) {
+        if (32 * warps <= walk_block_threads(c.GL)) cands.push_back({c, warps});
+      } else if (c.GL == 32) {
+        cands.push_back({c, 4});
+        cands.push_back({c, 8});
+      } else {
+        cands.push_back({c, warps_for(ctx, *Q, c, 0)});
       }
-      if (ok) vs.push_back(c);
     }
-    if (vs.empty()) return LABS_ERR_INVALID_ARG;
-    std::vector<int> wps = warps > 0 ? std::vector<int>{warps} : std::vector<int>{4, 8};
-    if (vs.size() * wps.size() == 1) {
-      v = vs[0];
-      warps = wps[0];
+    if (cands.empty()) {
+      delete Q;
+      return LABS_ERR_INVALID_ARG;
+    }
+    if (cands.size() == 1) {
+      v = cands[0].first;
+      warps = cands[0].second;
     } else {
       // trial: every length with 1/16 of its walks (at least one), 512 flips each, thresholds off
       std::vector<LenSpec> trial = lens;
@@ -1139,41 +1235,43 @@ int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       float best_ms = 0;
-      for (const Variant& c : vs)
-        for (int wp : wps) {
-          cudaEventRecord(e0, st);
-          int s = issue_batch(ctx, cfg, trial, c, wp, prefixes, n_prefix, out, nullptr, thr, stats, counter,
-                              std::min<int64_t>(cfg->flip_budget, 512), false, 0, st);
-          cudaEventRecord(e1, st);
-          if (s != LABS_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
-          float ms = 0;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (v.M == 0 || ms < best_ms) {
-            best_ms = ms;
-            v = c;
-            warps = wp;
-          }
+      for (const auto& cw : cands) {
+        cudaEventRecord(e0, st);
+        int s = issue_batch(ctx, cfg, trial, cw.first, cw.second, prefixes, n_prefix, out, nullptr, thr, stats,
+                            counter, std::min<int64_t>(cfg->flip_budget, 512), false, 0, st);
+        cudaEventRecord(e1, st);
+        if (s != LABS_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (v.M == 0 || ms < best_ms) {
+          best_ms = ms;
+          v = cw.first;
+          warps = cw.second;
         }
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      if (v.M == 0) return LABS_ERR_CUDA;
+      if (v.M == 0) {
+        delete Q;
+        return LABS_ERR_CUDA;
+      }
     }
     if (ctx->n_tuned < kMaxTuned) {
       ctx->tuned_key[ctx->n_tuned] = tkey;
       ctx->tuned[ctx->n_tuned][0] = v.M;
       ctx->tuned[ctx->n_tuned][1] = v.H;
-      ctx->tuned[ctx->n_tuned][2] = warps;
+      ctx->tuned[ctx->n_tuned][2] = v.GL;
+      ctx->tuned[ctx->n_tuned][3] = warps;
       ctx->n_tuned++;
     }
   }
   // kernel attributes and grid size before any capture
   long long blocks = 0;
   {
-    WalkParams* P = new (std::nothrow) WalkParams();
-    if (!P) return LABS_ERR_NOMEM;
-    fill_params(*P, lens, v);
-    int s = walk_variant(ctx, *P, v, warps, st, true, &blocks);
-    delete P;
+    int s = fill_params(*Q, lens, v, cfg->R, false, cfg->bloom_log2) ? LABS_OK : LABS_ERR_INVALID_ARG;
+    Q->bloom_log2 = cfg->bloom_log2;
+    if (s == LABS_OK) s = walk_variant(ctx, *Q, v, warps, st, true, &blocks);
+    delete Q;
     if (s != LABS_OK) return s;
   }
   if (!cfg->use_graph)
@@ -1182,7 +1280,7 @@ int launch_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_
 
   // ---- CUDA graph: capture once per (configuration, buffers), replay afterwards
   uint64_t gkey = tkey;
-  gkey = mix_key(gkey, ((uint64_t)v.M << 32) ^ ((uint64_t)v.H << 16) ^ (uint64_t)warps);
+  gkey = mix_key(gkey, ((uint64_t)v.M << 32) ^ ((uint64_t)v.H << 16) ^ ((uint64_t)v.GL << 8) ^ (uint64_t)warps);
   gkey = mix_key(gkey, (uint64_t)cfg->flip_budget ^ ((uint64_t)cfg->R << 48));
   gkey = mix_key(gkey, cfg->seed);
   gkey = mix_key(gkey, ((uint64_t)cfg->p << 32) ^ ((uint64_t)cfg->bloom_log2 << 16) ^ (uint64_t)cfg->bloom_k);

@@ -140,10 +140,10 @@ def test_exhaustive(lg, L, p, prefix):
 # labs_skew_search (Algorithm 1)
 # ------------------------------------------------------------------------------------------------
 def run_walks(lg, L, skew, p, prefixes, n_walks, budget, T_i, seed, R=16, bloom_log2=15, bloom_k=4,
-              E_thr=2**31 - 1, walk_begin=0, tile_m=0, warps=0):
+              E_thr=2**31 - 1, walk_begin=0, tile_m=0, warps=0, lanes=0):
     cfg = lg.make_walk_cfg(L, skew=skew, p=p, n_walks=n_walks, flip_budget=budget, T_i=T_i, seed=seed, R=R,
                            bloom_log2=bloom_log2, bloom_k=bloom_k, E_thr=E_thr, walk_begin=walk_begin, tile_m=tile_m,
-                           warps_per_cta=warps)
+                           warps_per_cta=warps, lanes_per_walk=lanes)
     out, ws, st = lg.labs_skew_search(cfg, prefixes)
     torch.cuda.synchronize()
     return lg.candidates_numpy(out, n_walks, R), ws.cpu().numpy(), lg.stats_numpy(st)
@@ -158,46 +158,55 @@ def compare_walks(cand, ws, L, skew, p, prefixes, n_walks, budget, T_i, seed, R,
     assert np.array_equal(ws[:, :5], ost)
 
 
+@pytest.mark.parametrize("lanes", [16, 32])
 @pytest.mark.parametrize("tile_m", [0, 8, 12, 16])
-def test_walks_l451_skew(lg, tile_m):
+def test_walks_l451_skew(lg, tile_m, lanes):
+    """Every tile variant, with one walk per warp and with two walks per warp (16 lanes each, the slabs
+    sized for the length)."""
     L, p = 451, 24
     pre = inp.distinct_prefixes(256, p, seed=2409)
     n, budget, T_i = 40, 700, 300
-    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16, tile_m=tile_m)
+    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16, tile_m=tile_m, lanes=lanes)
     compare_walks(cand, ws, L, True, p, pre, n, budget, T_i, 2409, 16)
     assert st["flips"] == n * budget and st["best_E"] == ws[:, 4].min()
 
 
-@pytest.mark.parametrize("L,skew,p", [(450, 0, 0), (527, 1, 24), (526, 0, 0), (487, 1, 24), (101, 1, 5), (64, 0, 0)])
-def test_walks_other_lengths(lg, L, skew, p):
+@pytest.mark.parametrize("lanes", [16, 32])
+@pytest.mark.parametrize("L,skew,p", [(450, 0, 0), (527, 1, 24), (526, 0, 0), (487, 1, 24), (101, 1, 5), (64, 0, 0),
+                                      (576, 0, 0), (575, 1, 0)])
+def test_walks_other_lengths(lg, L, skew, p, lanes):
     pre = inp.distinct_prefixes(8, p, seed=1) if p else np.zeros(1, dtype=np.uint64)
     n, budget, T_i = 12, 400, 150
-    cand, ws, st = run_walks(lg, L, skew, p, pre, n, budget, T_i, seed=77, R=8)
+    cand, ws, st = run_walks(lg, L, skew, p, pre, n, budget, T_i, seed=77, R=8, lanes=lanes)
     compare_walks(cand, ws, L, skew, p, pre, n, budget, T_i, 77, 8)
 
 
-def test_walks_sieve_threshold_and_small_bloom(lg):
-    """Tight sieve bound, a 32-bit Bloom filter (false positives, dead ends) and tiny lengths."""
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_walks_sieve_threshold_and_small_bloom(lg, lanes):
+    """Tight sieve bound, a 32-bit Bloom filter (false positives, dead ends: the two walks of a warp then
+    fall out of step) and tiny lengths."""
     for L, skew, p, bl, thr in [(13, 1, 0, 5, 30), (15, 1, 2, 5, 10**6), (21, 0, 0, 6, 40), (33, 1, 3, 7, 200)]:
         pre = inp.distinct_prefixes(4, p, seed=3) if p else np.zeros(1, dtype=np.uint64)
         n, budget, T_i = 64, 300, 25
         cand, ws, st = run_walks(lg, L, skew, p, pre, n, budget, T_i, seed=5, R=5, bloom_log2=bl, bloom_k=3,
-                                 E_thr=thr)
+                                 E_thr=thr, lanes=lanes)
         compare_walks(cand, ws, L, skew, p, pre, n, budget, T_i, 5, 5, bloom_log2=bl, bloom_k=3, E_thr=thr)
 
 
-def test_walks_wide_path_prefix_of_ones(lg):
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_walks_wide_path_prefix_of_ones(lg, lanes):
     """A long all-+1 prefix keeps |C_k| > 127 at the start of each segment (exact int16 path)."""
     L, p = 301, 140
     pre = np.array([(1 << 64) - 1, (1 << 64) - 1, (1 << 12) - 1], dtype=np.uint64)
-    cand, ws, st = run_walks(lg, L, True, p, pre, 6, 200, 100, seed=9, R=4)
+    cand, ws, st = run_walks(lg, L, True, p, pre, 6, 200, 100, seed=9, R=4, lanes=lanes)
     compare_walks(cand, ws, L, True, p, pre, 6, 200, 100, 9, 4)
 
 
-def test_walks_shard_offset_and_ragged_counts(lg):
+@pytest.mark.parametrize("lanes", [16, 32])
+def test_walks_shard_offset_and_ragged_counts(lg, lanes):
     L, p = 451, 24
     pre = inp.distinct_prefixes(256, p, seed=2409)
-    cand, ws, _ = run_walks(lg, L, True, p, pre, 37, 150, 64, seed=3, R=16, walk_begin=1000, warps=3)
+    cand, ws, _ = run_walks(lg, L, True, p, pre, 37, 150, 64, seed=3, R=16, walk_begin=1000, warps=3, lanes=lanes)
     compare_walks(cand, ws, L, True, p, pre, 37, 150, 64, 3, 16, walk_begin=1000)
 
 
@@ -208,7 +217,7 @@ def test_walks_l451_full_segments_through_restarts(lg):
     L, p = 451, 24
     pre = inp.distinct_prefixes(256, p, seed=2409)
     n, budget, T_i = 8, 4000, 1808
-    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16)
+    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16, lanes=16)
     compare_walks(cand, ws, L, True, p, pre, n, budget, T_i, 2409, 16)
     assert np.all(ws[:, 1] == 3)  # segments: two restarts per walk
     assert st["flips"] == n * budget
@@ -497,3 +506,13 @@ def test_pq_independent_visited_set_capacity_error(lg):
         assert bE[q] == oE and np.array_equal(best[q], ob) and int(stn[q]["best_fp"]) == ofp, q
         for k in ("expansions", "survivors", "h_size", "improvements"):
             assert int(stn[q][k]) == ost[k], (q, k, int(stn[q][k]), ost[k])
+
+
+def test_walks_r_above_half_warp_uses_whole_warps(lg):
+    """R = 32 sieve slots need one lane each: the library runs whole-warp walks, and 16 lanes are refused."""
+    L, p = 101, 5
+    pre = inp.distinct_prefixes(8, p, seed=1)
+    cand, ws, st = run_walks(lg, L, True, p, pre, 10, 300, 80, seed=4, R=32)
+    compare_walks(cand, ws, L, True, p, pre, 10, 300, 80, 4, 32)
+    with pytest.raises(lg.LabsError):
+        run_walks(lg, L, True, p, pre, 10, 300, 80, seed=4, R=32, lanes=16)

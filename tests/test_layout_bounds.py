@@ -44,7 +44,19 @@ def layout(L, skew, p, M, H=1):
     ok = (qmax_end + 4 * NGend + 8 < cap and Qr + 4 * NGend + 8 < cap and 2 * qmax_end < cap
           and 4 * NGend <= kCLen)
     return dict(lam=lam, G=G, NG=NG, c=c, mlast=mlast, tiles=tiles, Qr=Qr, cap=cap, ok=ok, NGh=NGh, NGend=NGend, R=R,
-                ntiles=ntiles)
+                ntiles=ntiles, cl=kCLen, qmax_end=qmax_end, L=L, skew=skew)
+
+
+def compact(ly):
+    """Mirror of compact_layout: the class arrays and the table shrunk to what the length needs."""
+    n_cls = (ly["L"] + 1) // 2 if ly["skew"] else ly["L"]
+    need = max(ly["qmax_end"] + 4 * ly["NGend"] + 8, ly["Qr"] + 4 * ly["NGend"] + 8, 2 * ly["qmax_end"] + 1,
+               kQOff + n_cls + 1)
+    out = dict(ly)
+    out["cap"] = -(-need // 16) * 16
+    out["cl"] = -(-max(4 * ly["NGend"], ly["G"] + 1) // 8) * 8
+    assert out["cap"] <= ly["cap"] and out["cl"] <= kCLen  # never larger than the fixed slab
+    return out
 
 
 
@@ -65,10 +77,12 @@ def _cases():
                 yield L, skew, p
 
 
-def _check(L, skew, p, M, H):
+def _check(L, skew, p, M, H, small=False):
     ly = layout(L, skew, p, M, H)
     if not ly["ok"]:
         return 0
+    if small:
+        ly = compact(ly)
     words = ly["cap"] // 4
     K = M // 4 + 1
     covered = set()
@@ -102,16 +116,22 @@ def _check(L, skew, p, M, H):
         for f in range(p + 1, c):  # the mirror L + 1 - f of a pair flip: class index c + 6 - b - q_f
             b = 1 if f & 1 else 2
             assert pos_q(skew, L + 1 - f) == c + 6 - b - pos_q(skew, f)
-            # the pair term reads C16[c - m - 1]
-            if skew and p + 1 <= m < c:
-                assert 0 <= c - m - 1 < kCLen
+            # the pair term reads C16[c - f - 1]; a slot without one reads C16[cl - 1], which lies beyond
+            # G (always zero)
+            assert 0 <= c - f - 1 < ly["cl"]
+        assert ly["cl"] - 1 >= ly["G"]
+    # the table arrays: entries 0..4 NG - 1 are rewritten by the update, 4 NGend are read by the scan
+    assert 4 * ly["NGend"] <= ly["cl"] and 4 * ly["NG"] <= ly["cl"]
     assert covered == set(range(p + 1, ly["mlast"] + 1)), (L, skew, p, M)
     return 1
 
 
+@pytest.mark.parametrize("small", [False, True])
 @pytest.mark.parametrize("M,H", VARIANTS)
-def test_layout_indices_stay_inside_their_arrays(M, H):
-    tested = sum(_check(L, skew, p, M, H) for L, skew, p in _cases())
+def test_layout_indices_stay_inside_their_arrays(M, H, small):
+    """Fixed slabs (every length up to 576) and slabs shrunk to the length (the walk kernels' dynamic
+    shared memory): every index inside its array."""
+    tested = sum(_check(L, skew, p, M, H, small) for L, skew, p in _cases())
     assert tested > 1000
 
 
@@ -122,9 +142,9 @@ def test_every_length_fits_some_variant():
 
 
 def test_fold_entry_split_without_divide():
-    """The P fold gives lane n (0..31) its first (slot k, task tl) of a class as k = (n * magic) >> 16,
-    tl = n - k * tasks, and steps by the same split of 32, with magic = ceil(2^16 / tasks): that must be
-    n // tasks for every class of every accepted layout."""
+    """The P fold gives group lane n (0..GL-1, GL = 16 or 32) its first (slot k, task tl) of a class as
+    k = (n * magic) >> 16, tl = n - k * tasks, and steps by the same split of GL, with magic =
+    ceil(2^16 / tasks): that must be n // tasks for every n <= 32, every class of every accepted layout."""
     seen = 0
     for M, H in VARIANTS:
         for L, skew, p in _cases():
@@ -182,7 +202,7 @@ def test_byte_windows_four_positions_per_word():
             bits = rng.getrandbits(L)
             lam = 2 if skew else 1
             byte = lambda i: (2 if (bits >> (i - 1)) & 1 else 0) if 1 <= i <= L else 1
-            words = (kClassBytes if skew else kDirBytes) // 4
+            words = compact(ly)["cap"] // 4
             for cls in range(2 if skew else 1):
                 first = q_pos(skew, cls, kQOff)
                 for w in range(words):
@@ -191,4 +211,4 @@ def test_byte_windows_four_positions_per_word():
                     r = _window_bytes(bits, L, first + lam * (ly["Qr"] - 4 * w - 3 - kQOff), lam, True)
                     assert r == sum(byte(q_pos(skew, cls, ly["Qr"] - 4 * w - e)) << (8 * e) for e in range(4)), (L, skew, cls, w)
                     checked += 1
-    assert checked > 10000
+    assert checked > 5000
