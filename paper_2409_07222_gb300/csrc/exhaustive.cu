@@ -1,6 +1,7 @@
 // exhaustive.cu -- labs_skew_exhaustive: every skew-symmetric sequence (Eq. 2) of odd length L <= 127
 // behind a fixed prefix (Eq. 3).  One thread per assignment of the k-p+1 free elements; the sequence
-// fits two 64-bit words, so the table is computed directly with 64-bit popcounts.  Two passes over the
+// fits two 64-bit words (one for L <= 64, a path of its own), so the table is computed directly with
+// 64-bit popcounts.  Two passes over the
 // assignment space (minimum, then count + smallest argmin) keep the result exact and independent of
 // the order in which threads finish; the outputs themselves hold the running reductions.
 #include "labs_core.cuh"
@@ -35,6 +36,24 @@ __device__ __forceinline__ Seq128 assignment_seq(int L, int p, uint64_t prefix, 
   return x;
 }
 
+// Energy of a skew-symmetric sequence of L <= 64 positions (one word): one 64-bit popcount per even lag.
+__device__ __forceinline__ int energy64(uint64_t x, int L) {
+  int E = 0;
+  for (int k = 2; k < L; k += 2) {  // odd lags vanish for skew-symmetric sequences (Eq. 2)
+    const int n = L - k;
+    const int dis = __popcll((x ^ (x >> k)) & (n >= 64 ? ~0ull : ((1ull << n) - 1ull)));
+    const int cval = n - 2 * dis;
+    E += cval * cval;
+  }
+  return E;
+}
+
+// NW = 1: the sequence fits one word (L <= 64) and the high word is never touched.
+template <int NW>
+__device__ __forceinline__ int energy_nw(const Seq128& x, int L);
+template <>
+__device__ __forceinline__ int energy_nw<1>(const Seq128& x, int L) { return energy64(x.lo, L); }
+
 __device__ __forceinline__ int energy128(const Seq128& x, int L) {
   int E = 0;
   for (int k = 2; k < L; k += 2) {  // odd lags vanish for skew-symmetric sequences (Eq. 2)
@@ -50,6 +69,8 @@ __device__ __forceinline__ int energy128(const Seq128& x, int L) {
   }
   return E;
 }
+template <>
+__device__ __forceinline__ int energy_nw<2>(const Seq128& x, int L) { return energy128(x, L); }
 
 __global__ void exh_init_kernel(int32_t* minE, uint64_t* count, uint64_t* argmin) {
   *minE = INT32_MAX;
@@ -57,20 +78,22 @@ __global__ void exh_init_kernel(int32_t* minE, uint64_t* count, uint64_t* argmin
   *argmin = ~0ull;
 }
 
+template <int NW>
 __global__ void exh_min_kernel(int L, int p, uint64_t prefix, uint64_t total, int32_t* minE) {
   int best = INT32_MAX;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += (uint64_t)gridDim.x * blockDim.x)
-    best = min(best, energy128(assignment_seq(L, p, prefix, a), L));
+    best = min(best, energy_nw<NW>(assignment_seq(L, p, prefix, a), L));
   best = warp_min_i32(best);
   if (lane_id() == 0) atomicMin(minE, best);
 }
 
+template <int NW>
 __global__ void exh_count_kernel(int L, int p, uint64_t prefix, uint64_t total, const int32_t* minE, uint64_t* count,
                                  uint64_t* argmin) {
   const int target = *minE;
   unsigned long long cnt = 0, arg = ~0ull;
   for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < total; a += (uint64_t)gridDim.x * blockDim.x)
-    if (energy128(assignment_seq(L, p, prefix, a), L) == target) {
+    if (energy_nw<NW>(assignment_seq(L, p, prefix, a), L) == target) {
       cnt++;
       arg = min(arg, (unsigned long long)a);
     }
@@ -102,8 +125,13 @@ int launch_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t
   uint64_t cap = (uint64_t)ctx->num_sms * 16;
   if (blocks > cap) blocks = cap;
   exh_init_kernel<<<1, 1, 0, st>>>(out_min_E, out_count, out_argmin_free);
-  exh_min_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E);
-  exh_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E, out_count, out_argmin_free);
+  if (L <= 64) {  // one word: no popcount of an empty high word
+    exh_min_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E);
+    exh_count_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E, out_count, out_argmin_free);
+  } else {
+    exh_min_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E);
+    exh_count_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(L, p, prefix, total, out_min_E, out_count, out_argmin_free);
+  }
   exh_seq_kernel<<<1, 1, 0, st>>>(L, p, prefix, out_argmin_free, out_argmin_seq);
   return cuda_status(cudaGetLastError());
 }

@@ -23,7 +23,9 @@ __device__ __forceinline__ void probe_op(uint32_t (&r)[kChains], uint32_t a, uin
 #pragma unroll
   for (int j = 0; j < kChains; j++) {
     uint32_t x = r[j];
-    if (OP == 0) asm volatile("add.s32 %0, %0, %1;" : "+r"(x) : "r"(a));
+    // the add's second operand is the next chain's current value, which that chain's own add also
+    // reads: no intermediate sum is single-use, so no two adds can be merged into one three-input add
+    if (OP == 0) asm volatile("add.s32 %0, %0, %1;" : "+r"(x) : "r"(r[(j + 1) % kChains]));
     if (OP == 1) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x) : "r"(a), "r"(b));
     if (OP == 2) asm volatile("shf.r.wrap.b32 %0, %0, %1, %2;" : "+r"(x) : "r"(a), "r"(b));
     if (OP == 3) asm volatile("mad.lo.s32 %0, %0, %1, %2;" : "+r"(x) : "r"(a), "r"(b));

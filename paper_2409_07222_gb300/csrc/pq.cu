@@ -50,6 +50,7 @@ struct PqState {
   long long pop_cnt;    // entries gathered for popping this round
   long long cand_cnt;   // boundary-bin candidates gathered
   long long nU;         // unique survivors of the round
+  long long n_dense;    // dense survivor entries of the round: b x width, or the seeds
   long long sel_lt;     // entries below the boundary bin
   long long sel_need;   // entries taken from the boundary bin; 0: none; -1: no cut (everything kept)
   long long ev_round;   // evicted this round
@@ -61,6 +62,9 @@ struct PqState {
   unsigned long long sel_fp;  // boundary key: a boundary-bin entry is taken iff (E, fp) <= (sel_E, sel_fp)
   unsigned long long minfp_round;
   unsigned best_rep_round, pad1;
+  int pmax_bin;        // highest occupied bin of the pool after the pops (-1: empty pool)
+  int hist_mode;       // survivor histogram: 0 none (everything fits), 1 bins <= pmax_bin only, 2 all
+  long long nU_low;    // survivors in bins <= pmax_bin
 };
 
 struct PqBufs {
@@ -78,19 +82,22 @@ struct PqBufs {
   unsigned* hP2;
   unsigned* hU;       // histogram of the round's unique survivors
   unsigned* hU2;
-  int32_t* popId;     // pool ids gathered for popping [B]
+  int32_t* popId;     // pool ids gathered for popping [B], with their keys
+  int32_t* popE;
+  uint64_t* popF;
   int32_t* pivE;      // pivots in key order [B]
   uint64_t* pivFp;
   uint64_t* pivSeq;   // [B][W]
   int32_t* candId;    // boundary candidates: pool id >= 0, or -(u + 1) for survivor u
+  int32_t* cE;        // their keys, gathered contiguously
+  uint64_t* cF;
+  int32_t* popRank;   // rank of each popped entry among the pops (its pivot index)
   int32_t* dE;        // dense survivors [pivot][column]: energy, or INT32_MAX (visited)
   uint64_t* dFp;
   uint64_t* hkey;     // dedup hash table: mixed (E, fp) key, 0 = empty
   int32_t* hval;      // the unique survivor of a slot
-  int32_t* uE;        // unique survivors
-  uint64_t* uFp;
-  unsigned* uRep;     // representative (pivot << kColBits | column): the smallest of equal keys
-  int32_t* uSlot;     // dedup slot of the survivor
+  unsigned* uRep;     // per dense entry: ~0 unless it is the unique survivor of its key, whose
+                      // representative (pivot << kColBits | column) is the smallest of the equal keys
   uint64_t* H;        // visited set (open addressing)
   uint64_t* ztab;
   PqState* st;
@@ -197,21 +204,50 @@ __device__ __forceinline__ long long warp_append(long long* ctr, bool pred) {
 // Adds the insertions of a warp to h_size (every lane calls it).
 __device__ __forceinline__ void h_count(const PqBufs& b, int inserted) { warp_add(&b.st->h_size, inserted); }
 
+// Block-wide sum added to *ctr with one atomic per block (every thread of the block calls it).
+__device__ __forceinline__ void block_add(long long* ctr, long long v) {
+  __shared__ long long part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if (lane_id() == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+    if (t) atomicAdd(reinterpret_cast<unsigned long long*>(ctr), (unsigned long long)t);
+  }
+  __syncthreads();
+}
+
+// Block-wide minimum folded into *dst with one atomic per block (every thread calls it).
+__device__ __forceinline__ void block_min(int* dst, int v) {
+  __shared__ int part[32];
+  v = __reduce_min_sync(kFull, v);
+  if (lane_id() == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = INT32_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = min(t, part[w]);
+    if (t != INT32_MAX) atomicMin(dst, t);
+  }
+  __syncthreads();
+}
+
+// Adds delta to the fine and coarse histogram bins of every lane with bin >= 0, one atomic per distinct
+// bin of the warp (every lane calls it): the energies of a round crowd into few bins, and same-address
+// atomics from every thread would serialise there.
+__device__ __forceinline__ void hist_add(unsigned* fine, unsigned* coarse, int bin, int delta) {
+  const unsigned lt = (1u << lane_id()) - 1u;
+  const unsigned pf = __match_any_sync(kFull, bin);
+  if (bin >= 0 && (pf & lt) == 0) atomicAdd(&fine[bin], (unsigned)(delta * __popc(pf)));
+  const int cb = bin >= 0 ? bin / kCoarse : -1;
+  const unsigned pc = __match_any_sync(kFull, cb);
+  if (cb >= 0 && (pc & lt) == 0) atomicAdd(&coarse[cb], (unsigned)(delta * __popc(pc)));
+}
+
 // Mixed key of (E, fp) for the dedup table; 0 marks an empty slot, so a mixed key of 0 becomes 1.
 __device__ __forceinline__ uint64_t dedup_key(int E, uint64_t fp) {
   const uint64_t k = fp ^ ((uint64_t)(uint32_t)E * 0xD6E8FEB86659FD93ull);
   return k ? k : 1ull;
-}
-
-// Key of a boundary candidate (pool entry or survivor).
-__device__ __forceinline__ void cand_key(const PqBufs& b, int32_t c, int& E, uint64_t& fp) {
-  if (c >= 0) {
-    E = b.pE[c];
-    fp = b.pFp[c];
-  } else {
-    E = b.uE[-c - 1];
-    fp = b.uFp[-c - 1];
-  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -236,6 +272,8 @@ __global__ void pq_init_kernel(PqBufs b) {
     z.minE_round = INT32_MAX;
     z.minfp_round = ~0ull;
     z.best_rep_round = ~0u;
+    z.pmax_bin = -1;
+    z.n_dense = b.n_seeds;
     *b.st = z;
   }
 }
@@ -296,11 +334,14 @@ __global__ void pq_round_begin_kernel(PqBufs b) {
   st->pop_cnt = 0;
   st->cand_cnt = 0;
   st->nU = 0;
+  st->n_dense = 0;
   st->ev_round = 0;
   st->adm_round = 0;
   st->minE_round = INT32_MAX;
   st->minfp_round = ~0ull;
   st->best_rep_round = ~0u;
+  st->nU_low = 0;
+  st->hist_mode = 0;
   if (st->stop) {
     st->b = 0;
     return;
@@ -308,6 +349,7 @@ __global__ void pq_round_begin_kernel(PqBufs b) {
   long long bb = min((long long)b.B, st->nP);
   bb = min(bb, b.max_exp - st->expansions);
   st->b = (int)bb;
+  st->n_dense = bb * b.width;
 }
 
 // One block: the fine bin where the count of entries reaches the target (POP: b over the pool; else
@@ -327,8 +369,7 @@ __global__ void __launch_bounds__(kSelThreads) pq_select_kernel(PqBufs b) {
       target = st->b;
     } else {
       st->cand_cnt = 0;  // the pop's candidates are done with
-      const long long total = st->nP - st->b + st->nU;
-      target = total > b.cap ? b.cap : -1;
+      target = st->hist_mode ? b.cap : -1;
     }
     s_target = target;
     if (target <= 0) {
@@ -390,55 +431,124 @@ __global__ void __launch_bounds__(256) pq_gather_kernel(PqBufs b) {
   PqState* st = b.st;
   if (POP ? st->b == 0 : st->sel_need <= 0) return;
   const int sel = st->sel_bin, Eb = st->E_base;
-  const long long n = U ? st->nU : b.cap;
+  const long long n = U ? st->n_dense : b.cap;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
     const long long i = base + threadIdx.x;
     int bin = kNB;
+    int E = INT32_MAX;
     if (i < n) {
-      const int E = U ? b.uE[i] : b.pE[i];
+      E = U ? (b.uRep[i] != ~0u ? b.dE[i] : INT32_MAX) : b.pE[i];
       if (E != INT32_MAX) bin = e_bin(E, Eb);
     }
     // the histogram bounds both counts (b entries below the boundary bin at most); a count beyond a
     // buffer can only come from an inconsistent state, which is reported instead of written
     if (POP) {
       const long long o = warp_append(&st->pop_cnt, bin < sel);
-      if (o >= b.B) st->error = 1;
-      else if (o >= 0) b.popId[o] = (int32_t)i;
+      if (o >= b.B) {
+        st->error = 1;
+      } else if (o >= 0) {
+        b.popId[o] = (int32_t)i;
+        b.popE[o] = E;
+        b.popF[o] = b.pFp[i];
+      }
     }
     const long long o2 = warp_append(&st->cand_cnt, bin == sel);
-    if (o2 >= b.cand_cap) st->error = 1;
-    else if (o2 >= 0) b.candId[o2] = U ? -(int32_t)i - 1 : (int32_t)i;
+    if (o2 >= b.cand_cap) {
+      st->error = 1;
+    } else if (o2 >= 0) {
+      b.candId[o2] = U ? -(int32_t)i - 1 : (int32_t)i;
+      b.cE[o2] = E;
+      b.cF[o2] = U ? b.dFp[i] : b.pFp[i];
+    }
   }
 }
 
 // One block: the sel_need smallest (E, fp) keys among the boundary candidates, by a most-significant-
-// digit-first radix select over the 96-bit key (four energy bytes, then eight fingerprint bytes); keys
-// are distinct, so exactly sel_need candidates are <= the selected key.  POP appends them to the pops.
+// digit-first radix select over the 96-bit key (four energy bytes, then eight fingerprint bytes; the
+// energy bytes are skipped when the boundary bin holds one energy, i.e. it is not clamped); keys are
+// distinct, so exactly sel_need candidates are <= the selected key.  The candidates' keys are read
+// from the contiguous gather arrays, staged in shared memory when they fit.  POP appends the selected
+// candidates to the pops.
+constexpr int kCandSmem = 8192;  // candidates staged in shared memory (12 B each)
 template <bool POP>
 __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   PqState* st = b.st;
   if (POP ? st->b == 0 : st->sel_need <= 0) return;
   const long long n = min(st->cand_cnt, b.cand_cap);
+  extern __shared__ unsigned long long sm_cand[];
+  uint64_t* sF = reinterpret_cast<uint64_t*>(sm_cand);
+  int* sE = reinterpret_cast<int*>(sm_cand + kCandSmem);
   __shared__ unsigned hist[256];
   __shared__ unsigned long long s_pre_e, s_pre_f;  // the digits fixed so far
   __shared__ long long s_k;
+  __shared__ int s_nw, s_ok;
+  __shared__ unsigned long long s_below;
   const int t = threadIdx.x;
+  const bool one_energy = st->sel_bin > 0 && st->sel_bin < kNB - 1;
+  bool staged = n <= kCandSmem;
+  long long nsel = n;  // entries the radix select ranks (all candidates, or the window)
   if (t == 0) {
-    s_pre_e = 0;
+    s_pre_e = one_energy ? (unsigned long long)(uint32_t)(st->E_base + st->sel_bin) : 0ull;
     s_pre_f = 0;
     s_k = st->sel_need;
+    s_nw = 0;
+    s_ok = 0;
+    s_below = 0;
   }
   __syncthreads();
-  for (int d = 0; d < 12; d++) {
+  if (staged) {
+    for (long long i = t; i < n; i += kSelThreads) {
+      sF[i] = b.cF[i];
+      sE[i] = b.cE[i];
+    }
+  } else if (one_energy) {
+    // Many candidates, one energy: their fingerprints are uniform 64-bit values, so the k-th smallest
+    // lies near k/n of the range.  One pass counts the candidates below a window around that point and
+    // stages the window's candidates; when the k-th smallest falls inside it, the select ranks only the
+    // window (else it falls back to ranking every candidate).
+    const double k = (double)s_k, delta = 4.0 * sqrt(k) + 64.0;
+    const double flo = fmax(0.0, (k - delta) / (double)n), fhi = (k + delta) / (double)n;
+    const uint64_t lo = flo <= 0.0 ? 0ull : (uint64_t)(flo * 18446744073709549568.0);
+    const uint64_t hi = fhi >= 1.0 ? ~0ull : (uint64_t)(fhi * 18446744073709549568.0);
+    unsigned long long below = 0;
+    for (long long i = t; i < n; i += kSelThreads) {
+      const uint64_t fp = b.cF[i];
+      if (fp < lo) {
+        below++;
+      } else if (fp <= hi) {
+        const int w = atomicAdd(&s_nw, 1);
+        if (w < kCandSmem) {
+          sF[w] = fp;
+          sE[w] = b.cE[i];
+        }
+      }
+    }
+    atomicAdd(&s_below, below);
+    __syncthreads();
+    if (t == 0) {
+      const long long kk = s_k;
+      if (s_nw <= kCandSmem && (long long)s_below < kk && kk <= (long long)s_below + s_nw) {
+        s_ok = 1;
+        s_k = kk - (long long)s_below;
+      }
+    }
+    __syncthreads();
+    if (s_ok) {
+      staged = true;
+      nsel = s_nw;
+    }
+  }
+  __syncthreads();
+  const uint64_t* F = staged ? sF : b.cF;
+  const int* Ev = staged ? sE : b.cE;
+  for (int d = one_energy ? 4 : 0; d < 12; d++) {
     if (t < 256) hist[t] = 0;
     __syncthreads();
     const unsigned long long pe = s_pre_e, pf = s_pre_f;
-    for (long long i = t; i < n; i += kSelThreads) {
-      int E;
-      uint64_t fp;
-      cand_key(b, b.candId[i], E, fp);
-      const uint64_t ue = (uint32_t)E;
+    for (long long i = t; i < nsel; i += kSelThreads) {
+      const uint64_t ue = (uint32_t)Ev[i];
+      const uint64_t fp = F[i];
       bool match;
       unsigned digit;
       if (d < 4) {
@@ -453,16 +563,25 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
       if (match) atomicAdd(&hist[digit], 1u);
     }
     __syncthreads();
-    if (t == 0) {
+    // the digit where the count reaches k: an inclusive scan of the 256 bins, then the one bin that
+    // crosses k
+    unsigned c = t < 256 ? hist[t] : 0u;
+    for (int off = 1; off < 256; off <<= 1) {
+      const unsigned v = (t < 256 && t >= off) ? hist[t - off] : 0u;
+      __syncthreads();
+      if (t < 256) hist[t] = c = c + v;
+      __syncthreads();
+    }
+    if (t < 256) {
       const long long k = s_k;
-      long long acc = 0;
-      int dg = 0;
-      while (dg < 255 && acc + hist[dg] < k) acc += hist[dg++];
-      s_k = k - acc;
-      if (d < 4)
-        s_pre_e = pe | ((unsigned long long)dg << (24 - 8 * d));
-      else
-        s_pre_f = pf | ((unsigned long long)dg << (56 - 8 * (d - 4)));
+      const long long before = t ? hist[t - 1] : 0;
+      if (before < k && (long long)c >= k) {
+        s_k = k - before;
+        if (d < 4)
+          s_pre_e = pe | ((unsigned long long)t << (24 - 8 * d));
+        else
+          s_pre_f = pf | ((unsigned long long)t << (56 - 8 * (d - 4)));
+      }
     }
     __syncthreads();
   }
@@ -474,92 +593,101 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   }
   if (POP) {
     for (long long i = t; i < n; i += kSelThreads) {
-      int E;
-      uint64_t fp;
-      const int32_t c = b.candId[i];
-      cand_key(b, c, E, fp);
-      if (key_le(E, fp, selE, selF)) {
+      if (key_le(b.cE[i], b.cF[i], selE, selF)) {
         const long long o = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&st->pop_cnt), 1ull);
-        if (o < b.B)
-          b.popId[o] = c;
-        else
+        if (o < b.B) {
+          b.popId[o] = b.candId[i];
+          b.popE[o] = b.cE[i];
+          b.popF[o] = b.cF[i];
+        } else {
           st->error = 1;
+        }
       }
     }
   }
 }
 
-// One block: the popped entries in key order (bitonic sort of (E, fp, id), padded to a power of two)
-// become pivots 0..b-1; their pool slots are freed and leave the histogram.
-__global__ void __launch_bounds__(kSelThreads) pq_pop_sort_kernel(PqBufs b) {
+// Grid (x: 256 popped entries per block, y: kRankChunks slices of the others): the popped entries in key
+// order.  Keys are distinct, so the number of popped keys smaller than a key is its rank; every block
+// adds its slice's count to the entry's rank.
+constexpr int kRankChunks = 16;
+__global__ void __launch_bounds__(256) pq_pop_rank_kernel(PqBufs b) {
   PqState* st = b.st;
   const int nb = st->b;
   if (nb == 0) return;
   if (st->pop_cnt != nb || st->error) {  // an inconsistent pop: stop the search (capacity status)
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
       st->error = 1;
       st->b = 0;
+      st->n_dense = 0;
     }
     return;
   }
-  extern __shared__ unsigned long long sm_pop[];
-  unsigned long long* kf = sm_pop;                      // fingerprints
-  int* ke = reinterpret_cast<int*>(sm_pop + kSortMax);  // energies
-  int* ki = ke + kSortMax;                              // pool ids
-  int n2 = 1;
-  while (n2 < nb) n2 <<= 1;
-  const int t = threadIdx.x;
-  for (int i = t; i < n2; i += kSelThreads) {
-    if (i < nb) {
-      const int id = b.popId[i];
-      kf[i] = b.pFp[id];
-      ke[i] = b.pE[id];
-      ki[i] = id;
-    } else {
-      kf[i] = ~0ull;
-      ke[i] = INT32_MAX;
-      ki[i] = -1;
-    }
+  __shared__ uint64_t sF[kSortMax / kRankChunks];
+  __shared__ int sE[kSortMax / kRankChunks];
+  const int per = (nb + kRankChunks - 1) / kRankChunks;
+  const int j0 = blockIdx.y * per, j1 = min(nb, j0 + per);
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    sF[j - j0] = b.popF[j];
+    sE[j - j0] = b.popE[j];
   }
   __syncthreads();
-  for (int size = 2; size <= n2; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = t; i < n2; i += kSelThreads) {
-        const int j = i ^ stride;
-        if (j > i) {
-          const bool up = (i & size) == 0;
-          const bool gt = key_lt(ke[j], kf[j], ke[i], kf[i]);  // a[i] > a[j]
-          if (gt == up) {
-            const unsigned long long f = kf[i];
-            kf[i] = kf[j];
-            kf[j] = f;
-            const int e = ke[i];
-            ke[i] = ke[j];
-            ke[j] = e;
-            const int d = ki[i];
-            ki[i] = ki[j];
-            ki[j] = d;
-          }
-        }
-      }
-      __syncthreads();
-    }
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += gridDim.x * blockDim.x) {
+    const int E = b.popE[q];
+    const uint64_t fp = b.popF[q];
+    int r = 0;
+    for (int j = 0; j < j1 - j0; j++) r += key_lt(sE[j], sF[j], E, fp) ? 1 : 0;
+    if (r) atomicAdd(&b.popRank[q], r);
+  }
+}
+
+// Grid: the pivots' sequences leave their pool slots, which are freed (pushed on the stack) and leave
+// the histogram.
+__global__ void __launch_bounds__(256) pq_pivot_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const int nb = st->b;
   const int Eb = st->E_base;
-  const long long top = st->free_top;
-  for (int q = t; q < nb; q += kSelThreads) {
-    const int id = ki[q];
-    b.pivE[q] = ke[q];
-    b.pivFp[q] = kf[q];
-    for (int w = 0; w < b.W; w++) b.pivSeq[(size_t)q * b.W + w] = b.pSeq[(size_t)id * b.W + w];
-    b.pE[id] = INT32_MAX;
-    b.freeIds[top + q] = id;
-    const int bin = e_bin(ke[q], Eb);
-    atomicSub(&b.hP[bin], 1u);
-    atomicSub(&b.hP2[bin / kCoarse], 1u);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nb; base += stride) {
+    const long long q = base + threadIdx.x;
+    const bool on = q < nb;
+    int id = 0, bin = -1;
+    if (on) {
+      int r = b.popRank[q];  // pivot index = rank (keys are distinct, so 0 <= r < nb)
+      if (r < 0 || r >= nb) {
+        st->error = 1;
+        r = (int)q;
+      }
+      id = b.popId[q];
+      const int E = b.popE[q];
+      b.pivE[r] = E;
+      b.pivFp[r] = b.popF[q];
+      for (int w = 0; w < b.W; w++) b.pivSeq[(size_t)r * b.W + w] = b.pSeq[(size_t)id * b.W + w];
+      b.pE[id] = INT32_MAX;
+      b.popRank[q] = 0;  // cleared for the next round
+      bin = e_bin(E, Eb);
+    }
+    const long long o = warp_append(&st->free_top, on);
+    if (on) b.freeIds[o] = id;
+    hist_add(b.hP, b.hP2, bin, -1);
+  }
+}
+
+// One block: the highest occupied bin of the pool (after the pops), -1 when it is empty.
+__global__ void __launch_bounds__(kSelThreads) pq_pmax_kernel(PqBufs b) {
+  __shared__ int s_cb, s_fb;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_cb = -1;
+    s_fb = -1;
   }
   __syncthreads();
-  if (t == 0) st->free_top = top + nb;
+  if (t < kNC && b.hP2[t]) atomicMax(&s_cb, t);
+  __syncthreads();
+  const int cb = s_cb;
+  if (cb >= 0 && t < kCoarse && b.hP[cb * kCoarse + t]) atomicMax(&s_fb, cb * kCoarse + t);
+  __syncthreads();
+  if (t == 0) b.st->pmax_bin = cb >= 0 ? s_fb : -1;
 }
 
 // One warp per pivot: Delta E of all L single flips, visited-set test, dense survivor output.
@@ -659,115 +787,102 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
   }
 }
 
-// Dense survivors of the round: b pivots x width columns, or the seeds (one column each).
+// Dedup, first pass: every survivor inserts its (E, fp) key; the first inserter of a key becomes the
+// key's unique survivor (marked in uRep, its representative settled by the second pass) and the table
+// slot points to its dense index.  Unique survivors stay at their dense index: nothing is compacted.
 template <bool SEED>
-__device__ __forceinline__ long long dense_n(const PqBufs& b, int n_seeds) {
-  return SEED ? (long long)n_seeds : (long long)b.st->b * b.width;
-}
-
-// Dedup, first pass: every survivor inserts its (E, fp) key; the first inserter of a key creates the
-// unique survivor (its representative is settled by the second pass).
-template <bool SEED>
-__global__ void __launch_bounds__(256) pq_dedup_insert_kernel(PqBufs b, int n_seeds) {
-  const long long n = dense_n<SEED>(b, n_seeds);
+__global__ void __launch_bounds__(256) pq_dedup_insert_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = st->n_dense;
   const uint64_t mask = (1ull << b.hs_log2) - 1;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
+  const int Eb = st->E_base, pmax = st->pmax_bin;
+  long long fresh_n = 0, low = 0;
+  int mE = INT32_MAX;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int E = b.dE[i];
     bool fresh = false;
-    uint64_t slot = 0;
-    int E = INT32_MAX;
-    uint64_t fp = 0;
-    if (i < n) {
-      E = b.dE[i];
-      fp = b.dFp[i];
-    }
     if (E != INT32_MAX) {
-      const uint64_t k = dedup_key(E, fp);
+      const uint64_t k = dedup_key(E, b.dFp[i]);
       uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
       for (uint64_t it = 0; it <= mask; it++) {  // the table holds at most half its slots
         const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&b.hkey[s]), 0ull, k);
         if (old == 0ull) {
           fresh = true;
-          slot = s;
+          b.hval[s] = (int32_t)i;
           break;
         }
         if (old == k) break;
         s = (s + 1) & mask;
       }
     }
-    const long long u = warp_append(&b.st->nU, fresh);
+    b.uRep[i] = fresh ? 0xFFFFFFFEu : ~0u;
+    fresh_n += fresh ? 1 : 0;
     if (fresh) {
-      b.uE[u] = E;
-      b.uFp[u] = fp;
-      b.uRep[u] = ~0u;
-      b.uSlot[u] = (int32_t)slot;
-      b.hval[slot] = (int32_t)u;
+      mE = min(mE, E);
+      low += e_bin(E, Eb) <= pmax ? 1 : 0;
     }
   }
+  block_add(&st->nU, fresh_n);
+  block_min(&st->minE_round, mE);
+  block_add(&st->nU_low, low);
 }
 
-// Dedup, second pass: each survivor finds its key's slot and lowers the representative to the smallest
-// (pivot, column) -- the pivots are in key order, so this is the sequential definition's first occurrence.
+// Which survivors the cut needs counted.  Everything fits: none.  The pool's rest and the survivors
+// inside its occupied bins reach the cap: the cut lies in those bins, so only they are counted.
+// Otherwise all of them.
+__device__ __forceinline__ int hist_mode_of(const PqState* st, long long cap) {
+  const long long rest = st->nP - st->b;
+  if (rest + st->nU <= cap) return 0;
+  if (st->pmax_bin >= 0 && rest + st->nU_low >= cap) return 1;
+  return 2;
+}
+
+// Dedup, second pass: each survivor finds its key's slot and lowers the representative of the key's
+// unique survivor to the smallest (pivot, column) -- the pivots are in key order, so this is the
+// sequential definition's first occurrence.  The unique survivors also enter the survivor histogram (the
+// bins the cut needs) and give the smallest fingerprint among the smallest-energy survivors.
 template <bool SEED>
-__global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b, int n_seeds) {
-  const long long n = dense_n<SEED>(b, n_seeds);
+__global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b) {
+  PqState* st = b.st;
+  const long long n = st->n_dense;
   const uint64_t mask = (1ull << b.hs_log2) - 1;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int E = b.dE[i];
-    if (E == INT32_MAX) continue;
-    const uint64_t k = dedup_key(E, b.dFp[i]);
-    uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
-    for (uint64_t it = 0; it <= mask; it++) {
-      if (b.hkey[s] == k) break;
-      s = (s + 1) & mask;
+  const int mode = hist_mode_of(st, b.cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->hist_mode = mode;
+  const int Eb = st->E_base, pmax = st->pmax_bin, mE = st->minE_round;
+  uint64_t mf = ~0ull;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const long long i = base + threadIdx.x;
+    int bin = -1;
+    if (i < n) {
+      const int E = b.dE[i];
+      if (E != INT32_MAX) {
+        const uint64_t fp = b.dFp[i];
+        const uint64_t k = dedup_key(E, fp);
+        uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
+        for (uint64_t it = 0; it <= mask; it++) {
+          if (b.hkey[s] == k) break;
+          s = (s + 1) & mask;
+        }
+        const unsigned rep = SEED ? (unsigned)i << kColBits
+                                  : ((unsigned)(i / b.width) << kColBits) | (unsigned)(i % b.width);
+        atomicMin(&b.uRep[b.hval[s]], rep);
+        if (b.hval[s] == (int32_t)i) {  // the key's unique survivor
+          const int eb = e_bin(E, Eb);
+          if (mode == 2 || (mode == 1 && eb <= pmax)) bin = eb;
+          if (E == mE) mf = min(mf, fp);
+        }
+      }
     }
-    const unsigned rep = SEED ? (unsigned)i << kColBits
-                              : ((unsigned)(i / b.width) << kColBits) | (unsigned)(i % b.width);
-    atomicMin(&b.uRep[b.hval[s]], rep);
+    if (mode) hist_add(b.hU, b.hU2, bin, 1);
   }
-}
-
-// The round's smallest survivor energy.
-__global__ void __launch_bounds__(256) pq_u_min_kernel(PqBufs b) {
-  const long long n = b.st->nU;
-  int m = INT32_MAX;
-  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
-    m = min(m, b.uE[u]);
-  m = __reduce_min_sync(kFull, m);
-  if (lane_id() == 0 && m != INT32_MAX) atomicMin(&b.st->minE_round, m);
+  if (mf != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(&st->minfp_round), (unsigned long long)mf);
 }
 
 // The histogram's energy window, from the smallest seed energy (improvements stay far inside it).
 __global__ void pq_set_window_kernel(PqBufs b) {
   PqState* st = b.st;
   st->E_base = st->minE_round == INT32_MAX ? 0 : max(0, st->minE_round - kNB / 2);
-}
-
-// Survivor histogram, and the smallest fingerprint among the smallest-energy survivors.
-__global__ void __launch_bounds__(256) pq_u_hist_kernel(PqBufs b) {
-  PqState* st = b.st;
-  const long long n = st->nU;
-  const int Eb = st->E_base, mE = st->minE_round;
-  uint64_t mf = ~0ull;
-  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
-    const int E = b.uE[u];
-    const int bin = e_bin(E, Eb);
-    atomicAdd(&b.hU[bin], 1u);
-    atomicAdd(&b.hU2[bin / kCoarse], 1u);
-    if (E == mE) mf = min(mf, b.uFp[u]);
-  }
-  if (mf != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(&st->minfp_round), (unsigned long long)mf);
-}
-
-// The representative of the smallest survivor key (unique).
-__global__ void __launch_bounds__(256) pq_u_best_kernel(PqBufs b) {
-  PqState* st = b.st;
-  const long long n = st->nU;
-  const int mE = st->minE_round;
-  const uint64_t mf = st->minfp_round;
-  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x)
-    if (b.uE[u] == mE && b.uFp[u] == mf) st->best_rep_round = b.uRep[u];
 }
 
 // One thread: the best (a strict improvement, as in Algorithm 2; for the seeds, the smallest seed) and
@@ -829,19 +944,19 @@ __global__ void __launch_bounds__(256) pq_evict_kernel(PqBufs b) {
     if (out) {
       b.freeIds[o] = (int32_t)i;
       b.pE[i] = INT32_MAX;
-      atomicSub(&b.hP[bin], 1u);
-      atomicSub(&b.hP2[bin / kCoarse], 1u);
     }
+    hist_add(b.hP, b.hP2, out ? bin : -1, -1);
     warp_add(&st->ev_round, out ? 1 : 0);
   }
 }
 
 // Survivor pass: the survivors inside the cut take a free slot (the sequence built from the pivot, or
-// copied from the seed) and enter the visited set; every survivor clears its dedup slot.
+// copied from the seed) and enter the visited set; the smallest survivor key's representative is noted
+// for the best.
 template <bool SEED>
 __global__ void __launch_bounds__(256) pq_admit_kernel(PqBufs b) {
   PqState* st = b.st;
-  const long long n = st->nU;
+  const long long n = st->n_dense;
   const int Eb = st->E_base;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -849,12 +964,12 @@ __global__ void __launch_bounds__(256) pq_admit_kernel(PqBufs b) {
     bool in = false;
     int E = 0, bin = 0;
     uint64_t fp = 0;
-    if (u < n) {
-      E = b.uE[u];
-      fp = b.uFp[u];
+    if (u < n && b.uRep[u] != ~0u) {
+      E = b.dE[u];
+      fp = b.dFp[u];
       bin = e_bin(E, Eb);
       in = below_cut(st, bin, E, fp);
-      b.hkey[b.uSlot[u]] = 0ull;
+      if (E == st->minE_round && fp == st->minfp_round) st->best_rep_round = b.uRep[u];  // the smallest key
     }
     // free slots come off the top of the stack, one atomic per warp
     const unsigned m = __ballot_sync(kFull, in);
@@ -887,10 +1002,9 @@ __global__ void __launch_bounds__(256) pq_admit_kernel(PqBufs b) {
         pq_child(b.pivSeq + (size_t)(rep >> kColBits) * b.W, b, (int)(rep & ((1u << kColBits) - 1u)),
                  b.pSeq + (size_t)id * b.W);
       }
-      atomicAdd(&b.hP[bin], 1u);
-      atomicAdd(&b.hP2[bin / kCoarse], 1u);
       ins = h_insert(b, fp);
     }
+    hist_add(b.hP, b.hP2, in ? bin : -1, 1);
     h_count(b, ins);
     warp_add(&st->adm_round, in ? 1 : 0);
   }
@@ -951,11 +1065,13 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   const size_t opE = take(4 * cap), opF = take(8 * cap), opS = take(8 * cap * W), ofree = take(4 * cap);
   const size_t ohP = take(4 * kNB), ohP2 = take(4 * kNC), ohU = take(4 * kNB), ohU2 = take(4 * kNC);
   const size_t opop = take(4 * (size_t)cfg->B), opivE = take(4 * (size_t)cfg->B), opivF = take(8 * (size_t)cfg->B);
+  const size_t opopE = take(4 * (size_t)cfg->B), opopF = take(8 * (size_t)cfg->B);
   const size_t opivS = take(8 * (size_t)cfg->B * W);
-  const size_t ocand = take(4 * (size_t)(cap + n_dense));
+  const size_t ocand = take(4 * (size_t)(cap + n_dense)), ocE = take(4 * (size_t)(cap + n_dense));
+  const size_t ocF = take(8 * (size_t)(cap + n_dense)), orank = take(4 * (size_t)cfg->B);
   const size_t odE = take(4 * n_dense), odF = take(8 * n_dense);
   const size_t ohk = take(8ull << hs_log2), ohv = take(4ull << hs_log2);
-  const size_t ouE = take(4 * n_dense), ouF = take(8 * n_dense), ouR = take(4 * n_dense), ouS = take(4 * n_dense);
+  const size_t ouR = take(4 * n_dense);
   const size_t ozt = take(8 * L), ost = take(sizeof(PqState)), obest = take(8 * W);
   const size_t oH = take(8ull << cfg->H_log2);
   char* base = static_cast<char*>(ws_get(ctx, kWsPq0, off));
@@ -982,18 +1098,20 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   b.hU = reinterpret_cast<unsigned*>(base + ohU);
   b.hU2 = reinterpret_cast<unsigned*>(base + ohU2);
   b.popId = reinterpret_cast<int32_t*>(base + opop);
+  b.popE = reinterpret_cast<int32_t*>(base + opopE);
+  b.popF = reinterpret_cast<uint64_t*>(base + opopF);
   b.pivE = reinterpret_cast<int32_t*>(base + opivE);
   b.pivFp = reinterpret_cast<uint64_t*>(base + opivF);
   b.pivSeq = reinterpret_cast<uint64_t*>(base + opivS);
   b.candId = reinterpret_cast<int32_t*>(base + ocand);
+  b.cE = reinterpret_cast<int32_t*>(base + ocE);
+  b.cF = reinterpret_cast<uint64_t*>(base + ocF);
+  b.popRank = reinterpret_cast<int32_t*>(base + orank);
   b.dE = reinterpret_cast<int32_t*>(base + odE);
   b.dFp = reinterpret_cast<uint64_t*>(base + odF);
   b.hkey = reinterpret_cast<uint64_t*>(base + ohk);
   b.hval = reinterpret_cast<int32_t*>(base + ohv);
-  b.uE = reinterpret_cast<int32_t*>(base + ouE);
-  b.uFp = reinterpret_cast<uint64_t*>(base + ouF);
   b.uRep = reinterpret_cast<unsigned*>(base + ouR);
-  b.uSlot = reinterpret_cast<int32_t*>(base + ouS);
   b.ztab = reinterpret_cast<uint64_t*>(base + ozt);
   b.st = reinterpret_cast<PqState*>(base + ost);
   b.best_seq = reinterpret_cast<uint64_t*>(base + obest);
@@ -1003,42 +1121,41 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   const unsigned g_pool = (unsigned)std::max(1ll, std::min<long long>((cap + 255) / 256, (long long)ctx->num_sms * 16));
   const unsigned g_dense =
       (unsigned)std::max(1ll, std::min<long long>((n_dense + 255) / 256, (long long)ctx->num_sms * 16));
-  const size_t sort_smem = (size_t)kSortMax * 16;
-  if (cudaFuncSetAttribute(pq_pop_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem) !=
-      cudaSuccess)
+  const size_t cand_smem = (size_t)kCandSmem * 12;
+  if (cudaFuncSetAttribute(pq_boundary_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cand_smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(pq_boundary_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cand_smem) !=
+          cudaSuccess)
     return LABS_ERR_CUDA;
+  const unsigned g_piv = (unsigned)std::max(1, std::min((cfg->B + 255) / 256, ctx->num_sms * 4));
 
   // The survivor path, shared by the seeds and every round: dedup, best, cut, eviction, admission.
   auto survivor_path = [&](bool seed, cudaStream_t s) {
     if (seed) {
-      pq_dedup_insert_kernel<true><<<g_dense, 256, 0, s>>>(b, n_seeds);
-      pq_dedup_rep_kernel<true><<<g_dense, 256, 0, s>>>(b, n_seeds);
+      pq_dedup_insert_kernel<true><<<g_dense, 256, 0, s>>>(b);
+      pq_set_window_kernel<<<1, 1, 0, s>>>(b);
+      pq_dedup_rep_kernel<true><<<g_dense, 256, 0, s>>>(b);
     } else {
-      pq_dedup_insert_kernel<false><<<g_dense, 256, 0, s>>>(b, n_seeds);
-      pq_dedup_rep_kernel<false><<<g_dense, 256, 0, s>>>(b, n_seeds);
+      pq_dedup_insert_kernel<false><<<g_dense, 256, 0, s>>>(b);
+      pq_dedup_rep_kernel<false><<<g_dense, 256, 0, s>>>(b);
     }
-    pq_u_min_kernel<<<g_dense, 256, 0, s>>>(b);
-    if (seed) pq_set_window_kernel<<<1, 1, 0, s>>>(b);
-    pq_u_hist_kernel<<<g_dense, 256, 0, s>>>(b);
-    pq_u_best_kernel<<<g_dense, 256, 0, s>>>(b);
-    if (seed)
-      pq_best_kernel<true><<<1, 1, 0, s>>>(b);
-    else
-      pq_best_kernel<false><<<1, 1, 0, s>>>(b);
     pq_select_kernel<false><<<1, kSelThreads, 0, s>>>(b);
     pq_gather_kernel<false, false><<<g_pool, 256, 0, s>>>(b);
     pq_gather_kernel<false, true><<<g_dense, 256, 0, s>>>(b);
-    pq_boundary_kernel<false><<<1, kSelThreads, 0, s>>>(b);
+    pq_boundary_kernel<false><<<1, kSelThreads, cand_smem, s>>>(b);
     pq_evict_kernel<<<g_pool, 256, 0, s>>>(b);
     if (seed) {
       pq_admit_kernel<true><<<g_dense, 256, 0, s>>>(b);
+      pq_best_kernel<true><<<1, 1, 0, s>>>(b);
       pq_round_end_kernel<true><<<1, 1, 0, s>>>(b);
     } else {
       pq_admit_kernel<false><<<g_dense, 256, 0, s>>>(b);
+      pq_best_kernel<false><<<1, 1, 0, s>>>(b);
       pq_round_end_kernel<false><<<1, 1, 0, s>>>(b);
     }
     cudaMemsetAsync(b.hU, 0, 4 * kNB, s);
     cudaMemsetAsync(b.hU2, 0, 4 * kNC, s);
+    cudaMemsetAsync(b.hkey, 0, 8ull << hs_log2, s);  // the dedup table, for the next round
   };
 
   // ---- set-up: visited set, pool, histograms, dedup table, Zobrist keys; the seeds go through the
@@ -1046,7 +1163,8 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
   if (cudaMemsetAsync(b.H, 0xff, 8ull << cfg->H_log2, st) != cudaSuccess) return LABS_ERR_CUDA;
   if (cudaMemsetAsync(b.hP, 0, 4 * kNB, st) != cudaSuccess || cudaMemsetAsync(b.hP2, 0, 4 * kNC, st) != cudaSuccess ||
       cudaMemsetAsync(b.hU, 0, 4 * kNB, st) != cudaSuccess || cudaMemsetAsync(b.hU2, 0, 4 * kNC, st) != cudaSuccess ||
-      cudaMemsetAsync(b.hkey, 0, 8ull << hs_log2, st) != cudaSuccess)
+      cudaMemsetAsync(b.hkey, 0, 8ull << hs_log2, st) != cudaSuccess ||
+      cudaMemsetAsync(b.popRank, 0, 4 * (size_t)cfg->B, st) != cudaSuccess)
     return LABS_ERR_CUDA;
   pq_ztab_kernel<<<(L + 255) / 256, 256, 0, st>>>(b.ztab, L);
   pq_init_kernel<<<g_pool, 256, 0, st>>>(b);
@@ -1069,8 +1187,10 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     pq_round_begin_kernel<<<1, 1, 0, cs>>>(b);
     pq_select_kernel<true><<<1, kSelThreads, 0, cs>>>(b);
     pq_gather_kernel<true, false><<<g_pool, 256, 0, cs>>>(b);
-    pq_boundary_kernel<true><<<1, kSelThreads, 0, cs>>>(b);
-    pq_pop_sort_kernel<<<1, kSelThreads, sort_smem, cs>>>(b);
+    pq_boundary_kernel<true><<<1, kSelThreads, cand_smem, cs>>>(b);
+    pq_pop_rank_kernel<<<dim3((unsigned)((cfg->B + 255) / 256), kRankChunks), 256, 0, cs>>>(b);
+    pq_pivot_kernel<<<g_piv, 256, 0, cs>>>(b);
+    pq_pmax_kernel<<<1, kSelThreads, 0, cs>>>(b);
     pq_expand_kernel<<<exp_blocks, 32 * kPqWarps, 0, cs>>>(b, ly);
     survivor_path(false, cs);
   }

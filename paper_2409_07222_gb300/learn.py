@@ -96,9 +96,15 @@ def _time_to_target(L, p, prefixes, n_walks, flip_budget, seed, E_star, policy, 
 
 def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=8192, train_steps=3000, batch=512,
                lr=1e-3, lambdas=(5.0, 20.0, 80.0), eval_walks=256, eval_flips=8192, n_seeds=30, ttt_walks=8192,
-               ttt_flips=16384, ttt_seeds=10, chunk=64, device=None, log=print):
+               ttt_pilot_flips=1 << 18, ttt_pilot_seeds=5, ttt_budget_factor=2, ttt_seeds=10, chunk=64, device=None,
+               log=print):
     """Collect tuples from plain walks, train the network, pick lambda on pilot seeds, then compare learned
-    vs plain at an equal flip budget on fresh seeds (rank-sum) and time both to a pre-registered E*."""
+    vs plain at an equal flip budget on fresh seeds (rank-sum) and time both to a pre-registered E*.
+
+    E* for the timing comes from a plain pilot of the timed shape itself: ttt_walks walks of ttt_pilot_flips
+    flips (seconds of plain search), median best F over ttt_pilot_seeds seeds, E* = floor(L^2 / (2 F*)).
+    Each timed run then gets ttt_budget_factor times the pilot's flips; a seed that never reaches E* counts
+    as slower than every seed that does."""
     import time
 
     out = {}
@@ -127,9 +133,19 @@ def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=81
         if gain > best_gain:
             best_lam, best_gain = lam, gain
     lam = best_lam if best_lam > 0 else float(lambdas[0])
-    F_star = float(np.median([L * L / (2.0 * e) for e in plain_pilot]))
+    # the timing target: the plain search of the timed shape, seconds long, on its own pilot seeds
+    ttt_pilot = [3000 + i for i in range(ttt_pilot_seeds)]
+    t = time.perf_counter()
+    pilot_best = [best_energies(L, p, prefixes, ttt_walks, ttt_pilot_flips, s, chunk=chunk, device=device)[0]
+                  for s in ttt_pilot]
+    pilot_s = (time.perf_counter() - t) / max(1, len(ttt_pilot))
+    F_star = float(np.median([L * L / (2.0 * e) for e in pilot_best]))
     E_star = int(np.floor(L * L / (2.0 * F_star)))
-    out["preregistered"] = {"lambda": lam, "pilot_seeds": pilot, "F_star": F_star, "E_star": E_star}
+    out["preregistered"] = {"lambda": lam, "lambda_pilot_seeds": pilot, "E_star_pilot_seeds": ttt_pilot,
+                            "E_star_pilot_best_E": pilot_best, "E_star_pilot_walks": ttt_walks,
+                            "E_star_pilot_flips_per_walk": ttt_pilot_flips, "E_star_pilot_seconds_each": pilot_s,
+                            "F_star": F_star, "E_star": E_star}
+    log("preregistered %s" % out["preregistered"])
     # equal-budget comparison on fresh seeds
     seeds = [1000 + i for i in range(n_seeds)]
     plain = [best_energies(L, p, prefixes, eval_walks, eval_flips, s, device=device)[0] for s in seeds]
@@ -145,6 +161,7 @@ def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=81
     # seed whose walks never reach E* counts as slower than every seed that does)
     ttt = {}
     ttt_seed_list = [2000 + i for i in range(ttt_seeds)]
+    ttt_flips = ttt_budget_factor * ttt_pilot_flips
     for name, pp, ll in (("plain", None, 0.0), ("learned", pol, lam)):
         hits, totals = [], []
         for sd in ttt_seed_list:
