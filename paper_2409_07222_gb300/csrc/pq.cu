@@ -236,6 +236,7 @@ __device__ __forceinline__ void block_min(int* dst, int v) {
 // bin of the warp (every lane calls it): the energies of a round crowd into few bins, and same-address
 // atomics from every thread would serialise there.
 __device__ __forceinline__ void hist_add(unsigned* fine, unsigned* coarse, int bin, int delta) {
+  if (!__any_sync(kFull, bin >= 0)) return;  // most warps of a pass change nothing
   const unsigned lt = (1u << lane_id()) - 1u;
   const unsigned pf = __match_any_sync(kFull, bin);
   if (bin >= 0 && (pf & lt) == 0) atomicAdd(&fine[bin], (unsigned)(delta * __popc(pf)));
@@ -425,41 +426,56 @@ __global__ void __launch_bounds__(kSelThreads) pq_select_kernel(PqBufs b) {
 }
 
 // Pass over the pool (U = false) or the survivors (U = true): POP gathers the pool entries below the
-// boundary bin (popped) and those in it (candidates); the cut gathers the boundary bin's entries.
+// boundary bin (popped) and those in it (candidates); the cut gathers the boundary bin's entries.  Each
+// thread takes four consecutive entries with one 16-byte load of their energies (the pool and the dense
+// arrays are 256-byte aligned, their sizes rounded to whole quads by the workspace layout).
 template <bool POP, bool U>
 __global__ void __launch_bounds__(256) pq_gather_kernel(PqBufs b) {
   PqState* st = b.st;
   if (POP ? st->b == 0 : st->sel_need <= 0) return;
   const int sel = st->sel_bin, Eb = st->E_base;
   const long long n = U ? st->n_dense : b.cap;
+  const long long nq = (n + 3) >> 2;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
-    int bin = kNB;
-    int E = INT32_MAX;
-    if (i < n) {
-      E = U ? (b.uRep[i] != ~0u ? b.dE[i] : INT32_MAX) : b.pE[i];
-      if (E != INT32_MAX) bin = e_bin(E, Eb);
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nq; base += stride) {
+    const long long qd = base + threadIdx.x;
+    int4 e4 = make_int4(INT32_MAX, INT32_MAX, INT32_MAX, INT32_MAX);
+    uint4 r4 = make_uint4(0u, 0u, 0u, 0u);
+    if (qd < nq) {
+      e4 = reinterpret_cast<const int4*>(U ? b.dE : b.pE)[qd];
+      if (U) r4 = reinterpret_cast<const uint4*>(b.uRep)[qd];
     }
-    // the histogram bounds both counts (b entries below the boundary bin at most); a count beyond a
-    // buffer can only come from an inconsistent state, which is reported instead of written
-    if (POP) {
-      const long long o = warp_append(&st->pop_cnt, bin < sel);
-      if (o >= b.B) {
-        st->error = 1;
-      } else if (o >= 0) {
-        b.popId[o] = (int32_t)i;
-        b.popE[o] = E;
-        b.popF[o] = b.pFp[i];
+    const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
+    const unsigned rv[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const long long i = 4 * qd + e;
+      int bin = kNB;
+      int E = INT32_MAX;
+      if (i < n) {
+        E = U ? (rv[e] != ~0u ? ev[e] : INT32_MAX) : ev[e];
+        if (E != INT32_MAX) bin = e_bin(E, Eb);
       }
-    }
-    const long long o2 = warp_append(&st->cand_cnt, bin == sel);
-    if (o2 >= b.cand_cap) {
-      st->error = 1;
-    } else if (o2 >= 0) {
-      b.candId[o2] = U ? -(int32_t)i - 1 : (int32_t)i;
-      b.cE[o2] = E;
-      b.cF[o2] = U ? b.dFp[i] : b.pFp[i];
+      // the histogram bounds both counts (b entries below the boundary bin at most); a count beyond a
+      // buffer can only come from an inconsistent state, which is reported instead of written
+      if (POP) {
+        const long long o = warp_append(&st->pop_cnt, bin < sel);
+        if (o >= b.B) {
+          st->error = 1;
+        } else if (o >= 0) {
+          b.popId[o] = (int32_t)i;
+          b.popE[o] = E;
+          b.popF[o] = b.pFp[i];
+        }
+      }
+      const long long o2 = warp_append(&st->cand_cnt, bin == sel);
+      if (o2 >= b.cand_cap) {
+        st->error = 1;
+      } else if (o2 >= 0) {
+        b.candId[o2] = U ? -(int32_t)i - 1 : (int32_t)i;
+        b.cE[o2] = E;
+        b.cF[o2] = U ? b.dFp[i] : b.pFp[i];
+      }
     }
   }
 }
@@ -467,9 +483,9 @@ __global__ void __launch_bounds__(256) pq_gather_kernel(PqBufs b) {
 // One block: the sel_need smallest (E, fp) keys among the boundary candidates, by a most-significant-
 // digit-first radix select over the 96-bit key (four energy bytes, then eight fingerprint bytes; the
 // energy bytes are skipped when the boundary bin holds one energy, i.e. it is not clamped); keys are
-// distinct, so exactly sel_need candidates are <= the selected key.  The candidates' keys are read
-// from the contiguous gather arrays, staged in shared memory when they fit.  POP appends the selected
-// candidates to the pops.
+// distinct, so exactly sel_need candidates are <= the selected key.  The candidates are streamed from the
+// gather arrays until those that match the digits fixed so far fit in shared memory; they are staged
+// there and the remaining digits rank only them.  POP appends the selected candidates to the pops.
 constexpr int kCandSmem = 8192;  // candidates staged in shared memory (12 B each)
 template <bool POP>
 __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
@@ -481,91 +497,56 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   int* sE = reinterpret_cast<int*>(sm_cand + kCandSmem);
   __shared__ unsigned hist[256];
   __shared__ unsigned long long s_pre_e, s_pre_f;  // the digits fixed so far
-  __shared__ long long s_k;
-  __shared__ int s_nw, s_ok;
-  __shared__ unsigned long long s_below;
+  __shared__ long long s_k, s_match;               // rank still to find; candidates matching the digits
+  __shared__ int s_ns;                             // candidates staged
   const int t = threadIdx.x;
   const bool one_energy = st->sel_bin > 0 && st->sel_bin < kNB - 1;
-  bool staged = n <= kCandSmem;
-  long long nsel = n;  // entries the radix select ranks (all candidates, or the window)
   if (t == 0) {
     s_pre_e = one_energy ? (unsigned long long)(uint32_t)(st->E_base + st->sel_bin) : 0ull;
     s_pre_f = 0;
     s_k = st->sel_need;
-    s_nw = 0;
-    s_ok = 0;
-    s_below = 0;
+    s_match = n;
+    s_ns = 0;
   }
   __syncthreads();
-  if (staged) {
-    for (long long i = t; i < n; i += kSelThreads) {
-      sF[i] = b.cF[i];
-      sE[i] = b.cE[i];
-    }
-  } else if (one_energy) {
-    // Many candidates, one energy: their fingerprints are uniform 64-bit values, so the k-th smallest
-    // lies near k/n of the range.  One pass counts the candidates below a window around that point and
-    // stages the window's candidates; when the k-th smallest falls inside it, the select ranks only the
-    // window (else it falls back to ranking every candidate).
-    const double k = (double)s_k, delta = 4.0 * sqrt(k) + 64.0;
-    const double flo = fmax(0.0, (k - delta) / (double)n), fhi = (k + delta) / (double)n;
-    const uint64_t lo = flo <= 0.0 ? 0ull : (uint64_t)(flo * 18446744073709549568.0);
-    const uint64_t hi = fhi >= 1.0 ? ~0ull : (uint64_t)(fhi * 18446744073709549568.0);
-    unsigned long long below = 0;
-    for (long long i = t; i < n; i += kSelThreads) {
-      const uint64_t fp = b.cF[i];
-      if (fp < lo) {
-        below++;
-      } else if (fp <= hi) {
-        const int w = atomicAdd(&s_nw, 1);
-        if (w < kCandSmem) {
-          sF[w] = fp;
-          sE[w] = b.cE[i];
+  bool staged = false;
+  const int d0 = one_energy ? 4 : 0;
+  for (int d = d0; d < 12; d++) {
+    const unsigned long long pe = s_pre_e, pf = s_pre_f;
+    // does key (ue, fp) match the digits fixed before digit d?
+    auto match = [&](uint64_t ue, uint64_t fp) {
+      if (d < 4) return d == 0 || (ue >> (32 - 8 * d)) == (pe >> (32 - 8 * d));
+      return ue == pe && (d == 4 || (fp >> (64 - 8 * (d - 4))) == (pf >> (64 - 8 * (d - 4))));
+    };
+    if (!staged && s_match <= kCandSmem) {  // stage the matching candidates
+      for (long long i = t; i < n; i += kSelThreads) {
+        const uint64_t ue = (uint32_t)b.cE[i], fp = b.cF[i];
+        if (d == d0 || match(ue, fp)) {
+          const int w = atomicAdd(&s_ns, 1);
+          if (w < kCandSmem) {
+            sF[w] = fp;
+            sE[w] = (int)(uint32_t)ue;
+          }
         }
       }
-    }
-    atomicAdd(&s_below, below);
-    __syncthreads();
-    if (t == 0) {
-      const long long kk = s_k;
-      if (s_nw <= kCandSmem && (long long)s_below < kk && kk <= (long long)s_below + s_nw) {
-        s_ok = 1;
-        s_k = kk - (long long)s_below;
-      }
-    }
-    __syncthreads();
-    if (s_ok) {
       staged = true;
-      nsel = s_nw;
+      __syncthreads();
     }
-  }
-  __syncthreads();
-  const uint64_t* F = staged ? sF : b.cF;
-  const int* Ev = staged ? sE : b.cE;
-  for (int d = one_energy ? 4 : 0; d < 12; d++) {
     if (t < 256) hist[t] = 0;
     __syncthreads();
-    const unsigned long long pe = s_pre_e, pf = s_pre_f;
+    const long long nsel = staged ? min((long long)s_ns, (long long)kCandSmem) : n;
     for (long long i = t; i < nsel; i += kSelThreads) {
-      const uint64_t ue = (uint32_t)Ev[i];
-      const uint64_t fp = F[i];
-      bool match;
-      unsigned digit;
-      if (d < 4) {
-        const int sh = 24 - 8 * d;
-        match = d == 0 || (ue >> (sh + 8)) == (pe >> (sh + 8));
-        digit = (unsigned)(ue >> sh) & 255u;
-      } else {
-        const int sh = 56 - 8 * (d - 4);
-        match = ue == pe && (d == 4 || (fp >> (sh + 8)) == (pf >> (sh + 8)));
-        digit = (unsigned)(fp >> sh) & 255u;
+      const uint64_t ue = (uint32_t)(staged ? sE[i] : b.cE[i]);
+      const uint64_t fp = staged ? sF[i] : b.cF[i];
+      if (d == d0 || match(ue, fp)) {
+        const unsigned digit = d < 4 ? (unsigned)(ue >> (24 - 8 * d)) & 255u : (unsigned)(fp >> (56 - 8 * (d - 4))) & 255u;
+        atomicAdd(&hist[digit], 1u);
       }
-      if (match) atomicAdd(&hist[digit], 1u);
     }
     __syncthreads();
     // the digit where the count reaches k: an inclusive scan of the 256 bins, then the one bin that
     // crosses k
-    unsigned c = t < 256 ? hist[t] : 0u;
+    unsigned own = t < 256 ? hist[t] : 0u, c = own;
     for (int off = 1; off < 256; off <<= 1) {
       const unsigned v = (t < 256 && t >= off) ? hist[t - off] : 0u;
       __syncthreads();
@@ -577,6 +558,7 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
       const long long before = t ? hist[t - 1] : 0;
       if (before < k && (long long)c >= k) {
         s_k = k - before;
+        s_match = own;
         if (d < 4)
           s_pre_e = pe | ((unsigned long long)t << (24 - 8 * d));
         else
@@ -590,6 +572,7 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   if (t == 0) {
     st->sel_E = selE;
     st->sel_fp = selF;
+    if (s_ns > kCandSmem) st->error = 1;  // cannot happen: at most s_match <= kCandSmem are staged
   }
   if (POP) {
     for (long long i = t; i < n; i += kSelThreads) {
@@ -923,30 +906,37 @@ __device__ __forceinline__ bool below_cut(const PqState* st, int bin, int E, uin
   return bin < st->sel_bin || (bin == st->sel_bin && key_le(E, fp, st->sel_E, st->sel_fp));
 }
 
-// Pool pass: the entries beyond the cut are evicted (slot freed, histogram updated).
+// Pool pass: the entries beyond the cut are evicted (slot freed, histogram updated); four slots per
+// thread, their energies in one 16-byte load.
 __global__ void __launch_bounds__(256) pq_evict_kernel(PqBufs b) {
   PqState* st = b.st;
   if (st->sel_need < 0) return;
   const int Eb = st->E_base;
+  const long long nq = (b.cap + 3) >> 2;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.cap; base += stride) {
-    const long long i = base + threadIdx.x;
-    bool out = false;
-    int bin = 0;
-    if (i < b.cap) {
-      const int E = b.pE[i];
-      if (E != INT32_MAX) {
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nq; base += stride) {
+    const long long qd = base + threadIdx.x;
+    int4 e4 = make_int4(INT32_MAX, INT32_MAX, INT32_MAX, INT32_MAX);
+    if (qd < nq) e4 = reinterpret_cast<const int4*>(b.pE)[qd];
+    const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const long long i = 4 * qd + e;
+      bool out = false;
+      int bin = 0;
+      const int E = ev[e];
+      if (i < b.cap && E != INT32_MAX) {
         bin = e_bin(E, Eb);
-        out = !below_cut(st, bin, E, b.pFp[i]);
+        out = bin > st->sel_bin || (bin == st->sel_bin && !key_le(E, b.pFp[i], st->sel_E, st->sel_fp));
       }
+      const long long o = warp_append(&st->free_top, out);
+      if (out) {
+        b.freeIds[o] = (int32_t)i;
+        b.pE[i] = INT32_MAX;
+      }
+      hist_add(b.hP, b.hP2, out ? bin : -1, -1);
+      warp_add(&st->ev_round, out ? 1 : 0);
     }
-    const long long o = warp_append(&st->free_top, out);
-    if (out) {
-      b.freeIds[o] = (int32_t)i;
-      b.pE[i] = INT32_MAX;
-    }
-    hist_add(b.hP, b.hP2, out ? bin : -1, -1);
-    warp_add(&st->ev_round, out ? 1 : 0);
   }
 }
 
@@ -1062,16 +1052,16 @@ int launch_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seed
     off += (bytes + 255) & ~size_t(255);
     return o;
   };
-  const size_t opE = take(4 * cap), opF = take(8 * cap), opS = take(8 * cap * W), ofree = take(4 * cap);
+  const size_t opE = take(4 * ((cap + 3) & ~3ll)), opF = take(8 * cap), opS = take(8 * cap * W), ofree = take(4 * cap);
   const size_t ohP = take(4 * kNB), ohP2 = take(4 * kNC), ohU = take(4 * kNB), ohU2 = take(4 * kNC);
   const size_t opop = take(4 * (size_t)cfg->B), opivE = take(4 * (size_t)cfg->B), opivF = take(8 * (size_t)cfg->B);
   const size_t opopE = take(4 * (size_t)cfg->B), opopF = take(8 * (size_t)cfg->B);
   const size_t opivS = take(8 * (size_t)cfg->B * W);
   const size_t ocand = take(4 * (size_t)(cap + n_dense)), ocE = take(4 * (size_t)(cap + n_dense));
   const size_t ocF = take(8 * (size_t)(cap + n_dense)), orank = take(4 * (size_t)cfg->B);
-  const size_t odE = take(4 * n_dense), odF = take(8 * n_dense);
+  const size_t odE = take(4 * ((n_dense + 3) & ~3ll)), odF = take(8 * n_dense);
   const size_t ohk = take(8ull << hs_log2), ohv = take(4ull << hs_log2);
-  const size_t ouR = take(4 * n_dense);
+  const size_t ouR = take(4 * ((n_dense + 3) & ~3ll));
   const size_t ozt = take(8 * L), ost = take(sizeof(PqState)), obest = take(8 * W);
   const size_t oH = take(8ull << cfg->H_log2);
   char* base = static_cast<char*>(ws_get(ctx, kWsPq0, off));
