@@ -49,12 +49,13 @@ def parse():
     ap.add_argument("--cpu-walks", type=int, default=64)
     ap.add_argument("--cpu-flips", type=int, default=6000)
     ap.add_argument("--workload", default="step1", choices=["step1", "mixed", "pq", "pq_indep", "learned", "network", "operators", "legendre",
-                             "exhaustive", "energy", "deltas", "peaks"],
+                             "exhaustive", "energy", "deltas", "peaks", "workflow"],
                     help="step1: L=451 walks (the headline); mixed: all lengths 450..527 in one batched launch; "
                          "pq: step-2 refinement from step-1 candidates; learned: the learned-proposal experiment; "
                          "network: the proposal network's inference alone; operators: the end-element operators; "
                          "legendre: Legendre seeds for step 2 (Table 2 lengths); pq_indep: step 2 with one queue per candidate; exhaustive: all skew sequences of L = 37 and 61; energy / deltas: the energy batch and the "
-                         "neighbour scan entry points alone")
+                         "neighbour scan entry points alone; workflow: Fig. 4 end to end (step 1 -> sieve -> step 2 -> "
+                         "operators -> step 2 at L +- 1)")
     ap.add_argument("--L", type=int, default=451, help="pq workload: sequence length")
     ap.add_argument("--pq-expansions", type=int, default=inp.STEP2["max_expansions"])
     ap.add_argument("--pq-hlog2", type=int, default=28)
@@ -62,6 +63,9 @@ def parse():
     ap.add_argument("--pq-indep-pops", type=int, default=500, help="pq_indep workload: pops per candidate")
     ap.add_argument("--pq-indep-hlog2", type=int, default=20,
                     help="pq_indep workload: log2 of each candidate's visited-set slots")
+    ap.add_argument("--wf-flips", type=int, default=10000, help="workflow workload: flips per step-1 walk")
+    ap.add_argument("--wf-op-expansions", type=int, default=10**6,
+                    help="workflow workload: step-2 expansions at L + 1 and L - 1")
     return ap.parse_args()
 
 
@@ -314,6 +318,58 @@ def run_pq(args, ws, rank, local):
             "roofline": {"bound": "alu", "achieved": terms / t / 1e9, "peak": peak, "unit": "Gop/s",
                          "frac": terms / t / 1e9 / peak, "traffic": None,
                          "work": "per expansion L(L-1) neighbour-lag multiply-adds (whole step timed, host-driven)"}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_workflow(args, ws, rank, local):
+    """Fig. 4 end to end at L = 451 (workflow.two_step_search): step 1 over the step-1 workload's walks
+    (65,536 per GPU, p = 24, sieve bound from 10^6 samples) with --wf-flips flips each, the 4,096 best
+    distinct candidates, step 2 at L (B = 4,096, open set 2^22), the end-element operators, step 2 at
+    L + 1 and L - 1.  Each rank runs its own walks (walk_begin = rank x walks); rank 0 merges the
+    candidates and runs the step-2 stages.  Timed on the host clock around whole workflow passes."""
+    import torch
+
+    import paper_2409_07222_gb300 as lg
+    from paper_2409_07222_gb300 import workflow
+
+    torch.cuda.set_device(local)
+    lg.load()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    L, p = 451, W1["p"]
+    pre_h = inp.distinct_prefixes(W1["n_prefix"], p, seed=W1["prefix_seed"])
+    S2 = inp.STEP2
+    times, res = [], None
+    for it in range(max(1, args.warmup) + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = workflow.two_step_search(L, pre_h, p=p, n_walks=args.walks, flip_budget=args.wf_flips, seed=W1["seed"],
+                                       R=W1["R"], n_thresh_samples=W1["n_thresh_samples"],
+                                       thresh_rank=W1["thresh_rank"], walk_begin=rank * args.walks,
+                                       K=S2["n_seeds"], B=S2["B"], cap=S2["cap"], H_log2=args.pq_hlog2,
+                                       max_expansions=args.pq_expansions, op_max_expansions=args.wf_op_expansions)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    if rank != 0:
+        return 0
+    t = statistics.mean(times[-args.steps:])
+    stages = {str(Ln): {"E": res[Ln]["E"], "F": round(res[Ln]["F"], 4), "seconds": round(res[Ln]["seconds"], 4),
+                        "expansions": res[Ln]["stats"]["expansions"], "improvements": res[Ln]["stats"]["improvements"],
+                        "hex": res[Ln]["hex"]} for Ln in (L, L + 1, L - 1)}
+    s1 = res["step1"]
+    line = {"metric": "workflow seconds", "value": t, "unit": "s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": t * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "fig4_workflow_L451_p24_%dwalks_x%dflips_step2_%d_ops_%d" % (
+                           args.walks * ws, args.wf_flips, args.pq_expansions, args.wf_op_expansions),
+                       "L": L, "walks_per_gpu": args.walks, "flips_per_walk": args.wf_flips,
+                       "seeds": s1["candidates"], "E_thr": s1["E_thr"], "max_expansions": args.pq_expansions,
+                       "op_max_expansions": args.wf_op_expansions, "timing": "host clock, whole workflow"},
+            "step1": {"seconds": round(s1["seconds"], 4), "flips": s1["flips"], "best_E": s1["best_E"]},
+            "operators": res["operators"], "stages": stages}
     print(json.dumps(line))
     return 0
 
@@ -751,6 +807,8 @@ def main():
         return run_learned(args, ws, rank, local)
     if args.workload == "peaks":
         return run_peaks(args, ws, rank, local)
+    if args.workload == "workflow":
+        return run_workflow(args, ws, rank, local)
 
     import torch
 
