@@ -132,7 +132,7 @@ int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* pr
   if (cfg->flip_budget > 0xffffffffLL) return LABS_ERR_INVALID_ARG;               // steps are stored as u32
   if (cfg->tile_m != 0 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16)
     return LABS_ERR_INVALID_ARG;
-  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 13) return LABS_ERR_INVALID_ARG;
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 12) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk != 0 && cfg->lanes_per_walk != 16 && cfg->lanes_per_walk != 32) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk == 32 && cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk == 16 && cfg->R > 16) return LABS_ERR_INVALID_ARG;
@@ -191,7 +191,7 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
     return LABS_ERR_INVALID_ARG;
   if (cfg->walk_begin + cfg->n_walks > 0xffffffffLL || cfg->flip_budget > 0x7fffffffLL) return LABS_ERR_INVALID_ARG;
   if (cfg->tile_m != 0 && cfg->tile_m != 8 && cfg->tile_m != 12 && cfg->tile_m != 16) return LABS_ERR_INVALID_ARG;
-  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 13) return LABS_ERR_INVALID_ARG;
+  if (cfg->warps_per_cta < 0 || cfg->warps_per_cta > 12) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk != 0 && cfg->lanes_per_walk != 16 && cfg->lanes_per_walk != 32) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk == 32 && cfg->warps_per_cta > 8) return LABS_ERR_INVALID_ARG;
   if (cfg->lanes_per_walk == 16 && cfg->R > 16) return LABS_ERR_INVALID_ARG;

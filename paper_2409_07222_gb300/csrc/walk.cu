@@ -909,8 +909,9 @@ static bool fill_params(WalkParams& P, const std::vector<LenSpec>& lens, const V
 }
 
 // Heuristic choice: least total per-warp scan work, sum(walks * NP * M / H * GL / 32) (a half-warp walk
-// shares its warp's instructions with another walk); ties to fewer lane passes (each pass repeats the
-// per-slot phases), then to more lanes per tile, then the larger tile.
+// shares its warp's instructions with another walk); ties to fewer lanes per walk (the two walks of a
+// warp then share every instruction of the serial phases), then to fewer lane passes (each pass repeats
+// the per-slot phases), then to more lanes per tile, then the larger tile.
 // req_m / req_gl: 0 or the tile size / lanes per walk the caller fixed; R: sieve slots per walk.
 static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, int req_gl, int R, Variant* out) {
   bool found = false;
@@ -934,9 +935,11 @@ static bool choose_variant(const std::vector<LenSpec>& lens, int req_m, int req_
       cost += (long double)std::max<int64_t>(s.walks, 1) * np * v.M / v.H * v.GL / 32;
     }
     if (!ok) continue;
-    const bool better = !found || cost < best_cost ||
-                        (cost == best_cost && (max_np < best_np || (max_np == best_np && (v.H > best.H ||
-                                                                    (v.H == best.H && v.M > best.M)))));
+    const bool better =
+        !found || cost < best_cost ||
+        (cost == best_cost &&
+         (v.GL < best.GL ||
+          (v.GL == best.GL && (max_np < best_np || (max_np == best_np && (v.H > best.H || (v.H == best.H && v.M > best.M)))))));
     if (better) {
       best = v;
       best_cost = cost;
