@@ -4,13 +4,14 @@
 // GB300 mapping.  The paper runs one priority queue per candidate in Rust on CPU cores; here one open
 // set of the cap smallest (E, fp) keys lives in HBM as an UNORDERED pool of entries (energy,
 // fingerprint, sequence) with a free-slot stack, and beside it a histogram of the entries' energies
-// (one bin per energy, clamped at both ends of a 2^17-bin window, and a coarse level of 256 bins per
-// entry).  The B smallest keys, or the cap smallest, are then found without ordering the pool: the
+// (one bin per energy, clamped at both ends of a 2^17-bin window, and a coarse level whose bins each
+// cover 256 fine bins).  The B smallest keys, or the cap smallest, are then found without ordering the pool: the
 // histogram's prefix sums give the bin where the count is reached, every entry below it is taken, and
 // only the entries of that one boundary bin are ranked (a radix select on their full (E, fp) key, so a
 // clamped bin holding several energies is still exact).  A round
 //   pop      -- the b = min(B, open, budget left) smallest keys leave the pool (one pass over it), are
-//               put in key order (one block) and become the round's pivots;
+//               ranked among themselves (a 2-D grid counts, for each, the smaller keys) and become the
+//               round's pivots in key order;
 //   expand   -- one warp per pivot: its correlation table, the all-position dp4a scan and a visited-set
 //               lookup per neighbour, written to a dense [pivot][column] survivor array;
 //   dedup    -- survivors with equal (E', fp') (the same sequence) are kept once, through a hash table;

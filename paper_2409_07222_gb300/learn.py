@@ -11,8 +11,8 @@ that ended well (advantage-weighted cross-entropy over the free positions).
 import numpy as np
 import torch
 
-from . import (INT32_MAX, Policy, candidates_numpy, labs_chunked_search, make_walk_cfg, stats_numpy,
-               words_per_seq)
+from . import (INT32_MAX, Policy, candidates_numpy, labs_chunked_search, labs_skew_search, make_walk_cfg,
+               stats_numpy, words_per_seq)
 
 
 def free_range(L, p):
@@ -70,41 +70,48 @@ def rank_sum(a, b):
     return float(r.statistic), float(r.pvalue)
 
 
-def _time_to_target(L, p, prefixes, n_walks, flip_budget, seed, E_star, policy, lam, chunk, cap_s, device=None):
-    """Seconds until some walk first reaches E <= E_star: the whole chunked run is timed with CUDA events and
-    the time to the chunk holding the earliest first hit (per-walk first-hit flip counts) is that share of
-    it (every chunk does the same work); None if no walk reaches E_star within the budget."""
+def _time_to_target(L, p, prefixes, n_walks, flip_budget, seed, E_star, policy, lam, chunk, device=None):
+    """Seconds until some walk first reaches E <= E_star, or None if none does within the budget, and the
+    whole run's seconds (CUDA events).  Plain walks (policy None) run as one labs_skew_search launch and
+    the hit time is the run's share up to the earliest first-hit flip count (every flip costs the same);
+    learned walks run in chunks of `chunk` flips, each scored by the network first, and the hit time is
+    the share of the chunks up to the one holding the earliest first hit (every chunk costs the same)."""
+    cfg = make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n_walks, flip_budget=flip_budget, seed=seed, R=4,
+                        E_thr=INT32_MAX, E_target=E_star)
     t0 = torch.cuda.Event(enable_timing=True)
     t0.record()
-    res = labs_chunked_search(make_walk_cfg(L, skew=L % 2 == 1, p=p, n_walks=n_walks, flip_budget=flip_budget,
-                                            seed=seed, R=4, E_thr=INT32_MAX, E_target=E_star),
-                              prefixes, policy=policy, lam=lam, chunk=chunk, device=device)
+    if policy is None:
+        _, ws, _ = labs_skew_search(cfg, prefixes, device=device)
+    else:
+        ws = labs_chunked_search(cfg, prefixes, policy=policy, lam=lam, chunk=chunk, device=device)["walk_stats"]
     t1 = torch.cuda.Event(enable_timing=True)
     t1.record()
     torch.cuda.synchronize()
     total_s = t0.elapsed_time(t1) * 1e-3
-    hit = res["walk_stats"][:, 5]
+    hit = ws[:, 5]
     reached = hit[hit >= 0]
     if reached.numel() == 0:
         return None, total_s
-    # the first hit happens within the chunk containing the smallest first-hit flip count; time scales
-    # with the chunks run (each chunk costs the same), so interpolate on the chunk index
     first_flip = int(reached.min())
+    if policy is None:
+        return total_s * first_flip / flip_budget, total_s
     n_chunks = (flip_budget + chunk - 1) // chunk
     return total_s * ((first_flip + chunk - 1) // chunk) / n_chunks, total_s
 
 
 def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=8192, train_steps=3000, batch=512,
                lr=1e-3, lambdas=(5.0, 20.0, 80.0), eval_walks=256, eval_flips=8192, n_seeds=30, ttt_walks=8192,
-               ttt_pilot_flips=1 << 18, ttt_pilot_seeds=5, ttt_budget_factor=2, ttt_seeds=10, chunk=64, device=None,
-               log=print):
+               ttt_pilot_flips=1 << 18, ttt_pilot_seeds=5, ttt_budget_factor=2, ttt_seeds=10, chunk=64,
+               ttt_chunks=(256, 64), device=None, log=print):
     """Collect tuples from plain walks, train the network, pick lambda on pilot seeds, then compare learned
     vs plain at an equal flip budget on fresh seeds (rank-sum) and time both to a pre-registered E*.
 
     E* for the timing comes from a plain pilot of the timed shape itself: ttt_walks walks of ttt_pilot_flips
     flips (seconds of plain search), median best F over ttt_pilot_seeds seeds, E* = floor(L^2 / (2 F*)).
     Each timed run then gets ttt_budget_factor times the pilot's flips; a seed that never reaches E* counts
-    as slower than every seed that does."""
+    as slower than every seed that does.  The plain arm is the plain walk itself (one launch, no chunks);
+    the learned arm is timed once per inference interval in ttt_chunks (flips between network scorings),
+    the first of them pre-registered as the headline."""
     import time
 
     out = {}
@@ -162,18 +169,23 @@ def experiment(L=451, p=24, prefixes=None, collect_walks=16384, collect_flips=81
     ttt = {}
     ttt_seed_list = [2000 + i for i in range(ttt_seeds)]
     ttt_flips = ttt_budget_factor * ttt_pilot_flips
-    for name, pp, ll in (("plain", None, 0.0), ("learned", pol, lam)):
+    arms = [("plain", None, 0.0, 0)] + [("learned" if i == 0 else "learned_chunk%d" % c, pol, lam, c)
+                                         for i, c in enumerate(ttt_chunks)]
+    for name, pp, ll, ck in arms:
         hits, totals = [], []
         for sd in ttt_seed_list:
-            s_hit, s_total = _time_to_target(L, p, prefixes, ttt_walks, ttt_flips, sd, E_star, pp, ll, chunk, 0,
+            s_hit, s_total = _time_to_target(L, p, prefixes, ttt_walks, ttt_flips, sd, E_star, pp, ll, ck,
                                              device=device)
             hits.append(s_hit)
             totals.append(s_total)
         med = float(np.median([h if h is not None else float("inf") for h in hits]))
         ttt[name] = {"seconds_to_E_star": med if np.isfinite(med) else None, "per_seed_seconds_to_E_star": hits,
-                     "seconds_total_median": float(np.median(totals))}
+                     "seconds_total_median": float(np.median(totals)), "inference_every_flips": ck or None}
     out["time_to_target"] = dict(ttt, walks=ttt_walks, flips_per_walk=ttt_flips, E_star=E_star, seeds=ttt_seed_list)
-    p_s, l_s = ttt["plain"]["seconds_to_E_star"], ttt["learned"]["seconds_to_E_star"]
-    out["time_to_target"]["speedup_learned_vs_plain"] = (p_s / l_s) if (p_s and l_s) else None
+    p_s = ttt["plain"]["seconds_to_E_star"]
+    for name, _, _, _ in arms[1:]:
+        l_s = ttt[name]["seconds_to_E_star"]
+        key = "speedup_learned_vs_plain" if name == "learned" else "speedup_%s_vs_plain" % name
+        out["time_to_target"][key] = (p_s / l_s) if (p_s and l_s) else None
     log("time to target %s" % out["time_to_target"])
     return out
