@@ -408,7 +408,11 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
       }
       // ---- scan; each lane keeps its best (key, m) where key orders the choice: Delta E, or the
       //      biased score Delta E - lambda * logit[m] mapped to an order-preserving integer
+      // each lane keeps its two best (key, m): a Bloom hit on its best then hands over the second without
+      // a rescan of the lane's slots
       int bk = INT32_MAX, bm = INT32_MAX, bdE = 0;
+      int bk2 = INT32_MAX, bm2 = INT32_MAX, bd2 = 0;
+      bool have2 = true;
       int kprev = INT32_MAX;  // this lane's key of the move back (only its owner sets it)
       for (int ps = 0; ps < NP; ps++) {
         int cls, q0, h;
@@ -477,19 +481,37 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
           mv[k] = m;
           dv[k] = d;
         }
+        // the pass's two smallest (key, m): slots come in increasing m, so strict comparisons keep the
+        // smaller m ahead among equal keys
+        int p1 = INT32_MAX, q1 = INT32_MAX, e1 = 0, p2 = INT32_MAX, q2 = INT32_MAX, e2 = 0;
 #pragma unroll
-        for (int st = 1; st < MH; st *= 2)
-#pragma unroll
-          for (int k = 0; k + st < MH; k += 2 * st)
-            if (kv[k + st] < kv[k]) {
-              kv[k] = kv[k + st];
-              mv[k] = mv[k + st];
-              if (BIASED) dv[k] = dv[k + st];
-            }
-        if (kv[0] < bk || (kv[0] == bk && kv[0] != INT32_MAX && mv[0] < bm)) {
-          bk = kv[0];
-          bm = mv[0];
-          bdE = BIASED ? dv[0] : kv[0];
+        for (int k = 0; k < MH; k++) {
+          const bool lt1 = kv[k] < p1, lt2 = kv[k] < p2;
+          p2 = lt1 ? p1 : (lt2 ? kv[k] : p2);
+          q2 = lt1 ? q1 : (lt2 ? mv[k] : q2);
+          if (BIASED) e2 = lt1 ? e1 : (lt2 ? dv[k] : e2);
+          p1 = lt1 ? kv[k] : p1;
+          q1 = lt1 ? mv[k] : q1;
+          if (BIASED) e1 = lt1 ? dv[k] : e1;
+        }
+        if (!BIASED) {
+          e1 = p1;
+          e2 = p2;
+        }
+        // merge with the earlier passes' two (a later pass may hold smaller m only in another class)
+        auto before = [](int ka, int ma, int kb, int mb) { return ka < kb || (ka == kb && ka != INT32_MAX && ma < mb); };
+        if (before(p1, q1, bk, bm)) {
+          const bool sec = before(bk, bm, p2, q2);  // the old best stays second unless the pass's second is smaller
+          bk2 = sec ? bk : p2;
+          bm2 = sec ? bm : q2;
+          bd2 = sec ? bdE : e2;
+          bk = p1;
+          bm = q1;
+          bdE = e1;
+        } else if (before(p1, q1, bk2, bm2)) {
+          bk2 = p1;
+          bm2 = q1;
+          bd2 = e1;
         }
       }
       // ---- select: smallest (key, m) whose neighbour is not in the Bloom filter
@@ -529,7 +551,13 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
           break;
         }
         skips++;
-        if (mine) {
+        if (mine && have2) {
+          // the owner lane's next best is its second
+          bk = bk2;
+          bm = bm2;
+          bdE = bd2;
+          have2 = false;
+        } else if (mine) {
           // the owner lane's next best: smallest key ranked after (kmin, mm); keys ranked ahead were
           // dropped earlier in this step
           bk = INT32_MAX;
