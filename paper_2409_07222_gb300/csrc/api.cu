@@ -84,6 +84,7 @@ void labs_ctx_destroy(labs_ctx* ctx) {
 
 int labs_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int32_t* E_out, int32_t* C_out,
                       void* stream) {
+  LABS_TRACE("labs_energy_batch");
   if (!ctx || L < 2 || L > LABS_MAX_L || n < 0) return LABS_ERR_INVALID_ARG;
   if (n > 0 && (!seqs || !E_out || !aligned8(seqs) || !aligned4(E_out) || (C_out && !aligned4(C_out))))
     return LABS_ERR_INVALID_ARG;
@@ -94,6 +95,7 @@ int labs_energy_batch(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, int
 
 int labs_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int L, int64_t n, int skew, int p,
                      int32_t* dE_out, void* stream) {
+  LABS_TRACE("labs_flip_deltas");
   if (!ctx || L < 2 || L > LABS_MAX_L || n < 0 || (skew != 0 && skew != 1) || p < 0) return LABS_ERR_INVALID_ARG;
   if (skew && (L % 2 == 0 || L < 3 || p > (L - 1) / 2)) return LABS_ERR_INVALID_ARG;
   if (!skew && p >= L) return LABS_ERR_INVALID_ARG;
@@ -107,6 +109,7 @@ int labs_flip_deltas(labs_ctx* ctx, const uint64_t* seqs, const int32_t* C, int 
 int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t* prefixes, int n_prefix,
                           uint64_t seed, int64_t n_samples, int64_t rank, int32_t* E_thr_out, int32_t* E_samples,
                           void* stream) {
+  LABS_TRACE("labs_sample_threshold");
   if (!ctx) return LABS_ERR_INVALID_ARG;
   int s = labsg::check_walk_shape(L, skew, p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
@@ -122,6 +125,7 @@ int labs_sample_threshold(labs_ctx* ctx, int L, int skew, int p, const uint64_t*
 
 int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* prefixes, int n_prefix,
                      labs_candidate* out, int64_t* walk_stats, labs_walk_stats* stats, void* stream) {
+  LABS_TRACE("labs_skew_search");
   if (!ctx || !cfg) return LABS_ERR_INVALID_ARG;
   int s = labsg::check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
@@ -151,6 +155,7 @@ int labs_skew_search(labs_ctx* ctx, const labs_walk_cfg* cfg, const uint64_t* pr
 int labs_batched_search(labs_ctx* ctx, const labs_batch_cfg* cfg, const int32_t* lengths, const int64_t* walks,
                         const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
                         int32_t* E_thr_out, labs_walk_stats* stats, void* stream) {
+  LABS_TRACE("labs_batched_search");
   if (!ctx || !cfg || !lengths || !walks || cfg->n_len < 1 || cfg->n_len > 96) return LABS_ERR_INVALID_ARG;
   int64_t total = 0;
   int min_odd = LABS_MAX_L + 1;
@@ -183,6 +188,7 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
                         const uint64_t* prefixes, int n_prefix, labs_candidate* out, int64_t* walk_stats,
                         labs_walk_stats* stats, float* logits_log, uint64_t* state_log, int32_t* move_log,
                         void* stream) {
+  LABS_TRACE("labs_chunked_search");
   if (!ctx || !cfg || chunk < 1 || !(lambda == lambda)) return LABS_ERR_INVALID_ARG;
   int s = labsg::check_walk_shape(cfg->L, cfg->skew, cfg->p, n_prefix, prefixes);
   if (s != LABS_OK) return s;
@@ -209,6 +215,7 @@ int labs_chunked_search(labs_ctx* ctx, const labs_walk_cfg* cfg, labs_policy* po
 
 int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds, int n_seeds, uint64_t* best_seq,
                    int32_t* best_E, labs_pq_stats* stats, void* stream) {
+  LABS_TRACE("labs_pq_refine");
   if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->B < 1 || cfg->B > 8192 || cfg->cap < 1 ||
       cfg->cap > (1ll << 24) || cfg->H_log2 < 10 || cfg->H_log2 > 31 || cfg->T_r < 0 || cfg->T_r > 64 || 2 * cfg->T_r >= cfg->L || cfg->max_expansions < 0 ||
       n_seeds < 1)
@@ -223,6 +230,7 @@ int labs_pq_refine(labs_ctx* ctx, const labs_pq_cfg* cfg, const uint64_t* seeds,
 
 int labs_sequence_operators(labs_ctx* ctx, const uint64_t* seqs, int L, int64_t n, uint64_t* grow, int32_t* E_grow,
                             uint64_t* shrink, int32_t* E_shrink, void* stream) {
+  LABS_TRACE("labs_sequence_operators");
   if (!ctx || L < 3 || L > LABS_MAX_L - 1 || n < 0) return LABS_ERR_INVALID_ARG;
   if (n > 0 && (!seqs || !aligned8(seqs) || (grow && !aligned8(grow)) || (shrink && !aligned8(shrink)) ||
                 (E_grow && !aligned4(E_grow)) || (E_shrink && !aligned4(E_shrink))))
@@ -241,6 +249,7 @@ int labs_legendre_family(int L, double r_lo, double r_hi, double t_max, int32_t*
 
 int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t n, uint64_t* seqs, int32_t* E_out,
                             void* stream) {
+  LABS_TRACE("labs_legendre_construct");
   if (!ctx || L < 3 || L > LABS_MAX_L || n < 0) return LABS_ERR_INVALID_ARG;
   if (n > 0 && (!params || !aligned4(params) || (seqs && !aligned8(seqs)) || (E_out && !aligned4(E_out))))
     return LABS_ERR_INVALID_ARG;
@@ -251,6 +260,7 @@ int labs_legendre_construct(labs_ctx* ctx, int L, const int32_t* params, int64_t
 
 int labs_pq_independent(labs_ctx* ctx, const labs_pq_indep_cfg* cfg, const uint64_t* seeds, int n, uint64_t* best_seqs,
                         int32_t* best_E, labs_pq_stats* stats, void* stream) {
+  LABS_TRACE("labs_pq_independent");
   if (!ctx || !cfg || cfg->L < 2 || cfg->L > LABS_MAX_L || cfg->T_r < 0 || cfg->T_r > 64 || 2 * cfg->T_r >= cfg->L ||
       cfg->H_log2 < 10 || cfg->H_log2 > 30 || cfg->max_expansions < 1 || cfg->max_expansions >= (1ll << 21) ||
       cfg->max_workspace_bytes < 0 || n < 0)
@@ -311,6 +321,7 @@ int labs_hex_to_seq(const char* hex, int L, uint64_t* seq) {
 
 int labs_skew_exhaustive(labs_ctx* ctx, int L, int p, uint64_t prefix, int32_t* out_min_E, uint64_t* out_count,
                          uint64_t* out_argmin_free, uint64_t* out_argmin_seq, void* stream) {
+  LABS_TRACE("labs_skew_exhaustive");
   if (!ctx || L < 3 || L > 127 || L % 2 == 0 || p < 0 || p > (L - 1) / 2) return LABS_ERR_INVALID_ARG;
   if ((L - 1) / 2 - p + 1 > 40 || p > 64) return LABS_ERR_INVALID_ARG;
   if (!out_min_E || !out_count || !out_argmin_free || !out_argmin_seq || !aligned4(out_min_E) ||

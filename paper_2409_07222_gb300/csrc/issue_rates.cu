@@ -77,6 +77,7 @@ int run_probe(int sms, size_t smem, int niter, long long* d_cycles, uint32_t* d_
 }  // namespace labsg
 
 extern "C" int labs_measure_issue_rates(int device, double* rates, int n_rates) {
+  LABS_TRACE("labs_measure_issue_rates");
   using namespace labsg;
   if (!rates || n_rates < 9) return LABS_ERR_INVALID_ARG;
   int n = 0;

@@ -3,8 +3,20 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "labs.h"
+
+// An NVTX range named after a C-ABI entry point, open while the call runs on the host (its kernels show
+// under it in a profiler's timeline).  NVTX v3 is header-only; without an attached tool a range costs a
+// branch.
+struct LabsTraceRange {
+  explicit LabsTraceRange(const char* name) { nvtxRangePushA(name); }
+  ~LabsTraceRange() { nvtxRangePop(); }
+  LabsTraceRange(const LabsTraceRange&) = delete;
+  LabsTraceRange& operator=(const LabsTraceRange&) = delete;
+};
+#define LABS_TRACE(name) LabsTraceRange labs_trace_range_(name)
 
 constexpr int kMaxTuned = 16;
 

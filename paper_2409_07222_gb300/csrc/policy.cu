@@ -584,6 +584,7 @@ int labs_policy_get_params(labs_policy* P, float* params, void* stream) {
 }
 
 int labs_policy_forward(labs_policy* P, const uint64_t* seqs, int64_t n, float* logits, void* stream) {
+  LABS_TRACE("labs_policy_forward");
   if (!P || n < 0 || (n > 0 && (!seqs || !logits))) return LABS_ERR_INVALID_ARG;
   if (n == 0) return LABS_OK;
   cudaStream_t st = (cudaStream_t)stream;
@@ -598,6 +599,7 @@ int labs_policy_forward(labs_policy* P, const uint64_t* seqs, int64_t n, float* 
 
 int labs_policy_train_step(labs_policy* P, const uint64_t* seqs, const int32_t* target, const float* weight, int64_t n,
                            int free_lo, int free_hi, float lr, float* loss_out, float* grads_out, void* stream) {
+  LABS_TRACE("labs_policy_train_step");
   if (!P || n < 1 || !seqs || !target || !weight || free_lo < 0 || free_hi >= P->L || free_lo > free_hi)
     return LABS_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
