@@ -774,37 +774,58 @@ __global__ void __launch_bounds__(32 * kPqWarps) pq_expand_kernel(PqBufs b, Layo
 // Dedup, first pass: every survivor inserts its (E, fp) key; the first inserter of a key becomes the
 // key's unique survivor (marked in uRep, its representative settled by the second pass) and the table
 // slot points to its dense index.  Unique survivors stay at their dense index: nothing is compacted.
+// Each thread takes four consecutive survivors and keeps their four probes in flight together (the
+// pass is bound by the latency of the table's compare-and-swaps).
 template <bool SEED>
 __global__ void __launch_bounds__(256) pq_dedup_insert_kernel(PqBufs b) {
   PqState* st = b.st;
   const long long n = st->n_dense;
+  const long long nq = (n + 3) >> 2;
   const uint64_t mask = (1ull << b.hs_log2) - 1;
   const int Eb = st->E_base, pmax = st->pmax_bin;
   long long fresh_n = 0, low = 0;
   int mE = INT32_MAX;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int E = b.dE[i];
-    bool fresh = false;
-    if (E != INT32_MAX) {
-      const uint64_t k = dedup_key(E, b.dFp[i]);
-      uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
-      for (uint64_t it = 0; it <= mask; it++) {  // the table holds at most half its slots
-        const unsigned long long old = atomicCAS(reinterpret_cast<unsigned long long*>(&b.hkey[s]), 0ull, k);
-        if (old == 0ull) {
-          fresh = true;
-          b.hval[s] = (int32_t)i;
-          break;
+  for (long long qd = (long long)blockIdx.x * blockDim.x + threadIdx.x; qd < nq; qd += (long long)gridDim.x * blockDim.x) {
+    const int4 e4 = reinterpret_cast<const int4*>(b.dE)[qd];
+    const int E[4] = {e4.x, e4.y, e4.z, e4.w};
+    uint64_t k[4], s[4];
+    bool act[4], fresh[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long i = 4 * qd + j;
+      act[j] = i < n && E[j] != INT32_MAX;
+      fresh[j] = false;
+      k[j] = act[j] ? dedup_key(E[j], b.dFp[i]) : 0ull;
+      s[j] = (k[j] * kGamma) >> (64 - b.hs_log2);
+    }
+    for (uint64_t it = 0; it <= mask && (act[0] || act[1] || act[2] || act[3]); it++) {  // at most half full
+      unsigned long long old[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        old[j] = act[j] ? atomicCAS(reinterpret_cast<unsigned long long*>(&b.hkey[s[j]]), 0ull, k[j]) : 0ull;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        if (!act[j]) continue;
+        if (old[j] == 0ull) {
+          fresh[j] = true;
+          b.hval[s[j]] = (int32_t)(4 * qd + j);
+          act[j] = false;
+        } else if (old[j] == k[j]) {
+          act[j] = false;
+        } else {
+          s[j] = (s[j] + 1) & mask;
         }
-        if (old == k) break;
-        s = (s + 1) & mask;
       }
     }
-    b.uRep[i] = fresh ? 0xFFFFFFFEu : ~0u;
-    fresh_n += fresh ? 1 : 0;
-    if (fresh) {
-      mE = min(mE, E);
-      low += e_bin(E, Eb) <= pmax ? 1 : 0;
-    }
+    reinterpret_cast<uint4*>(b.uRep)[qd] = make_uint4(fresh[0] ? 0xFFFFFFFEu : ~0u, fresh[1] ? 0xFFFFFFFEu : ~0u,
+                                                       fresh[2] ? 0xFFFFFFFEu : ~0u, fresh[3] ? 0xFFFFFFFEu : ~0u);
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      if (fresh[j]) {
+        fresh_n++;
+        mE = min(mE, E[j]);
+        low += e_bin(E[j], Eb) <= pmax ? 1 : 0;
+      }
   }
   block_add(&st->nU, fresh_n);
   block_min(&st->minE_round, mE);
@@ -824,41 +845,72 @@ __device__ __forceinline__ int hist_mode_of(const PqState* st, long long cap) {
 // Dedup, second pass: each survivor finds its key's slot and lowers the representative of the key's
 // unique survivor to the smallest (pivot, column) -- the pivots are in key order, so this is the
 // sequential definition's first occurrence.  The unique survivors also enter the survivor histogram (the
-// bins the cut needs) and give the smallest fingerprint among the smallest-energy survivors.
+// bins the cut needs) and give the smallest fingerprint among the smallest-energy survivors.  Four
+// consecutive survivors per thread, their lookups in flight together.
 template <bool SEED>
 __global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b) {
   PqState* st = b.st;
   const long long n = st->n_dense;
+  const long long nq = (n + 3) >> 2;
   const uint64_t mask = (1ull << b.hs_log2) - 1;
   const int mode = hist_mode_of(st, b.cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->hist_mode = mode;
   const int Eb = st->E_base, pmax = st->pmax_bin, mE = st->minE_round;
   uint64_t mf = ~0ull;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long i = base + threadIdx.x;
-    int bin = -1;
-    if (i < n) {
-      const int E = b.dE[i];
-      if (E != INT32_MAX) {
-        const uint64_t fp = b.dFp[i];
-        const uint64_t k = dedup_key(E, fp);
-        uint64_t s = (k * kGamma) >> (64 - b.hs_log2);
-        for (uint64_t it = 0; it <= mask; it++) {
-          if (b.hkey[s] == k) break;
-          s = (s + 1) & mask;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nq; base += stride) {  // warp-uniform
+    const long long qd = base + threadIdx.x;
+    int E[4] = {INT32_MAX, INT32_MAX, INT32_MAX, INT32_MAX};
+    if (qd < nq) {
+      const int4 e4 = reinterpret_cast<const int4*>(b.dE)[qd];
+      E[0] = e4.x;
+      E[1] = e4.y;
+      E[2] = e4.z;
+      E[3] = e4.w;
+    }
+    uint64_t fp[4], k[4], s[4];
+    bool act[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long i = 4 * qd + j;
+      act[j] = qd < nq && i < n && E[j] != INT32_MAX;
+      fp[j] = act[j] ? b.dFp[i] : 0ull;
+      k[j] = dedup_key(E[j], fp[j]);
+      s[j] = (k[j] * kGamma) >> (64 - b.hs_log2);
+    }
+    bool look[4] = {act[0], act[1], act[2], act[3]};
+    for (uint64_t it = 0; it <= mask && (look[0] || look[1] || look[2] || look[3]); it++) {
+      uint64_t hk[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) hk[j] = look[j] ? b.hkey[s[j]] : 0ull;
+#pragma unroll
+      for (int j = 0; j < 4; j++)
+        if (look[j]) {
+          if (hk[j] == k[j])
+            look[j] = false;
+          else
+            s[j] = (s[j] + 1) & mask;
         }
+    }
+    int hv[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) hv[j] = act[j] ? b.hval[s[j]] : -1;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      int bin = -1;
+      if (act[j]) {
+        const long long i = 4 * qd + j;
         const unsigned rep = SEED ? (unsigned)i << kColBits
                                   : ((unsigned)(i / b.width) << kColBits) | (unsigned)(i % b.width);
-        atomicMin(&b.uRep[b.hval[s]], rep);
-        if (b.hval[s] == (int32_t)i) {  // the key's unique survivor
-          const int eb = e_bin(E, Eb);
+        atomicMin(&b.uRep[hv[j]], rep);
+        if (hv[j] == (int32_t)i) {  // the key's unique survivor
+          const int eb = e_bin(E[j], Eb);
           if (mode == 2 || (mode == 1 && eb <= pmax)) bin = eb;
-          if (E == mE) mf = min(mf, fp);
+          if (E[j] == mE) mf = min(mf, fp[j]);
         }
       }
+      if (mode) hist_add(b.hU, b.hU2, bin, 1);
     }
-    if (mode) hist_add(b.hU, b.hU2, bin, 1);
   }
   if (mf != ~0ull) atomicMin(reinterpret_cast<unsigned long long*>(&st->minfp_round), (unsigned long long)mf);
 }
@@ -948,56 +1000,75 @@ template <bool SEED>
 __global__ void __launch_bounds__(256) pq_admit_kernel(PqBufs b) {
   PqState* st = b.st;
   const long long n = st->n_dense;
+  const long long nq = (n + 3) >> 2;
   const int Eb = st->E_base;
+  const bool cut = st->sel_need >= 0;
+  const int sel_bin = st->sel_bin, minE = st->minE_round;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const long long u = base + threadIdx.x;
-    bool in = false;
-    int E = 0, bin = 0;
-    uint64_t fp = 0;
-    if (u < n && b.uRep[u] != ~0u) {
-      E = b.dE[u];
-      fp = b.dFp[u];
-      bin = e_bin(E, Eb);
-      in = below_cut(st, bin, E, fp);
-      if (E == st->minE_round && fp == st->minfp_round) st->best_rep_round = b.uRep[u];  // the smallest key
+  // four consecutive survivors per thread: their representatives and energies in one 16-byte load each;
+  // a fingerprint is read only where the cut or the best test needs it
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nq; base += stride) {  // warp-uniform
+    const long long qd = base + threadIdx.x;
+    uint4 r4 = make_uint4(~0u, ~0u, ~0u, ~0u);
+    int4 e4 = make_int4(INT32_MAX, INT32_MAX, INT32_MAX, INT32_MAX);
+    if (qd < nq) {
+      r4 = reinterpret_cast<const uint4*>(b.uRep)[qd];
+      e4 = reinterpret_cast<const int4*>(b.dE)[qd];
     }
-    // free slots come off the top of the stack, one atomic per warp
-    const unsigned m = __ballot_sync(kFull, in);
-    long long top = 0;
-    if (m) {
-      const int leader = __ffs(m) - 1;
-      if (lane_id() == leader)
-        top = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&st->free_top),
-                                   (unsigned long long)(-(long long)__popc(m)));
-      top = __shfl_sync(kFull, top, leader);
-    }
-    int ins = 0;
-    const long long o = top - 1 - __popc(m & ((1u << lane_id()) - 1u));
-    if (in && o < 0) {  // more admissions than free slots: only an inconsistent state gets here
-      st->error = 1;
-      in = false;
-    }
-    const unsigned rep = in ? b.uRep[u] : 0u;
-    if (in && (rep >> kColBits) >= (unsigned)(SEED ? b.n_seeds : st->b)) {  // every survivor has one (pass 2)
-      st->error = 1;
-      in = false;
-    }
-    if (in) {
-      const int id = b.freeIds[o];
-      b.pE[id] = E;
-      b.pFp[id] = fp;
-      if (SEED) {
-        for (int t = 0; t < b.W; t++) b.pSeq[(size_t)id * b.W + t] = b.seeds[(size_t)(rep >> kColBits) * b.W + t];
-      } else {
-        pq_child(b.pivSeq + (size_t)(rep >> kColBits) * b.W, b, (int)(rep & ((1u << kColBits) - 1u)),
-                 b.pSeq + (size_t)id * b.W);
+    const unsigned R[4] = {r4.x, r4.y, r4.z, r4.w};
+    const int Ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long u = 4 * qd + j;
+      bool in = false;
+      const int E = Ev[j];
+      int bin = 0;
+      uint64_t fp = 0;
+      if (u < n && R[j] != ~0u) {
+        bin = e_bin(E, Eb);
+        if (!cut || bin <= sel_bin || E == minE) {
+          fp = b.dFp[u];
+          in = below_cut(st, bin, E, fp);
+          if (E == minE && fp == st->minfp_round) st->best_rep_round = R[j];  // the smallest key
+        }
       }
-      ins = h_insert(b, fp);
+      // free slots come off the top of the stack, one atomic per warp
+      const unsigned m = __ballot_sync(kFull, in);
+      long long top = 0;
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        if (lane_id() == leader)
+          top = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&st->free_top),
+                                     (unsigned long long)(-(long long)__popc(m)));
+        top = __shfl_sync(kFull, top, leader);
+      }
+      int ins = 0;
+      const long long o = top - 1 - __popc(m & ((1u << lane_id()) - 1u));
+      if (in && o < 0) {  // more admissions than free slots: only an inconsistent state gets here
+        st->error = 1;
+        in = false;
+      }
+      const unsigned rep = in ? R[j] : 0u;
+      if (in && (rep >> kColBits) >= (unsigned)(SEED ? b.n_seeds : st->b)) {  // every survivor has one (pass 2)
+        st->error = 1;
+        in = false;
+      }
+      if (in) {
+        const int id = b.freeIds[o];
+        b.pE[id] = E;
+        b.pFp[id] = fp;
+        if (SEED) {
+          for (int t = 0; t < b.W; t++) b.pSeq[(size_t)id * b.W + t] = b.seeds[(size_t)(rep >> kColBits) * b.W + t];
+        } else {
+          pq_child(b.pivSeq + (size_t)(rep >> kColBits) * b.W, b, (int)(rep & ((1u << kColBits) - 1u)),
+                   b.pSeq + (size_t)id * b.W);
+        }
+        ins = h_insert(b, fp);
+      }
+      hist_add(b.hP, b.hP2, in ? bin : -1, 1);
+      h_count(b, ins);
+      warp_add(&st->adm_round, in ? 1 : 0);
     }
-    hist_add(b.hP, b.hP2, in ? bin : -1, 1);
-    h_count(b, ins);
-    warp_add(&st->adm_round, in ? 1 : 0);
   }
 }
 
