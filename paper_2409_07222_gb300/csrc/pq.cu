@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   uint64_t* sF = reinterpret_cast<uint64_t*>(sm_cand);
   int* sE = reinterpret_cast<int*>(sm_cand + kCandSmem);
   __shared__ unsigned hist[256];
+  __shared__ unsigned wsum[8];                     // bin-count totals of the eight warps' 32 bins
   __shared__ unsigned long long s_pre_e, s_pre_f;  // the digits fixed so far
   __shared__ long long s_k, s_match;               // rank still to find; candidates matching the digits
   __shared__ int s_ns;                             // candidates staged
@@ -513,7 +514,10 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
   bool staged = false;
   const int d0 = one_energy ? 4 : 0;
   for (int d = d0; d < 12; d++) {
+    // the shared selection state is read here, behind the previous iteration's last barrier: the thread
+    // of the crossing bin rewrites it below while the others still test their bins
     const unsigned long long pe = s_pre_e, pf = s_pre_f;
+    const long long k = s_k;
     // does key (ue, fp) match the digits fixed before digit d?
     auto match = [&](uint64_t ue, uint64_t fp) {
       if (d < 4) return d == 0 || (ue >> (32 - 8 * d)) == (pe >> (32 - 8 * d));
@@ -545,18 +549,24 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
       }
     }
     __syncthreads();
-    // the digit where the count reaches k: an inclusive scan of the 256 bins, then the one bin that
-    // crosses k
-    unsigned own = t < 256 ? hist[t] : 0u, c = own;
-    for (int off = 1; off < 256; off <<= 1) {
-      const unsigned v = (t < 256 && t >= off) ? hist[t - off] : 0u;
-      __syncthreads();
-      if (t < 256) hist[t] = c = c + v;
-      __syncthreads();
-    }
+    // the digit where the count reaches k: an inclusive scan of the 256 bins (a shuffle scan per warp of
+    // 32 bins, then the eight warp totals), then the one bin that crosses k
+    const unsigned own = t < 256 ? hist[t] : 0u;
+    unsigned c = own;
     if (t < 256) {
-      const long long k = s_k;
-      const long long before = t ? hist[t - 1] : 0;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned v = __shfl_up_sync(kFull, c, off);
+        if (lane_id() >= off) c += v;
+      }
+      if (lane_id() == 31) wsum[t >> 5] = c;
+    }
+    __syncthreads();
+    if (t < 256) {
+      unsigned add = 0;
+      for (int w = 0; w < (t >> 5); w++) add += wsum[w];
+      c += add;
+      const long long before = (long long)(c - own);
       if (before < k && (long long)c >= k) {
         s_k = k - before;
         s_match = own;
@@ -567,6 +577,25 @@ __global__ void __launch_bounds__(kSelThreads) pq_boundary_kernel(PqBufs b) {
       }
     }
     __syncthreads();
+    // one candidate left with the digits fixed so far: it is the selected key, whatever its remaining
+    // digits (candidate keys are distinct)
+    if (s_match == 1 && d < 11) {
+      const unsigned long long pe2 = s_pre_e, pf2 = s_pre_f;
+      const int dn = d + 1;  // digits fixed now
+      const long long m2 = staged ? min((long long)s_ns, (long long)kCandSmem) : n;
+      for (long long i = t; i < m2; i += kSelThreads) {
+        const uint64_t ue = (uint32_t)(staged ? sE[i] : b.cE[i]);
+        const uint64_t fp = staged ? sF[i] : b.cF[i];
+        const bool hit = dn <= 4 ? (ue >> (32 - 8 * dn)) == (pe2 >> (32 - 8 * dn))
+                                 : ue == pe2 && (fp >> (64 - 8 * (dn - 4))) == (pf2 >> (64 - 8 * (dn - 4)));
+        if (hit) {
+          s_pre_e = ue;
+          s_pre_f = fp;
+        }
+      }
+      __syncthreads();
+      break;
+    }
   }
   const int selE = (int)(uint32_t)s_pre_e;
   const uint64_t selF = s_pre_f;
