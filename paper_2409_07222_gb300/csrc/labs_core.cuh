@@ -468,7 +468,8 @@ __device__ inline int table_sum(const S& sm, const Layout& ly) {
 // ------------------------------------------------------------------------------------------------
 // Hot loop: acc[j] += sum_{u in [u_begin, u_end)} sum_{e<4} C8[4u+e] * y'_{4u+e+1}(m_j) for the M
 // neighbours of one tile (class `cls`, class indices q0 .. q0+M-1; q0 = 3 mod 4 so every window has a
-// static alignment).  u_end - u_begin must be a multiple of R = M/4 + 1.
+// static alignment).  Groups are read in turns of R = M/4 + 1 (the ring of realigned words); a range
+// that is not a whole number of turns ends with a partial one.
 // ------------------------------------------------------------------------------------------------
 template <int M, bool WIDE, class S>
 __device__ __forceinline__ void scan_range(const S& sm, const Layout& ly, int cls, int q0, int u_begin, int u_end,
@@ -497,11 +498,9 @@ __device__ __forceinline__ void scan_range(const S& sm, const Layout& ly, int cl
     }
   const uint32_t* C8w = reinterpret_cast<const uint32_t*>(sm.C8) + u_begin;
   const uint32_t* C16w = reinterpret_cast<const uint32_t*>(sm.C16) + 2 * u_begin;
-  const int n = u_end - u_begin;
-  for (int u0 = 0; u0 < n; u0 += R) {
-#pragma unroll
-    for (int du = 0; du < R; du++) {
-      const int u = u0 + du;
+  const int n = u_end > u_begin ? u_end - u_begin : 0;
+  // group u of the range in ring slot du (du = u mod R, a constant after unrolling)
+  auto step = [&](const int u, const int du) {
       uint32_t c4 = 0, clo = 0, chi = 0;
       if (WIDE) {
         clo = C16w[2 * u];
@@ -534,6 +533,19 @@ __device__ __forceinline__ void scan_range(const S& sm, const Layout& ly, int cl
         sf[r - 1][sl] = __funnelshift_r(pf[sl], pf[du], 8 * r);
         sb[r - 1][sl] = __funnelshift_r(pb[sl], pb[du], 8 * r);
       }
+  };
+  // whole ring turns, then the last partial turn (groups beyond the range are not scanned: the table
+  // is zero there, so the accumulators would not change)
+  const int nfull = n - n % R;
+  for (int u0 = 0; u0 < nfull; u0 += R) {
+#pragma unroll
+    for (int du = 0; du < R; du++) step(u0 + du, du);
+  }
+  if (nfull < n) {
+#pragma unroll
+    for (int du = 0; du < R - 1; du++) {
+      if (nfull + du >= n) break;
+      step(nfull + du, du);
     }
   }
 }

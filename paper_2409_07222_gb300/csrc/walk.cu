@@ -434,8 +434,11 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
 #pragma unroll
         for (int j = 0; j < M; j++) acc[j] = 0;
         if (has) {
+          // one lag range per tile: only the groups that hold lags (the layout pads the range to whole
+          // ring turns and the table is zero beyond G); two ranges keep their padded turns, since the
+          // two lanes of a tile run in step and the longer range sets the time anyway
           const int u_begin = h ? ly.NGh : 0;
-          const int u_end = h ? ly.NGend : ly.NGh;
+          const int u_end = H == 1 ? min(ly.NGh, ly.NG) : (h ? ly.NGend : ly.NGh);
           if (fast)
             scan_range<M, false>(sm, ly, cls, q0, u_begin, u_end, acc);
           else
