@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(32 * kFdWarps) flip_deltas_kernel(const uint64
     const bool fast = pack_c8(sm, ly);
     const int SC = table_sum(sm, ly);
     build_bytes(sm, ly);
-    p_all(sm, ly, xb_all[threadIdx.x >> 5], rb_all[threadIdx.x >> 5], Pm);
+    p_all(sm, ly, xb_all[threadIdx.x >> 5], rb_all[threadIdx.x >> 5], Pm, p + 1, ly.mlast);  // the neighbours only
     int32_t* out = dE + q * L;
     for (int i = lane; i < L; i += 32) out[i] = INT32_MAX;
     __syncwarp();

@@ -386,12 +386,14 @@ __device__ __forceinline__ int corr_pair(const uint32_t* a, const uint32_t* b, i
 }
 
 // P_m = sum_{g} s_{m - lambda g} s_{m + lambda g} over the lags with both ends inside 1..L -- for a skew
-// layout without the pair's own lag gd = c - m -- for every position m, into P_out[m - 1] (int16).
+// layout without the pair's own lag gd = c - m -- for every position m in [m_lo, m_hi] (by default all of
+// them), into P_out[m - 1] (int16).
 // Per position class (every position for lambda = 1, each parity for lambda = 2) the class sequence x
 // (x_j = s at class index j) has the self-convolution (x * x)[k] = sum_j x_j x_{k-j}, which counts each
 // product of P twice plus x_j^2: P = ((x * x)[2j] - 1) / 2.  (x * x)[k] is the correlation of x with its
 // reversal at offset n-1-k, one popcount per 32 products.  xb, rb: per-warp scratch of kBitWords words.
-__device__ inline void p_all(const ScanSmem& sm, const Layout& ly, uint32_t* xb, uint32_t* rb, int16_t* P_out) {
+__device__ inline void p_all(const ScanSmem& sm, const Layout& ly, uint32_t* xb, uint32_t* rb, int16_t* P_out,
+                             int m_lo = 1, int m_hi = kMaxL) {
   const int lane = lane_id();
   for (int cls = 0; cls < ly.ncls; cls++) {
     const int b = ly.skew ? (cls ? 1 : 2) : 1;  // first position of the class
@@ -411,7 +413,10 @@ __device__ inline void p_all(const ScanSmem& sm, const Layout& ly, uint32_t* xb,
       }
     }
     __syncwarp();
-    for (int j = lane; j < n; j += 32) {
+    // only the class indices whose positions lie in [m_lo, m_hi]
+    const int j_lo = m_lo > b ? (m_lo - b + ly.lam - 1) / ly.lam : 0;
+    const int j_end = m_hi >= b ? min(n, (m_hi - b) / ly.lam + 1) : 0;
+    for (int j = j_lo + lane; j < j_end; j += 32) {
       const int d = n - 1 - 2 * j;
       const int conv = d >= 0 ? corr_pair(xb, rb, n, d) : corr_pair(rb, xb, n, -d);
       int P = (conv - 1) / 2;
