@@ -223,6 +223,31 @@ def test_walks_l451_full_segments_through_restarts(lg):
     assert st["flips"] == n * budget
 
 
+def test_walks_bench_launch_sampled(lg):
+    """The bench's walk count and launch configuration -- 65,536 walks of L = 451, p = 24, the library's
+    own choice of variant and persistent grid, T_i = 1808, R = 16 -- with 2,000 flips each; walks sampled
+    across the id range (both ends, prefix-class boundaries, the middle) equal the oracle's walks of the
+    same ids, run one by one."""
+    import concurrent.futures as cf
+
+    L, p = 451, 24
+    pre = inp.distinct_prefixes(256, p, seed=2409)
+    n, budget, T_i, thr = 65536, 2000, 1808, 70000
+    cand, ws, st = run_walks(lg, L, True, p, pre, n, budget, T_i, seed=2409, R=16, E_thr=thr)
+    assert st["flips"] == n * budget
+    ids = [0, 1, 255, 256, 4097, 32768, 50000, 65535]
+
+    def one(w):
+        return oracle.walk_search(L, True, p, pre, 1, budget, T_i, 2409, R=16, E_thr=thr, walk_begin=w)
+
+    with cf.ThreadPoolExecutor(max_workers=8) as ex:
+        res = list(ex.map(one, ids))
+    for w, (oc, ost) in zip(ids, res):
+        for f in ("E", "walk", "step", "fp", "seq"):
+            assert np.array_equal(cand[w:w + 1][f], oc[f]), (w, f)
+        assert np.array_equal(ws[w:w + 1, :5], ost), w
+
+
 # ------------------------------------------------------------------------------------------------
 # labs_batched_search (mixed lengths, one persistent launch, CUDA graph, autotuner)
 # ------------------------------------------------------------------------------------------------
