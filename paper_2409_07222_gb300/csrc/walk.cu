@@ -8,8 +8,9 @@
 // windows, correlation table, Bloom filter of 2^bloom_log2 bits, per-neighbour slots) lives in its
 // shared-memory slab; a step is
 //   scan   -- Delta E of every free neighbour (tiled dp4a loop, labs_core.cuh),
-//   select -- warp argmin of (Delta E, m); Bloom test of the winner's fingerprint; on a hit the owner
-//             lane drops that neighbour and the argmin repeats (same result as testing them all),
+//   select -- group argmin of (Delta E, m); Bloom test of the winner's fingerprint; on a hit the owner
+//             lane puts its second best in its place and the argmin repeats (same result as testing
+//             them all),
 //   apply  -- O(L) table update, O(1)-per-neighbour P update, byte/bit flips, fingerprint, Bloom insert,
 //   sieve  -- the walk's R best distinct (E, fp) states with E <= E_thr, one per lane.
 #include <algorithm>
@@ -406,10 +407,9 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
         fold_flip<M, H, GL>(sm, ly, pend, sl_w);
         pend.on = false;
       }
-      // ---- scan; each lane keeps its best (key, m) where key orders the choice: Delta E, or the
-      //      biased score Delta E - lambda * logit[m] mapped to an order-preserving integer
-      // each lane keeps its two best (key, m): a Bloom hit on its best then hands over the second without
-      // a rescan of the lane's slots
+      // ---- scan; each lane keeps its two best (key, m), where key orders the choice: Delta E, or the
+      //      biased score Delta E - lambda * logit[m] mapped to an order-preserving integer (a Bloom hit on
+      //      its best then hands over the second without a rescan of the lane's slots)
       int bk = INT32_MAX, bm = INT32_MAX, bdE = 0;
       int bk2 = INT32_MAX, bm2 = INT32_MAX, bd2 = 0;
       bool have2 = true;
@@ -454,8 +454,7 @@ __global__ void __launch_bounds__(walk_block_threads(GL), walk_min_blocks(GL))
             acc[k] = keep + gshfl_xor<GL>(send, 1);
           }
         }
-        // finish: keys of this pass's neighbours, then their minimum by a tree of strict comparisons
-        // (the slots of a pass are in increasing m, so the left operand wins ties: smallest (key, m))
+        // finish: keys of this pass's neighbours, then their two smallest (below)
         const int m_first = q_pos(ly, cls, q_first);
         int kv[MH], mv[MH], dv[MH];
 #pragma unroll
