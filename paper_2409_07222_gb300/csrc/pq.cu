@@ -875,7 +875,8 @@ __device__ __forceinline__ int hist_mode_of(const PqState* st, long long cap) {
 // unique survivor to the smallest (pivot, column) -- the pivots are in key order, so this is the
 // sequential definition's first occurrence.  The unique survivors also enter the survivor histogram (the
 // bins the cut needs) and give the smallest fingerprint among the smallest-energy survivors.  Four
-// consecutive survivors per thread, their lookups in flight together.
+// consecutive survivors per thread, their lookups in flight together; survivors the cut cannot reach
+// are skipped.
 template <bool SEED>
 __global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b) {
   PqState* st = b.st;
@@ -902,7 +903,9 @@ __global__ void __launch_bounds__(256) pq_dedup_rep_kernel(PqBufs b) {
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       const long long i = 4 * qd + j;
-      act[j] = qd < nq && i < n && E[j] != INT32_MAX;
+      // with the cut inside the pool's occupied bins (mode 1), a survivor above them is never admitted
+      // nor the round's smallest (survivors inside them exist then), so its representative is not needed
+      act[j] = qd < nq && i < n && E[j] != INT32_MAX && !(mode == 1 && e_bin(E[j], Eb) > pmax);
       fp[j] = act[j] ? b.dFp[i] : 0ull;
       k[j] = dedup_key(E[j], fp[j]);
       s[j] = (k[j] * kGamma) >> (64 - b.hs_log2);
